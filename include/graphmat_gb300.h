@@ -1,0 +1,213 @@
+/*
+ * graphmat_gb300.h -- C ABI of the GraphMat superstep engine for NVIDIA GB300 (sm_103a).
+ *
+ * GraphMat (Sundaram et al., VLDB 2015) runs a vertex program as a sequence of
+ * supersteps (Algorithm 2).  Each superstep turns the send_message outputs of the
+ * active vertices into a sparse vector x, multiplies the transposed adjacency
+ * matrix by x with process_message as the multiply and reduce as the add
+ * (Algorithm 1, the generalized SPMV), applies the reduced values to the vertex
+ * properties, and makes the vertices whose property changed active for the next
+ * superstep.  This library runs that loop on one GPU for the built-in programs of
+ * Section 3 (PageRank, BFS, SSSP, triangle counting, collaborative filtering).
+ *
+ * Conventions for every call:
+ *  - Every call returns a gm_status; nothing aborts, traps or prints.
+ *    gm_last_error() gives a one-line description of the last failure on the
+ *    calling thread.
+ *  - Input arrays are copied; the caller keeps ownership.  Outputs go to buffers
+ *    the caller provides.  A handle and all device memory it owns are released
+ *    only by gm_graph_destroy.
+ *  - Pointers flagged "on_device"/"is_device" are CUDA device pointers of the
+ *    current device; otherwise they are host pointers (pageable or pinned).
+ *  - All GPU work of a handle is ordered on the CUDA stream given at creation
+ *    (NULL = legacy default stream).  Calls that return data to the host
+ *    synchronise that stream.  A handle must not be used by two host threads at
+ *    once.
+ *  - Vertex ids are int32 in [0, n); n < 2^31 and edge counts < 2^31 - 1.
+ */
+#ifndef GRAPHMAT_GB300_H
+#define GRAPHMAT_GB300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GM_API __attribute__((visibility("default")))
+#else
+#define GM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gm_graph gm_graph;
+
+typedef enum gm_status {
+    GM_OK = 0,
+    GM_ERR_INVALID_ARG = 1,    /* bad pointer, size, vertex id or program parameter */
+    GM_ERR_OUT_OF_MEMORY = 2,  /* a device or pinned allocation failed */
+    GM_ERR_CUDA = 3,           /* a CUDA runtime call failed (see gm_last_error) */
+    GM_ERR_STATE = 4,          /* calls in the wrong order, e.g. gm_run before gm_program_set */
+    GM_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+    GM_ERR_UNSUPPORTED = 6     /* valid request this build does not handle */
+} gm_status;
+
+typedef enum gm_weight_type {
+    GM_W_NONE = 0, /* unweighted: every edge value is 1 */
+    GM_W_U32 = 1,  /* uint32 edge values (SSSP weights, CF ratings) */
+    GM_W_F32 = 2   /* float edge values (weighted PageRank) */
+} gm_weight_type;
+
+/* An edge list: edge i goes from src[i] to dst[i] with value weight[i]. */
+typedef struct gm_edge_list {
+    int64_t n_vertices;   /* n */
+    int64_t n_edges;      /* number of entries in src/dst/weight */
+    const int32_t* src;
+    const int32_t* dst;
+    const void* weight;   /* NULL, or n_edges values of weight_type */
+    int32_t weight_type;  /* gm_weight_type */
+    int32_t on_device;    /* 1: src/dst/weight are device pointers; 0: host pointers */
+    int64_t n_left;       /* collaborative filtering: users are [0, n_left), items [n_left, n) */
+} gm_edge_list;
+
+/* Ingest flags (Section 5.1 preprocessing). */
+enum {
+    GM_DROP_SELF_LOOPS = 1,   /* remove edges v -> v */
+    GM_DEDUP = 2,             /* keep the first occurrence (input order) of each (src, dst) */
+    GM_SYMMETRIZE = 4,        /* add dst -> src for every edge (after all originals, same value) */
+    GM_ORIENT_BY_DEGREE = 8   /* keep u -> v only if (deg(u), u) < (deg(v), v): a DAG for triangle counting */
+};
+
+/*
+ * gm_graph_create -- ingest an edge list into CSR (out-edges) and CSC (in-edges)
+ * form on the GPU, with out/in-degrees and degree-binned vertex lists.
+ * Paper: Section 4.3.1 (the matrix store; DCSC there, CSR + CSC here) and
+ * Section 5.1 (self-loop removal, symmetrisation, orientation).
+ *   el      edge list; ids outside [0, n) give GM_ERR_INVALID_ARG.
+ *   flags   GM_* ingest flags, applied in the order symmetrise, drop self-loops,
+ *           dedup, orient.
+ *   stream  cudaStream_t for all work of this handle (NULL = default stream).
+ *   out     receives the handle on GM_OK, NULL otherwise.
+ * The call synchronises `stream` before returning.
+ */
+GM_API gm_status gm_graph_create(const gm_edge_list* el, uint32_t flags, void* stream, gm_graph** out);
+
+/* Release the handle and all its device memory (synchronises its stream). NULL is a no-op. */
+GM_API gm_status gm_graph_destroy(gm_graph* g);
+
+/* Vertex count and edge count after cleaning. */
+GM_API gm_status gm_graph_info(const gm_graph* g, int64_t* n_vertices, int64_t* n_edges);
+
+/* Copy the cleaned edges in CSR order (sorted by (src, dst)): src, dst as int32
+ * and, if the graph is weighted and `weight` is not NULL, the 4-byte values.
+ * Any output pointer may be NULL.  Per-edge arrays of gm_wpagerank_* use this order. */
+GM_API gm_status gm_graph_get_edges(const gm_graph* g, int32_t* src, int32_t* dst, void* weight,
+                             int dst_is_device);
+
+/* Out-degree and in-degree of every vertex (int32[n] each; either may be NULL). */
+GM_API gm_status gm_graph_get_degrees(const gm_graph* g, int32_t* out_deg, int32_t* in_deg,
+                               int dst_is_device);
+
+typedef enum gm_program_kind {
+    GM_PAGERANK = 0,        /* Eq. 1 */
+    GM_BFS = 1,             /* Section 3.II */
+    GM_SSSP = 2,            /* Section 3.V and the appendix program */
+    GM_TRIANGLE_COUNT = 3,  /* Section 3.IV, two vertex programs (Section 4.2) */
+    GM_CF = 4               /* Section 3.III, Eqs. 2-5, gradient descent */
+} gm_program_kind;
+
+typedef struct gm_program_params {
+    double r;              /* PageRank random-surf probability r of Eq. 1 (damping 0.85 -> r = 0.15) */
+    int32_t pr_apply_all;  /* PageRank: 1 = Eq. 1 for every vertex (a vertex without in-edges gets r);
+                              0 = Algorithm 2, apply only to vertices that received a message */
+    int32_t K;             /* CF latent dimension (1..64) */
+    double lambda;         /* CF regularisation weight of Eqs. 2, 4, 5 */
+    double gamma;          /* CF step size of Eqs. 4, 5 */
+    double init_sigma;     /* CF initial factors ~ N(0, init_sigma) */
+    uint64_t seed;         /* CF initial-factor seed (counter-based SplitMix64 + Box-Muller) */
+} gm_program_params;
+
+/*
+ * gm_program_set -- select the vertex program and (re)initialise the vertex
+ * property of every vertex: PageRank 1.0 (Section 3.I), BFS/SSSP infinity =
+ * UINT32_MAX (Sections 3.II, 3.V; appendix run_sssp), triangle counts 0, CF
+ * factors N(0, init_sigma) drawn from `seed`.  No vertex is active afterwards
+ * (except PageRank and CF, where all vertices are active every superstep).
+ * `params` may be NULL for BFS, SSSP and triangle counting.
+ * SSSP needs a GM_W_U32 graph (an unweighted graph uses weight 1); CF needs
+ * n_left > 0 and GM_W_U32 ratings.
+ */
+GM_API gm_status gm_program_set(gm_graph* g, int32_t kind, const gm_program_params* params);
+
+/*
+ * gm_set_active -- mark vertices active for the next gm_run (appendix run_sssp:
+ * the source gets distance 0 and is marked active).  BFS/SSSP: each listed
+ * vertex gets property 0 and is active; several vertices make a multi-source
+ * traversal.  count < 0 marks every vertex active (vertices is ignored).
+ * Duplicate ids are allowed.  `src_is_device` says where `vertices` lives.
+ */
+GM_API gm_status gm_set_active(gm_graph* g, const int32_t* vertices, int64_t count, int src_is_device);
+
+/*
+ * gm_run -- Algorithm 2: run supersteps until no vertex is active or
+ * `max_iters` supersteps have run (max_iters = -1: until no vertex is active, as
+ * run_graph_program(..., -1, ...) in the appendix).  PageRank and CF run exactly
+ * max_iters >= 0 supersteps.  Triangle counting runs its two programs and
+ * ignores max_iters.  iters_done (may be NULL) receives the number of supersteps
+ * executed, counting the final one that found no active vertex.
+ * The call synchronises the stream.
+ */
+GM_API gm_status gm_run(gm_graph* g, int32_t max_iters, int32_t* iters_done);
+
+/*
+ * Copy the vertex property array out: BFS/SSSP uint32[n], PageRank float[n],
+ * triangle counting uint64[n] (triangles incident to each vertex), CF float[n*K]
+ * row-major.  `bytes` must equal that size.
+ */
+GM_API gm_status gm_get_vertex_state(gm_graph* g, void* dst, int64_t bytes, int dst_is_device);
+
+/* Overwrite the vertex property array (same layout and size as above); used to
+ * resume a run or to start CF from given factors.  Activity is not changed. */
+GM_API gm_status gm_set_vertex_state(gm_graph* g, const void* src, int64_t bytes, int src_is_device);
+
+enum {
+    GM_SCALAR_TC_TOTAL = 1,       /* uint64: triangles in the graph */
+    GM_SCALAR_CF_LOSS = 2,        /* double: Eq. 2 loss at the current factors (regulariser once per vertex) */
+    GM_SCALAR_REACHED_EDGES = 3,  /* int64: sum of out-degrees of vertices with finite BFS/SSSP property */
+    GM_SCALAR_SUPERSTEPS = 4,     /* int32: supersteps of the last gm_run */
+    GM_SCALAR_PUSH_STEPS = 5,     /* int32: supersteps of the last gm_run run top-down (push) */
+    GM_SCALAR_PULL_STEPS = 6,     /* int32: supersteps run bottom-up (pull) */
+    GM_SCALAR_SCANNED_EDGES = 7,  /* int64: edges read by the relax kernels in the last gm_run */
+    GM_SCALAR_RELAX_MS = 8,       /* double: profile mode, summed relax-kernel time (CUDA events) */
+    GM_SCALAR_RELAX_LAUNCHES = 9, /* int32: profile mode, relax-kernel launches timed */
+    GM_SCALAR_PROCESSED_VERTICES = 10 /* int64: vertices whose edge lists the relax kernels read */
+};
+GM_API gm_status gm_get_scalar(gm_graph* g, int32_t which, void* out);
+
+/* Engine options (not program parameters). */
+enum {
+    GM_OPT_DIRECTION = 1,     /* 0 auto push/pull switch (default), 1 push only, 2 pull only */
+    GM_OPT_LOOP_MODE = 2,     /* 0 superstep loop inside one CUDA graph (default), 1 host loop */
+    GM_OPT_PROFILE = 3,       /* 1: host loop with CUDA events around every relax launch */
+    GM_OPT_BIN_SMALL = 4,     /* degree below which vertices are processed 32 per warp */
+    GM_OPT_BIN_LARGE = 5,     /* degree from which a whole CTA processes one vertex */
+    GM_OPT_ALPHA_X1000 = 6,   /* BFS push->pull switch: frontier edges > unvisited in-edges / alpha */
+    GM_OPT_BETA_X1000 = 7,    /* BFS pull->push switch: frontier vertices < n / beta */
+    GM_OPT_SSSP_PULL_PPM = 8  /* SSSP: pull when frontier edges > ppm * 1e-6 * m */
+};
+GM_API gm_status gm_set_option(gm_graph* g, int32_t option, int64_t value);
+
+/* Number of kernel launches this library has issued since load (all handles). */
+GM_API uint64_t gm_kernel_launch_count(void);
+
+/* Readable name of a status code (static string). */
+GM_API const char* gm_status_string(gm_status s);
+
+/* One-line description of the last error on the calling thread ("" if none). */
+GM_API const char* gm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAPHMAT_GB300_H */

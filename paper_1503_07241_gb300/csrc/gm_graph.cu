@@ -1,0 +1,532 @@
+// Graph ingest: edge list -> cleaned CSR (out-edges) + CSC (in-edges) on the GPU,
+// degrees and degree-binned vertex lists.  Section 4.3.1 stores G^T as DCSC
+// partitions for OpenMP threads; on GB300 the whole graph sits in HBM as CSR (the
+// push side of Algorithm 1: the columns of G^T) plus CSC (the pull side), int32
+// indices, with vertices grouped by degree so each group gets a fitting
+// thread/warp/CTA mapping.  Section 5.1 gives the cleaning steps.
+#include <cstring>
+#include <new>
+
+#include "gm_internal.cuh"
+
+namespace gm {
+
+const char* last_error();
+
+namespace {
+
+__global__ void count_bad_ids(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
+                              int64_t n, unsigned long long* bad) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool b = false;
+    if (i < m) b = src[i] < 0 || src[i] >= n || dst[i] < 0 || dst[i] >= n;
+    unsigned mask = __ballot_sync(0xffffffffu, b);
+    if ((threadIdx.x & 31) == 0 && mask) atomicAdd(bad, (unsigned long long)__popc(mask));
+}
+
+// Keys (src << b | dst); the reversed copies of a symmetrised list follow all
+// originals.  Self-loops to drop get the all-ones key (sorted last).
+__global__ void build_keys(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
+                           int64_t total, int b, int drop_loops, uint64_t* __restrict__ keys,
+                           uint32_t* __restrict__ vals) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    int64_t j = i < m ? i : i - m;
+    uint32_t s = (uint32_t)(i < m ? src[j] : dst[j]);
+    uint32_t d = (uint32_t)(i < m ? dst[j] : src[j]);
+    uint64_t marker = (b >= 32) ? ~0ull : ((1ull << (2 * b)) - 1ull);
+    keys[i] = (drop_loops && s == d) ? marker : (((uint64_t)s << b) | d);
+    vals[i] = (uint32_t)j;
+}
+
+__global__ void keep_flags(const uint64_t* __restrict__ keys, int64_t total, int b, int drop_loops,
+                           int dedup, uint32_t* __restrict__ flags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    uint64_t marker = ((1ull << (2 * b)) - 1ull);
+    uint64_t k = keys[i];
+    bool keep = !(drop_loops && k == marker);
+    if (keep && dedup && i > 0 && keys[i - 1] == k) keep = false;
+    flags[i] = keep ? 1u : 0u;
+}
+
+// Scatter kept edges: split key into (first, second) ids, carry the value.
+__global__ void compact_edges(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                              const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pos,
+                              int64_t total, int b, int32_t* __restrict__ first, int32_t* __restrict__ second,
+                              uint32_t* __restrict__ val_out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total || !flags[i]) return;
+    uint32_t p = pos[i];
+    uint64_t k = keys[i];
+    first[p] = (int32_t)(k >> b);
+    second[p] = (int32_t)(k & ((1ull << b) - 1ull));
+    val_out[p] = vals[i];
+}
+
+// ptr[v] = first position p with ids[p] >= v (ids non-decreasing), ptr[n] = len.
+__global__ void fill_ptr(const int32_t* __restrict__ ids, int64_t len, int64_t n, int32_t* __restrict__ ptr) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > len) return;
+    int64_t lo = p == 0 ? 0 : (int64_t)ids[p - 1] + 1;
+    int64_t hi = p == len ? n : (int64_t)ids[p];
+    for (int64_t v = lo; v <= hi; ++v) ptr[v] = (int32_t)p;
+}
+
+__global__ void orient_flags(const int32_t* __restrict__ esrc, const int32_t* __restrict__ edst, int64_t len,
+                             const int32_t* __restrict__ ptr, uint32_t* __restrict__ flags) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= len) return;
+    int32_t u = esrc[p], v = edst[p];
+    int32_t du = ptr[u + 1] - ptr[u], dv = ptr[v + 1] - ptr[v];
+    flags[p] = (du < dv || (du == dv && u < v)) ? 1u : 0u;
+}
+
+__global__ void compact_triples(const int32_t* __restrict__ a, const int32_t* __restrict__ b,
+                                const uint32_t* __restrict__ c, const uint32_t* __restrict__ flags,
+                                const uint32_t* __restrict__ pos, int64_t len, int32_t* __restrict__ ao,
+                                int32_t* __restrict__ bo, uint32_t* __restrict__ co) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len || !flags[i]) return;
+    uint32_t p = pos[i];
+    ao[p] = a[i];
+    bo[p] = b[i];
+    co[p] = c[i];
+}
+
+__global__ void gather_u32(const uint32_t* __restrict__ in, const uint32_t* __restrict__ idx, int64_t len,
+                           uint32_t* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) out[i] = in[idx[i]];
+}
+
+__global__ void csc_keys(const int32_t* __restrict__ esrc, const int32_t* __restrict__ edst, int64_t len, int b,
+                         uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= len) return;
+    keys[p] = ((uint64_t)(uint32_t)edst[p] << b) | (uint32_t)esrc[p];
+    vals[p] = (uint32_t)p;
+}
+
+__global__ void csc_split(const uint64_t* __restrict__ keys, int64_t len, int b, int32_t* __restrict__ dst_ids,
+                          int32_t* __restrict__ row) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= len) return;
+    uint64_t k = keys[q];
+    dst_ids[q] = (int32_t)(k >> b);
+    row[q] = (int32_t)(k & ((1ull << b) - 1ull));
+}
+
+__global__ void degrees_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ cp, int64_t n,
+                               int32_t* __restrict__ od, int32_t* __restrict__ id) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    od[v] = rp[v + 1] - rp[v];
+    id[v] = cp[v + 1] - cp[v];
+}
+
+__device__ __forceinline__ uint8_t degree_bin(int32_t d, int32_t small, int32_t large) {
+    return d == 0 ? 0 : (d < small ? 1 : (d < large ? 2 : 3));
+}
+
+__global__ void bins_kernel(const int32_t* __restrict__ od, const int32_t* __restrict__ id, int64_t n,
+                            int32_t small, int32_t large, uint8_t* __restrict__ ob, uint8_t* __restrict__ ib) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    ob[v] = degree_bin(od[v], small, large);
+    ib[v] = degree_bin(id[v], small, large);
+}
+
+__global__ void bin_match_flags(const uint8_t* __restrict__ bins, int64_t n, uint8_t want,
+                                uint32_t* __restrict__ flags) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) flags[v] = bins[v] == want ? 1u : 0u;
+}
+
+inline unsigned blocks_for(int64_t n, int t = 256) {
+    int64_t b = (n + t - 1) / t;
+    return (unsigned)(b > 0 ? b : 1);
+}
+
+int bits_for(int64_t n) {
+    int b = 1;
+    while (b < 31 && (1ll << b) < n) ++b;
+    return b;
+}
+
+#define LAUNCH_CHECK()                                                                     \
+    do {                                                                                   \
+        g_launches++;                                                                      \
+        cudaError_t _e = cudaGetLastError();                                               \
+        if (_e != cudaSuccess) {                                                           \
+            set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(_e), __FILE__, \
+                      __LINE__);                                                           \
+            return GM_ERR_CUDA;                                                            \
+        }                                                                                  \
+    } while (0)
+
+}  // namespace
+
+// Rebuild degree bins and the binned in-degree vertex list for the current thresholds.
+gm_status build_bins(gm_graph* g) {
+    cudaStream_t s = g->stream;
+    const int64_t n = g->n;
+    GM_TRY(dev_alloc(g->out_bin, n > 0 ? n : 1, s));
+    GM_TRY(dev_alloc(g->in_bin, n > 0 ? n : 1, s));
+    if (n > 0) {
+        bins_kernel<<<blocks_for(n), 256, 0, s>>>(as<int32_t>(g->out_deg), as<int32_t>(g->in_deg), n,
+                                                  g->tune.bin_small, g->tune.bin_large,
+                                                  as<uint8_t>(g->out_bin), as<uint8_t>(g->in_bin));
+        LAUNCH_CHECK();
+    }
+    GM_TRY(dev_alloc(g->in_list, sizeof(int32_t) * (n > 0 ? n : 1), s));
+    GM_TRY(dev_alloc(g->zero_in_list, sizeof(int32_t) * (n > 0 ? n : 1), s));
+    DevBuf flags, cnt;
+    GM_TRY(dev_alloc(flags, sizeof(uint32_t) * (n > 0 ? n : 1), s));
+    gm_status st = dev_alloc(cnt, sizeof(uint32_t) * 4, s);
+    uint32_t hc[4] = {0, 0, 0, 0};
+    int64_t off = 0;
+    for (int bin = 0; bin <= 3 && st == GM_OK; ++bin) {
+        if (n > 0) {
+            bin_match_flags<<<blocks_for(n), 256, 0, s>>>(as<uint8_t>(g->in_bin), n, (uint8_t)bin,
+                                                          as<uint32_t>(flags));
+            g_launches++;
+        }
+        int32_t* dst = bin == 0 ? as<int32_t>(g->zero_in_list) : as<int32_t>(g->in_list) + off;
+        st = compact_indices(as<uint32_t>(flags), n, dst, as<uint32_t>(cnt) + bin, s);
+        if (st != GM_OK) break;
+        cudaError_t e = cudaMemcpyAsync(&hc[bin], as<uint32_t>(cnt) + bin, sizeof(uint32_t),
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { set_error("bins: %s", cudaGetErrorString(e)); st = GM_ERR_CUDA; break; }
+        if (bin > 0) off += hc[bin];
+    }
+    dev_free(flags, s);
+    dev_free(cnt, s);
+    if (st != GM_OK) return st;
+    g->zero_in_count = hc[0];
+    g->in_list_count[0] = 0;
+    g->in_list_count[1] = hc[1];
+    g->in_list_count[2] = hc[1] + hc[2];
+    g->in_list_count[3] = hc[1] + hc[2] + hc[3];
+    return GM_OK;
+}
+
+static gm_status ingest(gm_graph* g, const gm_edge_list* el, uint32_t flags) {
+    cudaStream_t s = g->stream;
+    const int64_t n = el->n_vertices, m = el->n_edges;
+    const bool sym = flags & GM_SYMMETRIZE, drop = flags & GM_DROP_SELF_LOOPS, dedup = flags & GM_DEDUP,
+               orient = flags & GM_ORIENT_BY_DEGREE;
+    const int64_t total = sym ? 2 * m : m;
+    const int b = bits_for(n);
+
+    // ---- upload the raw list ----
+    DevBuf d_src, d_dst, d_w;
+    const int32_t* src = el->src;
+    const int32_t* dst = el->dst;
+    const uint32_t* win = static_cast<const uint32_t*>(el->weight);
+    struct Scope {
+        cudaStream_t s;
+        DevBuf* bufs[24];
+        int k = 0;
+        ~Scope() { for (int i = 0; i < k; ++i) dev_free(*bufs[i], s); }
+        void add(DevBuf& b) { bufs[k++] = &b; }
+    } scope{s};
+    scope.add(d_src); scope.add(d_dst); scope.add(d_w);
+    if (!el->on_device && m > 0) {
+        GM_TRY(dev_alloc(d_src, sizeof(int32_t) * m, s));
+        GM_TRY(dev_alloc(d_dst, sizeof(int32_t) * m, s));
+        GM_CUDA_TRY(cudaMemcpyAsync(d_src.p, el->src, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+        GM_CUDA_TRY(cudaMemcpyAsync(d_dst.p, el->dst, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+        src = as<int32_t>(d_src);
+        dst = as<int32_t>(d_dst);
+        if (g->wtype != GM_W_NONE) {
+            GM_TRY(dev_alloc(d_w, sizeof(uint32_t) * m, s));
+            GM_CUDA_TRY(cudaMemcpyAsync(d_w.p, el->weight, sizeof(uint32_t) * m, cudaMemcpyHostToDevice, s));
+            win = as<uint32_t>(d_w);
+        }
+    }
+
+    // ---- validate ids ----
+    DevBuf bad;
+    scope.add(bad);
+    GM_TRY(dev_alloc(bad, sizeof(unsigned long long), s));
+    GM_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(unsigned long long), s));
+    if (m > 0) {
+        count_bad_ids<<<blocks_for(m), 256, 0, s>>>(src, dst, m, n, as<unsigned long long>(bad));
+        LAUNCH_CHECK();
+    }
+    unsigned long long hbad = 0;
+    GM_CUDA_TRY(cudaMemcpyAsync(&hbad, bad.p, sizeof(hbad), cudaMemcpyDeviceToHost, s));
+    GM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hbad) {
+        set_error("gm_graph_create: %llu edge endpoints outside [0, %lld)", hbad, (long long)n);
+        return GM_ERR_INVALID_ARG;
+    }
+
+    // ---- sort (src, dst), clean ----
+    DevBuf keys, vals, keys2, vals2, fl, pos;
+    scope.add(keys); scope.add(vals); scope.add(keys2); scope.add(vals2); scope.add(fl); scope.add(pos);
+    GM_TRY(dev_alloc(keys, sizeof(uint64_t) * (total > 0 ? total : 1), s));
+    GM_TRY(dev_alloc(vals, sizeof(uint32_t) * (total > 0 ? total : 1), s));
+    GM_TRY(dev_alloc(keys2, sizeof(uint64_t) * (total > 0 ? total : 1), s));
+    GM_TRY(dev_alloc(vals2, sizeof(uint32_t) * (total > 0 ? total : 1), s));
+    GM_TRY(dev_alloc(fl, sizeof(uint32_t) * (total > 0 ? total : 1), s));
+    GM_TRY(dev_alloc(pos, sizeof(uint32_t) * (total + 1), s));
+    if (total > 0) {
+        build_keys<<<blocks_for(total), 256, 0, s>>>(src, dst, m, total, b, drop ? 1 : 0, as<uint64_t>(keys),
+                                                     as<uint32_t>(vals));
+        LAUNCH_CHECK();
+        GM_TRY(radix_sort_pairs(as<uint64_t>(keys), as<uint32_t>(vals), as<uint64_t>(keys2),
+                                as<uint32_t>(vals2), total, 2 * b, s));
+        keep_flags<<<blocks_for(total), 256, 0, s>>>(as<uint64_t>(keys), total, b, drop ? 1 : 0, dedup ? 1 : 0,
+                                                     as<uint32_t>(fl));
+        LAUNCH_CHECK();
+    }
+    GM_TRY(scan_exclusive_u32(as<uint32_t>(fl), as<uint32_t>(pos), total, s));
+    uint32_t m1 = 0;
+    GM_CUDA_TRY(cudaMemcpyAsync(&m1, as<uint32_t>(pos) + total, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    GM_CUDA_TRY(cudaStreamSynchronize(s));
+
+    DevBuf esrc, edst, perm;
+    scope.add(esrc); scope.add(edst); scope.add(perm);
+    GM_TRY(dev_alloc(esrc, sizeof(int32_t) * (m1 > 0 ? m1 : 1), s));
+    GM_TRY(dev_alloc(edst, sizeof(int32_t) * (m1 > 0 ? m1 : 1), s));
+    GM_TRY(dev_alloc(perm, sizeof(uint32_t) * (m1 > 0 ? m1 : 1), s));
+    if (total > 0) {
+        compact_edges<<<blocks_for(total), 256, 0, s>>>(as<uint64_t>(keys), as<uint32_t>(vals), as<uint32_t>(fl),
+                                                        as<uint32_t>(pos), total, b, as<int32_t>(esrc),
+                                                        as<int32_t>(edst), as<uint32_t>(perm));
+        LAUNCH_CHECK();
+    }
+    GM_TRY(dev_alloc(g->row_ptr, sizeof(int32_t) * (n + 1), s));
+    fill_ptr<<<blocks_for((int64_t)m1 + 1), 256, 0, s>>>(as<int32_t>(esrc), m1, n, as<int32_t>(g->row_ptr));
+    LAUNCH_CHECK();
+
+    int64_t mm = m1;
+    if (orient && mm > 0) {
+        orient_flags<<<blocks_for(mm), 256, 0, s>>>(as<int32_t>(esrc), as<int32_t>(edst), mm,
+                                                    as<int32_t>(g->row_ptr), as<uint32_t>(fl));
+        LAUNCH_CHECK();
+        GM_TRY(scan_exclusive_u32(as<uint32_t>(fl), as<uint32_t>(pos), mm, s));
+        uint32_t m2 = 0;
+        GM_CUDA_TRY(cudaMemcpyAsync(&m2, as<uint32_t>(pos) + mm, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        GM_CUDA_TRY(cudaStreamSynchronize(s));
+        DevBuf esrc2, edst2, perm2;
+        scope.add(esrc2); scope.add(edst2); scope.add(perm2);
+        GM_TRY(dev_alloc(esrc2, sizeof(int32_t) * (m2 > 0 ? m2 : 1), s));
+        GM_TRY(dev_alloc(edst2, sizeof(int32_t) * (m2 > 0 ? m2 : 1), s));
+        GM_TRY(dev_alloc(perm2, sizeof(uint32_t) * (m2 > 0 ? m2 : 1), s));
+        compact_triples<<<blocks_for(mm), 256, 0, s>>>(as<int32_t>(esrc), as<int32_t>(edst), as<uint32_t>(perm),
+                                                       as<uint32_t>(fl), as<uint32_t>(pos), mm, as<int32_t>(esrc2),
+                                                       as<int32_t>(edst2), as<uint32_t>(perm2));
+        LAUNCH_CHECK();
+        std::swap(esrc, esrc2);
+        std::swap(edst, edst2);
+        std::swap(perm, perm2);
+        mm = m2;
+        fill_ptr<<<blocks_for(mm + 1), 256, 0, s>>>(as<int32_t>(esrc), mm, n, as<int32_t>(g->row_ptr));
+        LAUNCH_CHECK();
+    }
+    g->m = mm;
+
+    // ---- CSR arrays ----
+    GM_TRY(dev_alloc(g->col, sizeof(int32_t) * (mm > 0 ? mm : 1), s));
+    if (mm > 0)
+        GM_CUDA_TRY(cudaMemcpyAsync(g->col.p, edst.p, sizeof(int32_t) * mm, cudaMemcpyDeviceToDevice, s));
+    if (g->wtype != GM_W_NONE) {
+        GM_TRY(dev_alloc(g->w, sizeof(uint32_t) * (mm > 0 ? mm : 1), s));
+        if (mm > 0) {
+            gather_u32<<<blocks_for(mm), 256, 0, s>>>(win, as<uint32_t>(perm), mm, as<uint32_t>(g->w));
+            LAUNCH_CHECK();
+        }
+    }
+
+    // ---- CSC by a second sort on (dst, src) ----
+    GM_TRY(dev_alloc(g->col_ptr, sizeof(int32_t) * (n + 1), s));
+    GM_TRY(dev_alloc(g->row, sizeof(int32_t) * (mm > 0 ? mm : 1), s));
+    GM_TRY(dev_alloc(g->csc_pos, sizeof(uint32_t) * (mm > 0 ? mm : 1), s));
+    if (mm > 0) {
+        csc_keys<<<blocks_for(mm), 256, 0, s>>>(as<int32_t>(esrc), as<int32_t>(edst), mm, b, as<uint64_t>(keys),
+                                                as<uint32_t>(vals));
+        LAUNCH_CHECK();
+        GM_TRY(radix_sort_pairs(as<uint64_t>(keys), as<uint32_t>(vals), as<uint64_t>(keys2), as<uint32_t>(vals2),
+                                mm, 2 * b, s));
+        csc_split<<<blocks_for(mm), 256, 0, s>>>(as<uint64_t>(keys), mm, b, as<int32_t>(esrc), as<int32_t>(g->row));
+        LAUNCH_CHECK();
+        GM_CUDA_TRY(cudaMemcpyAsync(g->csc_pos.p, vals.p, sizeof(uint32_t) * mm, cudaMemcpyDeviceToDevice, s));
+    }
+    fill_ptr<<<blocks_for(mm + 1), 256, 0, s>>>(as<int32_t>(esrc), mm, n, as<int32_t>(g->col_ptr));
+    LAUNCH_CHECK();
+    if (g->wtype != GM_W_NONE) {
+        GM_TRY(dev_alloc(g->cw, sizeof(uint32_t) * (mm > 0 ? mm : 1), s));
+        if (mm > 0) {
+            gather_u32<<<blocks_for(mm), 256, 0, s>>>(as<uint32_t>(g->w), as<uint32_t>(g->csc_pos), mm,
+                                                      as<uint32_t>(g->cw));
+            LAUNCH_CHECK();
+        }
+    }
+
+    // ---- degrees and bins ----
+    GM_TRY(dev_alloc(g->out_deg, sizeof(int32_t) * (n > 0 ? n : 1), s));
+    GM_TRY(dev_alloc(g->in_deg, sizeof(int32_t) * (n > 0 ? n : 1), s));
+    if (n > 0) {
+        degrees_kernel<<<blocks_for(n), 256, 0, s>>>(as<int32_t>(g->row_ptr), as<int32_t>(g->col_ptr), n,
+                                                     as<int32_t>(g->out_deg), as<int32_t>(g->in_deg));
+        LAUNCH_CHECK();
+    }
+    GM_TRY(build_bins(g));
+    GM_CUDA_TRY(cudaStreamSynchronize(s));
+    return GM_OK;
+}
+
+void release_graph(gm_graph* g);
+
+}  // namespace gm
+
+using namespace gm;
+
+extern "C" {
+
+gm_status gm_graph_create(const gm_edge_list* el, uint32_t flags, void* stream, gm_graph** out) {
+    if (out) *out = nullptr;
+    if (!el || !out) { set_error("gm_graph_create: NULL argument"); return GM_ERR_INVALID_ARG; }
+    if (el->n_vertices < 0 || el->n_vertices >= (1ll << 31) - 1 || el->n_edges < 0) {
+        set_error("gm_graph_create: n_vertices must be in [0, 2^31-1) and n_edges >= 0");
+        return GM_ERR_INVALID_ARG;
+    }
+    if (el->n_edges > 0 && (!el->src || !el->dst)) {
+        set_error("gm_graph_create: NULL src/dst with n_edges > 0");
+        return GM_ERR_INVALID_ARG;
+    }
+    if (el->weight_type < GM_W_NONE || el->weight_type > GM_W_F32 ||
+        (el->weight_type != GM_W_NONE && el->n_edges > 0 && !el->weight)) {
+        set_error("gm_graph_create: bad weight_type or NULL weight");
+        return GM_ERR_INVALID_ARG;
+    }
+    if (flags & ~(uint32_t)(GM_DROP_SELF_LOOPS | GM_DEDUP | GM_SYMMETRIZE | GM_ORIENT_BY_DEGREE)) {
+        set_error("gm_graph_create: unknown flag bits");
+        return GM_ERR_INVALID_ARG;
+    }
+    const int64_t total = (flags & GM_SYMMETRIZE) ? 2 * el->n_edges : el->n_edges;
+    if (total >= (1ll << 31) - 1) {
+        set_error("gm_graph_create: %lld edges exceed the int32 edge-offset limit", (long long)total);
+        return GM_ERR_UNSUPPORTED;
+    }
+    if (el->n_left < 0 || el->n_left > el->n_vertices) {
+        set_error("gm_graph_create: n_left outside [0, n]");
+        return GM_ERR_INVALID_ARG;
+    }
+    gm_graph* g = new (std::nothrow) gm_graph();
+    if (!g) { set_error("gm_graph_create: host allocation failed"); return GM_ERR_OUT_OF_MEMORY; }
+    g->n = el->n_vertices;
+    g->n_left = el->n_left;
+    g->flags = flags;
+    g->stream = static_cast<cudaStream_t>(stream);
+    g->wtype = el->weight_type;
+    gm_status st = ingest(g, el, flags);
+    if (st != GM_OK) {
+        cudaStreamSynchronize(g->stream);
+        release_graph(g);
+        return st;
+    }
+    *out = g;
+    return GM_OK;
+}
+
+gm_status gm_graph_destroy(gm_graph* g) {
+    if (!g) return GM_OK;
+    release_graph(g);
+    return GM_OK;
+}
+
+gm_status gm_graph_info(const gm_graph* g, int64_t* n_vertices, int64_t* n_edges) {
+    if (!g) { set_error("gm_graph_info: NULL handle"); return GM_ERR_INVALID_ARG; }
+    if (n_vertices) *n_vertices = g->n;
+    if (n_edges) *n_edges = g->m;
+    return GM_OK;
+}
+
+gm_status gm_graph_get_edges(const gm_graph* g, int32_t* src, int32_t* dst, void* weight, int dst_is_device) {
+    if (!g) { set_error("gm_graph_get_edges: NULL handle"); return GM_ERR_INVALID_ARG; }
+    cudaStream_t s = g->stream;
+    cudaMemcpyKind k = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (src && g->m > 0) {
+        // expand row_ptr into per-edge sources
+        DevBuf tmp;
+        int32_t* target = src;
+        if (!dst_is_device) {
+            GM_TRY(dev_alloc(tmp, sizeof(int32_t) * g->m, s));
+            target = as<int32_t>(tmp);
+        }
+        gm_status st = expand_rows(as<int32_t>(g->row_ptr), g->n, target, s);
+        if (st == GM_OK && !dst_is_device) {
+            cudaError_t e = cudaMemcpyAsync(src, target, sizeof(int32_t) * g->m, cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) { set_error("gm_graph_get_edges: %s", cudaGetErrorString(e)); st = GM_ERR_CUDA; }
+        }
+        cudaStreamSynchronize(s);
+        dev_free(tmp, s);
+        if (st != GM_OK) return st;
+    }
+    if (dst && g->m > 0) GM_CUDA_TRY(cudaMemcpyAsync(dst, g->col.p, sizeof(int32_t) * g->m, k, s));
+    if (weight && g->m > 0 && g->w.p) GM_CUDA_TRY(cudaMemcpyAsync(weight, g->w.p, sizeof(uint32_t) * g->m, k, s));
+    GM_CUDA_TRY(cudaStreamSynchronize(s));
+    return GM_OK;
+}
+
+gm_status gm_graph_get_degrees(const gm_graph* g, int32_t* out_deg, int32_t* in_deg, int dst_is_device) {
+    if (!g) { set_error("gm_graph_get_degrees: NULL handle"); return GM_ERR_INVALID_ARG; }
+    cudaMemcpyKind k = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (out_deg && g->n > 0) GM_CUDA_TRY(cudaMemcpyAsync(out_deg, g->out_deg.p, sizeof(int32_t) * g->n, k, g->stream));
+    if (in_deg && g->n > 0) GM_CUDA_TRY(cudaMemcpyAsync(in_deg, g->in_deg.p, sizeof(int32_t) * g->n, k, g->stream));
+    GM_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return GM_OK;
+}
+
+uint64_t gm_kernel_launch_count(void) { return g_launches.load(); }
+
+const char* gm_status_string(gm_status s) {
+    switch (s) {
+        case GM_OK: return "GM_OK";
+        case GM_ERR_INVALID_ARG: return "GM_ERR_INVALID_ARG";
+        case GM_ERR_OUT_OF_MEMORY: return "GM_ERR_OUT_OF_MEMORY";
+        case GM_ERR_CUDA: return "GM_ERR_CUDA";
+        case GM_ERR_STATE: return "GM_ERR_STATE";
+        case GM_ERR_TIMEOUT: return "GM_ERR_TIMEOUT";
+        case GM_ERR_UNSUPPORTED: return "GM_ERR_UNSUPPORTED";
+    }
+    return "GM_ERR_UNKNOWN";
+}
+
+const char* gm_last_error(void) { return gm::last_error(); }
+
+}  // extern "C"
+
+namespace gm {
+
+__global__ void expand_rows_kernel(const int32_t* __restrict__ ptr, int64_t n, int32_t* __restrict__ out) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    for (int32_t e = ptr[v]; e < ptr[v + 1]; ++e) out[e] = (int32_t)v;
+}
+
+gm_status expand_rows(const int32_t* ptr, int64_t n, int32_t* out, cudaStream_t s) {
+    if (n <= 0) return GM_OK;
+    expand_rows_kernel<<<blocks_for(n), 256, 0, s>>>(ptr, n, out);
+    LAUNCH_CHECK();
+    return GM_OK;
+}
+
+void release_graph(gm_graph* g) {
+    cudaStream_t s = g->stream;
+    trav_release(g);
+    DevBuf* bufs[] = {&g->row_ptr, &g->col, &g->w, &g->col_ptr, &g->row, &g->cw, &g->csc_pos,
+                      &g->out_deg, &g->in_deg, &g->out_bin, &g->in_bin, &g->in_list, &g->zero_in_list,
+                      &g->state, &g->work, &g->ctl_buf};
+    for (DevBuf* b : bufs) dev_free(*b, s);
+    if (g->host_pinned) cudaFreeHost(g->host_pinned);
+    cudaStreamSynchronize(s);
+    delete g;
+}
+
+}  // namespace gm

@@ -1,0 +1,158 @@
+// Internal declarations of the GraphMat GB300 library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include <atomic>
+#include <string>
+
+#include "graphmat_gb300.h"
+
+namespace gm {
+
+constexpr uint32_t kInf = 0xFFFFFFFFu;  // "infinite" BFS depth / SSSP distance
+constexpr int kNumBins = 3;             // degree bins: small (warp-cooperative), medium (warp), large (CTA)
+
+// Library-wide count of kernel launches issued (a graph replay counts each
+// kernel node it runs).
+extern std::atomic<uint64_t> g_launches;
+
+void set_error(const char* fmt, ...);
+
+#define GM_CUDA_TRY(expr)                                                             \
+    do {                                                                              \
+        cudaError_t _e = (expr);                                                      \
+        if (_e != cudaSuccess) {                                                      \
+            ::gm::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e),    \
+                            __FILE__, __LINE__);                                      \
+            return _e == cudaErrorMemoryAllocation ? GM_ERR_OUT_OF_MEMORY : GM_ERR_CUDA; \
+        }                                                                             \
+    } while (0)
+
+#define GM_TRY(expr)                          \
+    do {                                      \
+        gm_status _s = (expr);                \
+        if (_s != GM_OK) return _s;           \
+    } while (0)
+
+// Device buffer owned by the library (cudaMallocAsync on the graph's stream).
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+gm_status dev_alloc(DevBuf& b, size_t bytes, cudaStream_t s);
+void dev_free(DevBuf& b, cudaStream_t s);
+template <typename T>
+inline T* as(const DevBuf& b) { return static_cast<T*>(b.p); }
+
+// ---- primitives (gm_primitives.cu) -------------------------------------------------
+// Exclusive scan of n uint32 values; out[n] receives the total (out has n+1 slots).
+gm_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the keys.
+// keys/vals are sorted in place; the alternate buffers are scratch of the same size.
+gm_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                           int64_t n, int bits, cudaStream_t s);
+// Compact the indices i in [0, n) with flag[i] != 0 into out (ascending); count to *count_dev.
+gm_status compact_indices(const uint32_t* flags, int64_t n, int32_t* out, uint32_t* count_dev,
+                          cudaStream_t s);
+
+int num_sms();
+
+// ---- traversal control block (device memory) --------------------------------------
+struct TravCtl {
+    uint32_t iter;                // superstep index t
+    uint32_t dir;                 // 0 = push (top-down over the queue), 1 = pull (bottom-up over in-edges)
+    uint32_t done;                // 1 once converged or at max_iters
+    uint32_t ticket;              // last-CTA election in the finalize kernel
+    uint32_t count[3][4];         // active vertices per rotating slot and out-degree bin (0 = no out-edges)
+    unsigned long long medges[3]; // sum of out-degrees of each slot's queue
+    unsigned long long unvisited_in_edges;  // BFS: in-edges of still-unvisited vertices
+    unsigned long long scanned_edges;       // edges read (statistics)
+    unsigned long long processed_vertices;  // vertices whose edge list was read (statistics)
+    uint32_t pushes, pulls;       // supersteps run in each direction
+    uint32_t iters_done;
+    uint32_t bad_ids;             // seeding saw vertex ids outside [0, n)
+    uint32_t guard_hit;           // the loop passed n + 1 supersteps (impossible for valid runs)
+    uint32_t pad;
+};
+
+// Options and tuning knobs of a graph handle.
+struct Tuning {
+    int32_t bin_small = 32;     // degree < bin_small: warp-cooperative group of 32 vertices
+    int32_t bin_large = 2048;   // degree >= bin_large: one CTA per vertex
+    double alpha = 14.0;        // push -> pull when frontier edges > unvisited edges / alpha
+    double beta = 24.0;         // pull -> push when frontier vertices < n / beta
+    double sssp_pull_frac = 0.05;  // SSSP: pull when frontier edges > sssp_pull_frac * m
+    int32_t direction = 0;      // 0 auto, 1 push only, 2 pull only
+    int32_t loop_mode = 0;      // 0 device loop (CUDA graph with a conditional WHILE node), 1 host loop
+    int32_t profile = 0;        // 1: host loop with CUDA events around every relax launch
+};
+
+struct RunStats {
+    int32_t supersteps = 0, pushes = 0, pulls = 0;
+    int64_t scanned_edges = 0;
+    int64_t processed_vertices = 0;
+    double relax_ms = 0.0;      // profile mode: summed relax-kernel time
+    int32_t relax_launches = 0;
+    double finalize_ms = 0.0;
+    int32_t finalize_launches = 0;
+};
+
+}  // namespace gm
+
+// The opaque handle.
+struct gm_graph {
+    int64_t n = 0, m = 0, n_left = 0;
+    uint32_t flags = 0;
+    cudaStream_t stream = nullptr;
+    int32_t wtype = GM_W_NONE;
+    // CSR: out-edges sorted by (src, dst)
+    gm::DevBuf row_ptr, col, w;      // w: uint32 or float per CSR edge (as wtype)
+    // CSC: in-edges sorted by (dst, src)
+    gm::DevBuf col_ptr, row, cw, csc_pos;  // cw: CSC copy of w; csc_pos: CSR index of each CSC edge
+    gm::DevBuf out_deg, in_deg;      // int32
+    gm::DevBuf out_bin, in_bin;      // uint8 bin of each vertex by out/in degree (0 = degree zero)
+    gm::DevBuf in_list;              // vertex ids with in_deg > 0, grouped by in-degree bin
+    int64_t in_list_count[gm::kNumBins + 1] = {0};  // offsets of bins 1..3 inside in_list
+    gm::DevBuf zero_in_list;         // vertex ids with in_deg == 0
+    int64_t zero_in_count = 0;
+    gm::Tuning tune;
+    gm::RunStats stats;
+
+    // program state
+    int32_t kind = -1;
+    gm_program_params params{};
+    bool active_set = false;
+    gm::DevBuf state;                // uint32 dist / float rank / uint64 count / float factors
+    gm::DevBuf work;                 // program workspace (see each program)
+    int64_t work_bytes = 0;
+    gm::DevBuf ctl_buf;              // TravCtl
+    void* host_pinned = nullptr;     // small pinned staging buffer
+    // device-loop graph for traversal
+    cudaGraph_t loop_graph = nullptr;
+    cudaGraphExec_t loop_exec = nullptr;
+    int32_t loop_graph_max_iters = -2;
+    uint64_t loop_graph_kernels = 0;
+    // results
+    uint64_t tc_total = 0;
+};
+
+namespace gm {
+// per-program entry points (implemented in gm_traverse.cu, gm_pagerank.cu, ...)
+gm_status trav_prepare(gm_graph* g);
+gm_status trav_set_active(gm_graph* g, const int32_t* vertices_dev, int64_t count);
+gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done);
+void trav_release(gm_graph* g);
+gm_status pr_prepare(gm_graph* g);
+gm_status pr_run(gm_graph* g, int32_t iters, int32_t* iters_done);
+gm_status tc_run(gm_graph* g, int32_t* iters_done);
+gm_status cf_prepare(gm_graph* g);
+gm_status cf_run(gm_graph* g, int32_t iters, int32_t* iters_done);
+gm_status cf_loss(gm_graph* g, double* out);
+gm_status reached_edges(gm_graph* g, int64_t* out);
+// Per-edge source ids of a CSR (out[e] = v for e in [ptr[v], ptr[v+1])).
+gm_status expand_rows(const int32_t* ptr, int64_t n, int32_t* out, cudaStream_t s);
+}  // namespace gm

@@ -1,0 +1,315 @@
+// Device-wide primitives used by graph ingest: exclusive scan, stable LSD radix
+// sort of (uint64 key, uint32 value) pairs, and index compaction.  Written for
+// sm_103a: 32-wide warps, warp match/ballot for stable digit ranking.
+#include <cstdarg>
+#include <cstdio>
+
+#include "gm_internal.cuh"
+
+namespace gm {
+
+std::atomic<uint64_t> g_launches{0};
+
+static thread_local char t_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_err, sizeof(t_err), fmt, ap);
+    va_end(ap);
+}
+
+const char* last_error() { return t_err; }
+
+gm_status dev_alloc(DevBuf& b, size_t bytes, cudaStream_t s) {
+    dev_free(b, s);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(&b.p, bytes, s);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? GM_ERR_OUT_OF_MEMORY : GM_ERR_CUDA;
+    }
+    b.bytes = bytes;
+    return GM_OK;
+}
+
+void dev_free(DevBuf& b, cudaStream_t s) {
+    if (b.p) cudaFreeAsync(b.p, s);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+// ------------------------------------------------------------------------------
+// Exclusive scan (three phases: tile sums, scan of tile sums, tile scans).
+// ------------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;  // 4096 values per CTA
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the block total.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* smem_warp, uint32_t& excl) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = warp_incl_scan(v);
+    if (lane == 31) smem_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t = lane < (kScanThreads / 32) ? smem_warp[lane] : 0;
+        uint32_t ti = warp_incl_scan(t);
+        if (lane < (kScanThreads / 32)) smem_warp[lane] = ti - t;
+        if (lane == 31) smem_warp[kScanThreads / 32] = ti;
+    }
+    __syncthreads();
+    excl = smem_warp[warp] + incl - v;
+    uint32_t total = smem_warp[kScanThreads / 32];
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_tile_sums(const uint32_t* __restrict__ in, int64_t n,
+                                                               uint32_t* __restrict__ sums) {
+    __shared__ uint32_t sw[kScanThreads / 32 + 1];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < n) acc += in[i];
+    }
+    uint32_t excl;
+    uint32_t tot = block_excl_scan(acc, sw, excl);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Each thread scans kScanItems consecutive values (blocked arrangement).
+__global__ void __launch_bounds__(kScanThreads) scan_tiles(const uint32_t* __restrict__ in, int64_t n,
+                                                           const uint32_t* __restrict__ tile_off,
+                                                           uint32_t* __restrict__ out, int write_total) {
+    __shared__ uint32_t sw[kScanThreads / 32 + 1];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + k;
+        v[k] = i < n ? in[i] : 0u;
+        acc += v[k];
+    }
+    uint32_t excl;
+    uint32_t tot = block_excl_scan(acc, sw, excl);
+    uint32_t run = excl + (tile_off ? tile_off[blockIdx.x] : 0u);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + k;
+        if (i < n) out[i] = run;
+        run += v[k];
+    }
+    if (write_total && threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) {
+        out[n] = (tile_off ? tile_off[blockIdx.x] : 0u) + tot;
+    }
+}
+
+gm_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s) {
+    if (n <= 0) {
+        GM_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(uint32_t), s));
+        return GM_OK;
+    }
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 1) {
+        scan_tiles<<<1, kScanThreads, 0, s>>>(in, n, nullptr, out, 1);
+        g_launches++;
+        GM_CUDA_TRY(cudaGetLastError());
+        return GM_OK;
+    }
+    DevBuf sums, offs;
+    GM_TRY(dev_alloc(sums, sizeof(uint32_t) * tiles, s));
+    gm_status st = dev_alloc(offs, sizeof(uint32_t) * (tiles + 1), s);
+    if (st != GM_OK) { dev_free(sums, s); return st; }
+    scan_tile_sums<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, as<uint32_t>(sums));
+    g_launches++;
+    st = scan_exclusive_u32(as<uint32_t>(sums), as<uint32_t>(offs), tiles, s);
+    if (st == GM_OK) {
+        scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, as<uint32_t>(offs), out, 1);
+        g_launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) { set_error("scan: %s", cudaGetErrorString(e)); st = GM_ERR_CUDA; }
+    }
+    dev_free(sums, s);
+    dev_free(offs, s);
+    return st;
+}
+
+// ------------------------------------------------------------------------------
+// Stable LSD radix sort, 8-bit digits.  One pass = per-tile digit histogram,
+// exclusive scan of the digit-major histogram, stable scatter.  The scatter
+// ranks keys inside a tile with __match_any_sync: warp w owns a contiguous
+// sub-range of the tile and walks it 32 keys at a time in input order.
+// ------------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortRounds = 8;                            // 32-key rounds per warp
+constexpr int kSortTile = kSortThreads * kSortRounds;     // 2048 keys per CTA
+constexpr int kRadix = 256;
+
+__global__ void __launch_bounds__(kSortThreads) radix_hist(const uint64_t* __restrict__ keys, int64_t n,
+                                                           int shift, int64_t tiles,
+                                                           uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[kRadix];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll
+    for (int k = 0; k < kSortRounds; ++k) {
+        int64_t i = base + (int64_t)k * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 0xFF], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint64_t* __restrict__ keys_in,
+                                                              const uint32_t* __restrict__ vals_in, int64_t n,
+                                                              int shift, int64_t tiles,
+                                                              const uint32_t* __restrict__ hist_scan,
+                                                              uint64_t* __restrict__ keys_out,
+                                                              uint32_t* __restrict__ vals_out) {
+    __shared__ uint32_t wcnt[kSortWarps][kRadix];
+    __shared__ uint32_t goff[kRadix];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&wcnt[0][0])[i] = 0;
+    goff[threadIdx.x] = hist_scan[(int64_t)threadIdx.x * tiles + blockIdx.x];
+    __syncthreads();
+
+    const int64_t wbase = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * (32 * kSortRounds);
+    uint64_t k[kSortRounds];
+    uint32_t v[kSortRounds];
+    uint32_t rank[kSortRounds];
+    const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        int64_t i = wbase + r * 32 + lane;
+        bool valid = i < n;
+        k[r] = valid ? keys_in[i] : 0ull;
+        v[r] = valid ? vals_in[i] : 0u;
+        // invalid lanes get a digit value no valid key has (256)
+        uint32_t d = valid ? (uint32_t)((k[r] >> shift) & 0xFF) : 256u;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t base = valid ? wcnt[warp][d] : 0u;
+        __syncwarp();
+        if (valid) {
+            rank[r] = base + __popc(peers & lt_mask);
+            int leader = __ffs(peers) - 1;
+            if (lane == leader) wcnt[warp][d] = base + __popc(peers);
+        } else {
+            rank[r] = 0;
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // exclusive prefix over warps, one digit per thread
+    {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) {
+            uint32_t c = wcnt[w][threadIdx.x];
+            wcnt[w][threadIdx.x] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        int64_t i = wbase + r * 32 + lane;
+        if (i < n) {
+            uint32_t d = (uint32_t)((k[r] >> shift) & 0xFF);
+            uint32_t pos = goff[d] + wcnt[warp][d] + rank[r];
+            keys_out[pos] = k[r];
+            vals_out[pos] = v[r];
+        }
+    }
+}
+
+gm_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                           int64_t n, int bits, cudaStream_t s) {
+    if (n <= 1 || bits <= 0) return GM_OK;
+    const int64_t tiles = (n + kSortTile - 1) / kSortTile;
+    const int passes = (bits + 7) / 8;
+    DevBuf hist, hscan;
+    GM_TRY(dev_alloc(hist, sizeof(uint32_t) * kRadix * tiles, s));
+    gm_status st = dev_alloc(hscan, sizeof(uint32_t) * (kRadix * tiles + 1), s);
+    if (st != GM_OK) { dev_free(hist, s); return st; }
+    uint64_t* kin = keys; uint32_t* vin = vals;
+    uint64_t* kout = keys_alt; uint32_t* vout = vals_alt;
+    for (int p = 0; p < passes && st == GM_OK; ++p) {
+        const int shift = 8 * p;
+        radix_hist<<<(unsigned)tiles, kSortThreads, 0, s>>>(kin, n, shift, tiles, as<uint32_t>(hist));
+        g_launches++;
+        st = scan_exclusive_u32(as<uint32_t>(hist), as<uint32_t>(hscan), kRadix * tiles, s);
+        if (st != GM_OK) break;
+        radix_scatter<<<(unsigned)tiles, kSortThreads, 0, s>>>(kin, vin, n, shift, tiles,
+                                                               as<uint32_t>(hscan), kout, vout);
+        g_launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) { set_error("radix sort: %s", cudaGetErrorString(e)); st = GM_ERR_CUDA; }
+        uint64_t* tk = kin; kin = kout; kout = tk;
+        uint32_t* tv = vin; vin = vout; vout = tv;
+    }
+    if (st == GM_OK && kin != keys) {
+        cudaError_t e1 = cudaMemcpyAsync(keys, kin, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s);
+        cudaError_t e2 = cudaMemcpyAsync(vals, vin, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) { set_error("radix sort copy-back failed"); st = GM_ERR_CUDA; }
+    }
+    dev_free(hist, s);
+    dev_free(hscan, s);
+    return st;
+}
+
+// ------------------------------------------------------------------------------
+// Compaction of flagged indices (stable).
+// ------------------------------------------------------------------------------
+__global__ void compact_scatter(const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pos,
+                                int64_t n, int32_t* __restrict__ out, uint32_t* __restrict__ count_dev) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flags[i]) out[pos[i]] = (int32_t)i;
+    if (i == 0) *count_dev = pos[n];
+}
+
+gm_status compact_indices(const uint32_t* flags, int64_t n, int32_t* out, uint32_t* count_dev,
+                          cudaStream_t s) {
+    DevBuf pos;
+    GM_TRY(dev_alloc(pos, sizeof(uint32_t) * (n + 1), s));
+    gm_status st = scan_exclusive_u32(flags, as<uint32_t>(pos), n, s);
+    if (st == GM_OK) {
+        int64_t blocks = (n + 255) / 256;
+        if (blocks == 0) blocks = 1;
+        compact_scatter<<<(unsigned)blocks, 256, 0, s>>>(flags, as<uint32_t>(pos), n, out, count_dev);
+        g_launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) { set_error("compact: %s", cudaGetErrorString(e)); st = GM_ERR_CUDA; }
+    }
+    dev_free(pos, s);
+    return st;
+}
+
+}  // namespace gm

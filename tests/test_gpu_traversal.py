@@ -1,0 +1,175 @@
+"""BFS and SSSP on the GPU against the FP64 oracle: bit-exact properties and
+identical superstep counts (Algorithm 2 semantics), every direction mode and
+loop mode, edge cases, and the scale-22 workload."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import CLEAN, check_sssp_certificate, random_case, rmat_case
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+DIRS = [0, 1, 2]  # auto, push only, pull only
+
+
+def _run(gm, g, kind, sources, max_iters=-1):
+    g.program_set(kind)
+    g.set_active(sources)
+    it = g.run(max_iters)
+    return g.state(), it
+
+
+@pytest.mark.parametrize("direction", DIRS)
+@pytest.mark.parametrize("kind", ["bfs", "sssp"])
+def test_rmat_small_parity(gm, kind, direction):
+    n, s, d, w = rmat_case(12, weighted=True)
+    g = gm.Graph(n, s, d, w)
+    g.set_option(gm.GM_OPT_DIRECTION, direction)
+    og = oracle.Graph(n, s, d, w)
+    for src in synth.pick_sources(n, s, d, 4, seed=11):
+        if kind == "bfs":
+            got, it = _run(gm, g, gm.GM_BFS, [src])
+            ref, rit = og.bfs([src])
+        else:
+            got, it = _run(gm, g, gm.GM_SSSP, [src])
+            ref, rit = og.sssp([src])
+        assert np.array_equal(got, ref)
+        assert it == rit
+
+
+@pytest.mark.parametrize("loop_mode", [0, 1])
+@pytest.mark.parametrize("seed", range(3))
+def test_random_graphs_multi_source(gm, seed, loop_mode):
+    rng = np.random.default_rng(1000 + seed)
+    n, s, d, w = random_case(rng, int(rng.integers(2, 5000)), int(rng.integers(1, 40000)), weighted=True)
+    g = gm.Graph(n, s, d, w)
+    g.set_option(gm.GM_OPT_LOOP_MODE, loop_mode)
+    og = oracle.Graph(n, s, d, w)
+    srcs = rng.choice(n, size=min(n, 3), replace=False).astype(np.int32)
+    got, it = _run(gm, g, gm.GM_BFS, srcs)
+    ref, rit = og.bfs(srcs)
+    assert np.array_equal(got, ref) and it == rit
+    got, it = _run(gm, g, gm.GM_SSSP, srcs)
+    ref, rit = og.sssp(srcs)
+    assert np.array_equal(got, ref) and it == rit
+
+
+def test_bin_thresholds_do_not_change_results(gm):
+    n, s, d, w = rmat_case(13, weighted=True)
+    g = gm.Graph(n, s, d, w)
+    og = oracle.Graph(n, s, d, w)
+    src = synth.pick_sources(n, s, d, 1, seed=3)
+    ref, rit = og.sssp(src)
+    for small, large in [(2, 4), (8, 64), (32, 2048), (64, 1 << 20)]:
+        g.set_option(gm.GM_OPT_BIN_SMALL, small)
+        g.set_option(gm.GM_OPT_BIN_LARGE, large)
+        for direction in DIRS:
+            g.set_option(gm.GM_OPT_DIRECTION, direction)
+            got, it = _run(gm, g, gm.GM_SSSP, src)
+            assert np.array_equal(got, ref) and it == rit
+
+
+def test_max_iters_truncates_like_oracle(gm):
+    n, s, d, w = rmat_case(11, weighted=True)
+    g = gm.Graph(n, s, d, w)
+    og = oracle.Graph(n, s, d, w)
+    src = synth.pick_sources(n, s, d, 1, seed=5)
+    for k in (0, 1, 2, 3, 5):
+        got, it = _run(gm, g, gm.GM_SSSP, src, max_iters=k)
+        ref, rit = og.sssp(src, max_iters=k)
+        assert it == rit
+        if k > 0:
+            assert np.array_equal(got, ref)
+
+
+def test_golden_tiny(gm):
+    gd = json.load(open(os.path.join(GOLDEN, "sssp_bfs_tiny.json")))
+    g = gm.Graph(gd["n"], np.array(gd["src"], np.int32), np.array(gd["dst"], np.int32),
+                 np.array(gd["w"], np.uint32))
+    for loop_mode in (0, 1):
+        g.set_option(gm.GM_OPT_LOOP_MODE, loop_mode)
+        got, it = _run(gm, g, gm.GM_SSSP, [gd["source"]])
+        assert got.tolist() == gd["sssp_dist"] and it == gd["sssp_supersteps"]
+        got, it = _run(gm, g, gm.GM_BFS, [gd["source"]])
+        assert got.tolist() == gd["bfs_depth"] and it == gd["bfs_supersteps"]
+
+
+def test_edge_cases(gm):
+    # isolated source: one superstep that finds nothing
+    g = gm.Graph(5, np.array([1], np.int32), np.array([2], np.int32))
+    got, it = _run(gm, g, gm.GM_BFS, [0])
+    assert it == 1 and got.tolist() == [0] + [gm.INF_U32] * 4
+    # no active vertex
+    g.program_set(gm.GM_SSSP)
+    assert g.run() == 1
+    assert np.all(g.state() == gm.INF_U32)
+    # unweighted SSSP is BFS
+    n, s, d, _ = rmat_case(10)
+    g = gm.Graph(n, s, d)
+    a, _ = _run(gm, g, gm.GM_SSSP, [1])
+    b, _ = _run(gm, g, gm.GM_BFS, [1])
+    assert np.array_equal(a, b)
+    # all vertices active: every property 0, one superstep... plus convergence
+    g.program_set(gm.GM_BFS)
+    g.set_active(None)
+    g.run()
+    assert np.all(g.state() == 0)
+    # duplicate sources
+    a, _ = _run(gm, g, gm.GM_BFS, [1, 1, 1])
+    b, _ = _run(gm, g, gm.GM_BFS, [1])
+    assert np.array_equal(a, b)
+    # bad source id
+    g.program_set(gm.GM_BFS)
+    with pytest.raises(gm.GMError):
+        g.set_active([n])
+    # run before program_set
+    g2 = gm.Graph(3, np.array([0], np.int32), np.array([1], np.int32))
+    with pytest.raises(gm.GMError) as ei:
+        g2.run()
+    assert ei.value.status == gm.GM_ERR_STATE
+
+
+def test_saturating_weights(gm):
+    big = np.array([0xFFFFFFF0, 0x20], np.uint32)
+    g = gm.Graph(3, np.array([0, 1], np.int32), np.array([1, 2], np.int32), big)
+    got, _ = _run(gm, g, gm.GM_SSSP, [0])
+    assert got.tolist() == [0, 0xFFFFFFF0, gm.INF_U32]
+
+
+def test_symmetrized_bfs(gm):
+    n, s, d, _ = rmat_case(12)
+    flags = CLEAN | oracle.SYMMETRIZE
+    g = gm.Graph(n, s, d, flags=flags)
+    og = oracle.Graph(n, s, d, flags=flags)
+    src = synth.pick_sources(n, s, d, 2, seed=9)
+    got, it = _run(gm, g, gm.GM_BFS, src[:1])
+    ref, rit = og.bfs(src[:1])
+    assert np.array_equal(got, ref) and it == rit
+
+
+@pytest.mark.slow
+def test_scale22_workload(gm):
+    """The benchmark workload: RMAT scale 22, edge factor 16, uint32 weights in
+    [1, 255].  BFS depths and superstep counts match the oracle on two sources;
+    SSSP matches the oracle on one source and passes the exact shortest-path
+    certificate (relaxed + tight edges) on two more."""
+    n, s, d, w = rmat_case(22, weighted=True)
+    g = gm.Graph(n, s, d, w)
+    og = oracle.Graph(n, s, d, w)
+    cs, cd, cv = og.edges()
+    srcs = synth.pick_sources(n, s, d, 16, seed=synth.BASE_SEED + 1)
+    for src in srcs[:2]:
+        got, it = _run(gm, g, gm.GM_BFS, [src])
+        ref, rit = og.bfs([src])
+        assert np.array_equal(got, ref) and it == rit
+    got, it = _run(gm, g, gm.GM_SSSP, [srcs[0]])
+    ref, rit = og.sssp([srcs[0]])
+    assert np.array_equal(got, ref) and it == rit
+    for src in srcs[1:3]:
+        got, _ = _run(gm, g, gm.GM_SSSP, [src])
+        check_sssp_certificate(n, cs, cd, cv.astype(np.uint32), got, np.array([src]))
