@@ -184,6 +184,15 @@ enum {
 };
 GM_API gm_status gm_get_scalar(gm_graph* g, int32_t which, void* out);
 
+/*
+ * Per-superstep trace of the last gm_run in profile mode (GM_OPT_PROFILE = 1):
+ * up to max_rows rows of 7 doubles -- superstep index, direction (0 push, 1 pull),
+ * active vertices at its start, edges read, vertices whose edge lists were read,
+ * relax-kernel time in ms (CUDA events), and the out-edges of the next frontier.
+ * *n_rows receives the number of rows available.
+ */
+GM_API gm_status gm_get_trace(gm_graph* g, double* rows, int32_t max_rows, int32_t* n_rows);
+
 /* Engine options (not program parameters). */
 enum {
     GM_OPT_DIRECTION = 1,     /* 0 auto push/pull switch (default), 1 push only, 2 pull only */

@@ -71,6 +71,7 @@ SIGNATURES = {
     "gm_set_vertex_state": ([_P, _P, _I64, ctypes.c_int], ctypes.c_int),
     "gm_get_scalar": ([_P, _I32, _P], ctypes.c_int),
     "gm_set_option": ([_P, _I32, _I64], ctypes.c_int),
+    "gm_get_trace": ([_P, _P, _I32, ctypes.POINTER(_I32)], ctypes.c_int),
     "gm_kernel_launch_count": ([], _U64),
     "gm_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "gm_last_error": ([], ctypes.c_char_p),
@@ -244,6 +245,15 @@ class Graph:
         v = _SCALAR_TYPES[which]()
         _check(lib().gm_get_scalar(self._h, which, ctypes.byref(v)), "gm_get_scalar")
         return v.value
+
+    def trace(self):
+        """Per-superstep rows of the last profiled run (see gm_get_trace)."""
+        k = ctypes.c_int32()
+        _check(lib().gm_get_trace(self._h, None, 0, ctypes.byref(k)), "gm_get_trace")
+        rows = np.empty((k.value, 7), np.float64)
+        if k.value:
+            _check(lib().gm_get_trace(self._h, rows.ctypes.data, k.value, ctypes.byref(k)), "gm_get_trace")
+        return rows
 
     def set_option(self, option, value):
         _check(lib().gm_set_option(self._h, option, int(value)), "gm_set_option")

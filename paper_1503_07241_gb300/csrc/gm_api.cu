@@ -194,6 +194,15 @@ gm_status gm_get_scalar(gm_graph* g, int32_t which, void* out) {
     return GM_ERR_INVALID_ARG;
 }
 
+gm_status gm_get_trace(gm_graph* g, double* rows, int32_t max_rows, int32_t* n_rows) {
+    if (!g || (max_rows > 0 && !rows)) { set_error("gm_get_trace: NULL argument"); return GM_ERR_INVALID_ARG; }
+    const int64_t avail = (int64_t)(g->stats.trace.size() / kTraceCols);
+    if (n_rows) *n_rows = (int32_t)avail;
+    const int64_t k = max_rows < avail ? max_rows : avail;
+    for (int64_t i = 0; i < k * kTraceCols; ++i) rows[i] = g->stats.trace[(size_t)i];
+    return GM_OK;
+}
+
 gm_status gm_set_option(gm_graph* g, int32_t option, int64_t value) {
     if (!g) { set_error("gm_set_option: NULL handle"); return GM_ERR_INVALID_ARG; }
     Tuning& t = g->tune;

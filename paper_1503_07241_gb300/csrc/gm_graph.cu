@@ -288,8 +288,9 @@ static gm_status ingest(gm_graph* g, const gm_edge_list* el, uint32_t flags) {
     GM_CUDA_TRY(cudaMemcpyAsync(&m1, as<uint32_t>(pos) + total, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
 
-    DevBuf esrc, edst, perm;
+    DevBuf esrc, edst, perm, esrc2, edst2, perm2;  // function scope: the cleanup list points at them
     scope.add(esrc); scope.add(edst); scope.add(perm);
+    scope.add(esrc2); scope.add(edst2); scope.add(perm2);
     GM_TRY(dev_alloc(esrc, sizeof(int32_t) * (m1 > 0 ? m1 : 1), s));
     GM_TRY(dev_alloc(edst, sizeof(int32_t) * (m1 > 0 ? m1 : 1), s));
     GM_TRY(dev_alloc(perm, sizeof(uint32_t) * (m1 > 0 ? m1 : 1), s));
@@ -312,8 +313,6 @@ static gm_status ingest(gm_graph* g, const gm_edge_list* el, uint32_t flags) {
         uint32_t m2 = 0;
         GM_CUDA_TRY(cudaMemcpyAsync(&m2, as<uint32_t>(pos) + mm, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         GM_CUDA_TRY(cudaStreamSynchronize(s));
-        DevBuf esrc2, edst2, perm2;
-        scope.add(esrc2); scope.add(edst2); scope.add(perm2);
         GM_TRY(dev_alloc(esrc2, sizeof(int32_t) * (m2 > 0 ? m2 : 1), s));
         GM_TRY(dev_alloc(edst2, sizeof(int32_t) * (m2 > 0 ? m2 : 1), s));
         GM_TRY(dev_alloc(perm2, sizeof(uint32_t) * (m2 > 0 ? m2 : 1), s));

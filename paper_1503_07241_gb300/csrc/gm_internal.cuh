@@ -7,6 +7,7 @@
 
 #include <atomic>
 #include <string>
+#include <vector>
 
 #include "graphmat_gb300.h"
 
@@ -99,7 +100,10 @@ struct RunStats {
     int32_t relax_launches = 0;
     double finalize_ms = 0.0;
     int32_t finalize_launches = 0;
+    // profile mode: one row per superstep (see gm_get_trace)
+    std::vector<double> trace;
 };
+constexpr int kTraceCols = 7;
 
 }  // namespace gm
 

@@ -743,7 +743,17 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
             GM_CUDA_TRY(cudaEventCreate(&ev0));
             GM_CUDA_TRY(cudaEventCreate(&ev1));
         }
+        unsigned long long prev_e = 0, prev_v = 0;
         for (int32_t it = 0;; ++it) {
+            uint32_t dir_before = 0, frontier_before = 0;
+            if (ev0) {  // direction and frontier size of this superstep, for the trace
+                GM_CUDA_TRY(cudaMemcpyAsync(hp, g->ctl_buf.p, sizeof(TravCtlDev), cudaMemcpyDeviceToHost, s));
+                GM_CUDA_TRY(cudaStreamSynchronize(s));
+                dir_before = hp->c.dir;
+                const uint32_t slot = hp->c.iter % 3u;
+                frontier_before = hp->c.count[slot][0] + hp->c.count[slot][1] + hp->c.count[slot][2] +
+                                  hp->c.count[slot][3];
+            }
             if (ev0) cudaEventRecord(ev0, s);
             if (sssp) trav_relax<true><<<rg, kThreads, 0, s>>>(a);
             else trav_relax<false><<<rg, kThreads, 0, s>>>(a);
@@ -762,6 +772,17 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
                 cudaEventElapsedTime(&ms, ev0, ev1);
                 g->stats.relax_ms += ms;
                 g->stats.relax_launches++;
+                const uint32_t done = hp->c.done;
+                GM_CUDA_TRY(cudaMemcpyAsync(hp, g->ctl_buf.p, sizeof(TravCtlDev), cudaMemcpyDeviceToHost, s));
+                GM_CUDA_TRY(cudaStreamSynchronize(s));
+                const double row[kTraceCols] = {(double)it, (double)dir_before, (double)frontier_before,
+                                                (double)(hp->c.scanned_edges - prev_e),
+                                                (double)(hp->c.processed_vertices - prev_v), (double)ms,
+                                                (double)hp->c.medges[(it + 1) % 3]};
+                prev_e = hp->c.scanned_edges;
+                prev_v = hp->c.processed_vertices;
+                g->stats.trace.insert(g->stats.trace.end(), row, row + kTraceCols);
+                hp->c.done = done;
             }
             if (hp->c.done) break;
         }

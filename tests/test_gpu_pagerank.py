@@ -56,6 +56,7 @@ def test_bins_and_hub(gm):
     og = oracle.Graph(n, s, d)
     ref, _ = og.pagerank(0.15, 20)
     for small, large in [(32, 2048), (4, 16), (2, 1 << 20)]:
+        g.set_option(gm.GM_OPT_BIN_LARGE, 1 << 30)
         g.set_option(gm.GM_OPT_BIN_SMALL, small)
         g.set_option(gm.GM_OPT_BIN_LARGE, large)
         assert _relerr(_pr(gm, g), ref) <= TOL

@@ -66,6 +66,7 @@ def test_bin_thresholds_do_not_change_results(gm):
     src = synth.pick_sources(n, s, d, 1, seed=3)
     ref, rit = og.sssp(src)
     for small, large in [(2, 4), (8, 64), (32, 2048), (64, 1 << 20)]:
+        g.set_option(gm.GM_OPT_BIN_LARGE, 1 << 30)
         g.set_option(gm.GM_OPT_BIN_SMALL, small)
         g.set_option(gm.GM_OPT_BIN_LARGE, large)
         for direction in DIRS:
