@@ -35,7 +35,7 @@ gm_status ensure_pinned(gm_graph* g) {
 // SSSP on an unweighted graph relaxes with weight 1.
 gm_status ensure_unit_weights(gm_graph* g) {
     if (g->w.p) return GM_OK;
-    const int64_t m = g->m > 0 ? g->m : 1;
+    const int64_t m = g->m + kEdgePad;
     GM_TRY(dev_alloc(g->w, sizeof(uint32_t) * m, g->stream));
     GM_TRY(dev_alloc(g->cw, sizeof(uint32_t) * m, g->stream));
     fill_u32_k<<<num_sms() * 4, 256, 0, g->stream>>>(as<uint32_t>(g->w), g->m, 1u);

@@ -209,6 +209,27 @@ gm_status build_bins(gm_graph* g) {
     g->in_list_count[1] = hc[1];
     g->in_list_count[2] = hc[1] + hc[2];
     g->in_list_count[3] = hc[1] + hc[2] + hc[3];
+    // Static work items of the pull side for large in-degree vertices: one
+    // (vertex, chunk) pair per kChunk in-edges, so a hub is spread over CTAs.
+    std::vector<int32_t> big(hc[3]);
+    std::vector<int2> items;
+    if (hc[3] > 0) {
+        GM_CUDA_TRY(cudaMemcpyAsync(big.data(), as<int32_t>(g->in_list) + g->in_list_count[2],
+                                    sizeof(int32_t) * hc[3], cudaMemcpyDeviceToHost, s));
+        std::vector<int32_t> indeg((size_t)n);
+        GM_CUDA_TRY(cudaMemcpyAsync(indeg.data(), g->in_deg.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+        GM_CUDA_TRY(cudaStreamSynchronize(s));
+        for (size_t i = 0; i < big.size(); ++i) {
+            const int32_t d = indeg[(size_t)big[i]];
+            for (int32_t c = 0; (int64_t)c * kChunk < d; ++c) items.push_back(make_int2(big[i], c));
+        }
+    }
+    g->n_in_chunks = (int64_t)items.size();
+    GM_TRY(dev_alloc(g->in_chunks, sizeof(int2) * (items.size() + 1), s));
+    if (!items.empty())
+        GM_CUDA_TRY(cudaMemcpyAsync(g->in_chunks.p, items.data(), sizeof(int2) * items.size(),
+                                    cudaMemcpyHostToDevice, s));
+    GM_CUDA_TRY(cudaStreamSynchronize(s));
     return GM_OK;
 }
 
@@ -330,11 +351,11 @@ static gm_status ingest(gm_graph* g, const gm_edge_list* el, uint32_t flags) {
     g->m = mm;
 
     // ---- CSR arrays ----
-    GM_TRY(dev_alloc(g->col, sizeof(int32_t) * (mm > 0 ? mm : 1), s));
+    GM_TRY(dev_alloc(g->col, sizeof(int32_t) * (mm + kEdgePad), s));
     if (mm > 0)
         GM_CUDA_TRY(cudaMemcpyAsync(g->col.p, edst.p, sizeof(int32_t) * mm, cudaMemcpyDeviceToDevice, s));
     if (g->wtype != GM_W_NONE) {
-        GM_TRY(dev_alloc(g->w, sizeof(uint32_t) * (mm > 0 ? mm : 1), s));
+        GM_TRY(dev_alloc(g->w, sizeof(uint32_t) * (mm + kEdgePad), s));
         if (mm > 0) {
             gather_u32<<<blocks_for(mm), 256, 0, s>>>(win, as<uint32_t>(perm), mm, as<uint32_t>(g->w));
             LAUNCH_CHECK();
@@ -343,7 +364,7 @@ static gm_status ingest(gm_graph* g, const gm_edge_list* el, uint32_t flags) {
 
     // ---- CSC by a second sort on (dst, src) ----
     GM_TRY(dev_alloc(g->col_ptr, sizeof(int32_t) * (n + 1), s));
-    GM_TRY(dev_alloc(g->row, sizeof(int32_t) * (mm > 0 ? mm : 1), s));
+    GM_TRY(dev_alloc(g->row, sizeof(int32_t) * (mm + kEdgePad), s));
     GM_TRY(dev_alloc(g->csc_pos, sizeof(uint32_t) * (mm > 0 ? mm : 1), s));
     if (mm > 0) {
         csc_keys<<<blocks_for(mm), 256, 0, s>>>(as<int32_t>(esrc), as<int32_t>(edst), mm, b, as<uint64_t>(keys),
@@ -358,7 +379,7 @@ static gm_status ingest(gm_graph* g, const gm_edge_list* el, uint32_t flags) {
     fill_ptr<<<blocks_for(mm + 1), 256, 0, s>>>(as<int32_t>(esrc), mm, n, as<int32_t>(g->col_ptr));
     LAUNCH_CHECK();
     if (g->wtype != GM_W_NONE) {
-        GM_TRY(dev_alloc(g->cw, sizeof(uint32_t) * (mm > 0 ? mm : 1), s));
+        GM_TRY(dev_alloc(g->cw, sizeof(uint32_t) * (mm + kEdgePad), s));
         if (mm > 0) {
             gather_u32<<<blocks_for(mm), 256, 0, s>>>(as<uint32_t>(g->w), as<uint32_t>(g->csc_pos), mm,
                                                       as<uint32_t>(g->cw));
@@ -521,6 +542,7 @@ void release_graph(gm_graph* g) {
     trav_release(g);
     DevBuf* bufs[] = {&g->row_ptr, &g->col, &g->w, &g->col_ptr, &g->row, &g->cw, &g->csc_pos,
                       &g->out_deg, &g->in_deg, &g->out_bin, &g->in_bin, &g->in_list, &g->zero_in_list,
+                      &g->in_chunks,
                       &g->state, &g->work, &g->ctl_buf};
     for (DevBuf* b : bufs) dev_free(*b, s);
     if (g->host_pinned) cudaFreeHost(g->host_pinned);

@@ -15,6 +15,9 @@ namespace gm {
 
 constexpr uint32_t kInf = 0xFFFFFFFFu;  // "infinite" BFS depth / SSSP distance
 constexpr int kNumBins = 3;             // degree bins: small (warp-cooperative), medium (warp), large (CTA)
+constexpr int kEdgePad = 16;            // per-edge arrays carry this many spare entries, so 16-byte
+                                        // vector loads that start inside a row never leave the buffer
+constexpr int kChunk = 2048;            // edges of one large-vertex work item (256 threads x 8 edges)
 
 // Library-wide count of kernel launches issued (a graph replay counts each
 // kernel node it runs).
@@ -121,6 +124,8 @@ struct gm_graph {
     gm::DevBuf out_bin, in_bin;      // uint8 bin of each vertex by out/in degree (0 = degree zero)
     gm::DevBuf in_list;              // vertex ids with in_deg > 0, grouped by in-degree bin
     int64_t in_list_count[gm::kNumBins + 1] = {0};  // offsets of bins 1..3 inside in_list
+    gm::DevBuf in_chunks;            // int2 (vertex, chunk) items covering the in-edges of large-bin vertices
+    int64_t n_in_chunks = 0;
     gm::DevBuf zero_in_list;         // vertex ids with in_deg == 0
     int64_t zero_in_count = 0;
     gm::Tuning tune;

@@ -4,23 +4,26 @@
 //   relax     the generalized SPMV with Process_Message/Reduce fused into the
 //             update of the vertex property (Apply = min), either
 //               push: over the out-edges (CSR) of the compacted frontier queue,
-//                     atomicMin / atomicCAS on the destination, or
-//               pull: over the in-edges (CSC) of every candidate vertex, testing
-//                     the frontier bitvector (Section 4.3.2: the bitvector form
-//                     of the sparse vector), no atomics on the property;
-//             vertices whose property changed are written to the next frontier
-//             (bitvector bit + queue entry, warp-aggregated) -- Algorithm 2's
-//             "mark changed vertices active" without a separate scan.
-//   finalize  SSSP: snapshot the messages (property values) of the next frontier;
-//             the last CTA to finish counts the active vertices, stops at
-//             convergence or max_iters, and picks push or pull for the next
-//             superstep from the frontier size.
-// Work inside a relax launch is split by degree bin: vertices of small degree
-// are processed 32 to a warp with their edge lists concatenated, medium ones a
-// warp each, large ones a CTA each.
+//                     atomicCAS (BFS) / atomicMin (SSSP) on the destination, or
+//               pull: over the in-edges (CSC) of every candidate vertex; BFS
+//                     tests the frontier bitvector (Section 4.3.2's bitvector
+//                     form of the sparse vector), SSSP gathers the message array
+//                     (infinity off the frontier), the owner applies min;
+//             vertices whose property changed join the next frontier (bitvector
+//             bit + binned queue, warp-aggregated) -- Algorithm 2's "mark changed
+//             vertices active" without a separate scan of the active array.
+//   finalize  SSSP: writes the messages of the next frontier; the last CTA to
+//             finish counts the active vertices, stops at convergence or
+//             max_iters, and picks push or pull for the next superstep.
+//
+// Work decomposition for HBM bandwidth: every lane handles 8 edges per step with
+// two 16-byte streaming loads per edge array, so each warp keeps 1-2 KB of edge
+// data in flight.  Vertices of small degree go 32 to a warp with their edge lists
+// concatenated, medium ones a warp each, large ones as 2048-edge chunks, one CTA
+// per chunk, combined with atomics.
 //
 // BSP semantics are exact: messages come from values fixed at the start of the
-// superstep (BFS: the constant t+1; SSSP: the snapshot `msg`), so the property
+// superstep (BFS: the constant t+1; SSSP: the message array), so the property
 // after each superstep and the superstep count equal Algorithm 2's.
 #include "gm_internal.cuh"
 
@@ -29,7 +32,12 @@ namespace gm {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kEPT = 8;                    // edges per lane per step
+constexpr int kWarpSpan = 32 * kEPT;       // 256 edges per warp step
+constexpr int kCtaSpan = kThreads * kEPT;  // 2048 edges per CTA step (== kChunk)
 constexpr uint32_t kFull = 0xffffffffu;
+static_assert(kCtaSpan == kChunk, "a large-vertex chunk is one CTA step");
 
 struct TravCtlDev {
     TravCtl c;
@@ -42,29 +50,31 @@ struct TravArgs {
     const int32_t* row_ptr; const int32_t* col; const uint32_t* w;
     const int32_t* col_ptr; const int32_t* row; const uint32_t* cw;
     const int32_t* out_deg; const int32_t* in_deg; const uint8_t* out_bin;
-    const int32_t* in_list; int64_t in_off[4];
+    const int32_t* in_list; int64_t in_s0, in_s1, in_m1;  // small bin [in_s0, in_s1), medium [in_s1, in_m1)
+    const int2* in_chunks; int64_t n_in_chunks;          // large in-degree vertices as (vertex, chunk)
     int64_t n, m, nwords;
-    uint32_t* dist; uint32_t* msg;
-    uint32_t* bv[3];
-    int32_t* q[3][4];        // [slot][bin], bin 1..3 used
+    uint32_t* dist;
+    uint32_t* msg[2];        // SSSP messages of superstep t live in msg[t & 1], infinity elsewhere
+    uint32_t* bv[3];         // frontier bitvectors, rotating by superstep
+    int32_t* q[3][3];        // [slot][bin], bins 1 (small) and 2 (medium)
+    int2* qc[3];             // [slot] large-bin work items (vertex, chunk)
     TravCtlDev* ctl;
     cudaGraphConditionalHandle cond;
     int use_cond;
 };
 
+// Per-thread statistics, flushed once per kernel.
+struct Acc {
+    unsigned long long scanned, verts, medges, unvis;
+};
+
 __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) {
-    uint32_t s = a + b;
+    const uint32_t s = a + b;
     return (s < a || s == kInf) ? kInf : s;
 }
 
 __device__ __forceinline__ bool test_bit(const uint32_t* bv, int32_t v) {
     return (__ldg(bv + (v >> 5)) >> (v & 31)) & 1u;
-}
-
-__device__ __forceinline__ uint32_t lanemask_lt() {
-    uint32_t m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
 }
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
@@ -83,297 +93,430 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(kFull, v, o);
+        const uint32_t y = __shfl_up_sync(kFull, v, o);
         if (lane >= o) v += y;
     }
     return v;
 }
 
-// Append the vertices with want == true (one per lane) to the next frontier of
-// slot `nxt`, grouped by out-degree bin.  Must be called by all 32 lanes.
+// 8 consecutive 4-byte values at p[e0..e0+7]; e0 % 4 == 0, streaming (evict-first).
+template <typename T>
+__device__ __forceinline__ void load8(const T* p, int32_t e0, T (&x)[kEPT]) {
+    const int4 lo = __ldcs(reinterpret_cast<const int4*>(p + e0));
+    const int4 hi = __ldcs(reinterpret_cast<const int4*>(p + e0 + 4));
+    x[0] = (T)lo.x; x[1] = (T)lo.y; x[2] = (T)lo.z; x[3] = (T)lo.w;
+    x[4] = (T)hi.x; x[5] = (T)hi.y; x[6] = (T)hi.z; x[7] = (T)hi.w;
+}
+
+// Append the vertices v[k] with want[k] to the next frontier of slot `nxt`,
+// grouped by out-degree bin (large vertices as one item per chunk).  Warp-collective.
 template <bool BFS>
-__device__ __forceinline__ void warp_enqueue(const TravArgs& a, bool want, int32_t v, int nxt) {
-    const uint32_t any = __ballot_sync(kFull, want);
-    if (!any) return;
+__device__ __forceinline__ void enqueue_batch(const TravArgs& a, const bool (&want)[kEPT], const int32_t (&v)[kEPT],
+                                              int nxt, Acc& acc) {
+    bool mine = false;
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) mine |= want[k];
+    if (!__any_sync(kFull, mine)) return;
     const int lane = threadIdx.x & 31;
-    uint32_t bin = 0, deg = 0, indeg = 0;
-    if (want) {
-        bin = a.out_bin[v];
-        deg = (uint32_t)a.out_deg[v];
-        if (BFS) indeg = (uint32_t)a.in_deg[v];
+    uint32_t cnt[4] = {0u, 0u, 0u, 0u};
+    uint32_t bin[kEPT], nch[kEPT];
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) {
+        bin[k] = 0u;
+        nch[k] = 0u;
+        if (want[k]) {
+            const uint32_t b = a.out_bin[v[k]];
+            const uint32_t d = (uint32_t)a.out_deg[v[k]];
+            acc.medges += d;
+            if (BFS) acc.unvis += (uint32_t)a.in_deg[v[k]];
+            bin[k] = b;
+            nch[k] = b == 3u ? (d + kChunk - 1u) / kChunk : 1u;
+            cnt[b] += nch[k];
+        }
     }
-    unsigned long long ds = warp_sum_u64(deg);
-    unsigned long long is = BFS ? warp_sum_u64(indeg) : 0ull;
     TravCtl* c = &a.ctl->c;
-    if (lane == 0) {
-        if (ds) atomicAdd(&c->medges[nxt], ds);
-        if (BFS && is) atomicAdd(&c->unvisited_in_edges, 0ull - is);
-    }
-    const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (uint32_t b = 0; b < 4; ++b) {
-        const uint32_t mb = __ballot_sync(kFull, want && bin == b);
-        if (!mb) continue;
-        const int leader = __ffs(mb) - 1;
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(&c->count[nxt][b], (uint32_t)__popc(mb));
-        base = __shfl_sync(kFull, base, leader);
-        if (b > 0 && want && bin == b) a.q[nxt][b][base + __popc(mb & lt)] = v;
+        const uint32_t incl = warp_incl_scan(cnt[b]);
+        const uint32_t tot = __shfl_sync(kFull, incl, 31);
+        if (tot == 0u) continue;
+        uint32_t base = 0u;
+        if (lane == 31) base = atomicAdd(&c->count[nxt][b], tot);
+        base = __shfl_sync(kFull, base, 31);
+        if (b == 0u) continue;  // no out-edges: counted as active, never pushed from
+        uint32_t pos = base + incl - cnt[b];
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) {
+            if (!want[k] || bin[k] != b) continue;
+            if (b < 3u) {
+                a.q[nxt][b][pos++] = v[k];
+            } else {
+                for (uint32_t ch = 0; ch < nch[k]; ++ch) a.qc[nxt][pos++] = make_int2(v[k], (int32_t)ch);
+            }
+        }
     }
 }
 
-// Push-side relaxation of edge (u -> v) with message du (SSSP) / t+1 (BFS).
-// Returns true for the single caller that must enqueue v.
+// Push relaxation of up to 8 edges (u -> v[k]) with messages du[k]; `ok` masks
+// valid edges.  Atomics are issued in phases so a lane keeps several in flight.
 template <bool SSSP>
-__device__ __forceinline__ bool push_edge(const TravArgs& a, int32_t v, uint32_t du, uint32_t wgt, uint32_t t,
-                                          int nxt) {
+__device__ __forceinline__ void push_relax8(const TravArgs& a, const int32_t (&v)[kEPT], const uint32_t (&wt)[kEPT],
+                                            const uint32_t (&du)[kEPT], uint32_t ok, uint32_t t, int nxt,
+                                            bool (&want)[kEPT]) {
+    uint32_t curd[kEPT];
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) curd[k] = ((ok >> k) & 1u) ? a.dist[v[k]] : 0u;
     if (!SSSP) {
-        if (a.dist[v] != kInf) return false;
-        if (atomicCAS(&a.dist[v], kInf, t + 1) != kInf) return false;
-        atomicOr(&a.bv[nxt][v >> 5], 1u << (v & 31));
-        return true;
+        uint32_t old[kEPT];
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k)
+            old[k] = (((ok >> k) & 1u) && curd[k] == kInf) ? atomicCAS(&a.dist[v[k]], kInf, t + 1u) : 0u;
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) {
+            want[k] = ((ok >> k) & 1u) && curd[k] == kInf && old[k] == kInf;
+            if (want[k]) atomicOr(&a.bv[nxt][v[k] >> 5], 1u << (v[k] & 31));
+        }
     } else {
-        const uint32_t nd = sat_add(du, wgt);
-        if (nd >= a.dist[v]) return false;
-        const uint32_t old = atomicMin(&a.dist[v], nd);
-        if (nd >= old) return false;
-        const uint32_t bit = 1u << (v & 31);
-        return (atomicOr(&a.bv[nxt][v >> 5], bit) & bit) == 0;
+        uint32_t nd[kEPT], old[kEPT];
+        bool tr[kEPT];
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) {
+            nd[k] = sat_add(du[k], wt[k]);
+            tr[k] = ((ok >> k) & 1u) && nd[k] < curd[k];
+        }
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) old[k] = tr[k] ? atomicMin(&a.dist[v[k]], nd[k]) : 0u;
+        uint32_t prev[kEPT];
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) {
+            tr[k] = tr[k] && nd[k] < old[k];
+            prev[k] = tr[k] ? atomicOr(&a.bv[nxt][v[k] >> 5], 1u << (v[k] & 31)) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) want[k] = tr[k] && !((prev[k] >> (v[k] & 31)) & 1u);
     }
+}
+
+// Lane step over a contiguous edge range: edges e0..e0+7 masked to [beg, end).
+template <bool SSSP>
+__device__ __forceinline__ void push_contig(const TravArgs& a, int32_t e0, int32_t beg, int32_t end, uint32_t du,
+                                            uint32_t t, int nxt, Acc& acc) {
+    int32_t v[kEPT];
+    uint32_t wt[kEPT], dv[kEPT];
+    uint32_t ok = 0u;
+    if (e0 < end) {
+        load8(a.col, e0, v);
+        if (SSSP) load8(a.w, e0, wt);
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k)
+            if (e0 + k >= beg && e0 + k < end) ok |= 1u << k;
+    }
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) {
+        if (!((ok >> k) & 1u)) { v[k] = 0; wt[k] = 0u; }
+        if (!SSSP) wt[k] = 0u;
+        dv[k] = du;
+    }
+    bool want[kEPT];
+    push_relax8<SSSP>(a, v, wt, dv, ok, t, nxt, want);
+    acc.scanned += (unsigned)__popc(ok);
+    enqueue_batch<!SSSP>(a, want, v, nxt, acc);
+}
+
+// Largest o in [0, 31] with ex[o] <= j (ex non-decreasing, 33 entries).
+__device__ __forceinline__ int owner_of(const uint32_t* ex, uint32_t j) {
+    int o = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1)
+        if (ex[o + step] <= j) o += step;
+    return o;
 }
 
 // ---------------------------------------------------------------- push
 template <bool SSSP>
-__device__ void push_phase(const TravArgs& a, uint32_t t, int cur, int nxt, unsigned long long& scanned, unsigned long long& vcount) {
+__device__ void push_phase(const TravArgs& a, uint32_t t, int cur, int nxt, Acc& acc, uint32_t* sw) {
     const TravCtl* c = &a.ctl->c;
-    const uint32_t nS = c->count[cur][1], nM = c->count[cur][2], nL = c->count[cur][3];
+    const uint32_t nS = c->count[cur][1], nM = c->count[cur][2], nC = c->count[cur][3];
+    const uint32_t* __restrict__ msgc = a.msg[t & 1u];
     const int lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * kThreads + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * kThreads) >> 5;
 
-    // large: one CTA per vertex
-    for (uint32_t i = blockIdx.x; i < nL; i += gridDim.x) {
-        const int32_t u = a.q[cur][3][i];
-        if (threadIdx.x == 0) ++vcount;
-        const uint32_t du = SSSP ? a.msg[u] : 0u;
-        const int32_t beg = a.row_ptr[u], end = a.row_ptr[u + 1];
-        for (int32_t base = beg; base < end; base += kThreads) {
-            const int32_t e = base + threadIdx.x;
-            bool want = false;
-            int32_t v = 0;
-            if (e < end) {
-                v = a.col[e];
-                want = push_edge<SSSP>(a, v, du, SSSP ? a.w[e] : 0u, t, nxt);
-                ++scanned;
-            }
-            warp_enqueue<!SSSP>(a, want, v, nxt);
-        }
+    // large: one CTA per 2048-edge chunk
+    for (uint32_t i = blockIdx.x; i < nC; i += gridDim.x) {
+        const int2 it = a.qc[cur][i];
+        const int32_t u = it.x;
+        if (threadIdx.x == 0 && it.y == 0) acc.verts++;
+        const int32_t re = a.row_ptr[u + 1];
+        const int32_t beg = a.row_ptr[u] + it.y * kChunk;
+        const int32_t end = min(re, beg + kChunk);
+        const uint32_t du = SSSP ? msgc[u] : 0u;
+        for (int32_t base = beg & ~3; base < end; base += kCtaSpan)
+            push_contig<SSSP>(a, base + (int32_t)threadIdx.x * kEPT, beg, end, du, t, nxt, acc);
     }
     // medium: one warp per vertex
     for (uint32_t i = gwarp; i < nM; i += nwarps) {
         const int32_t u = a.q[cur][2][i];
-        if (lane == 0) ++vcount;
-        const uint32_t du = SSSP ? a.msg[u] : 0u;
+        if (lane == 0) acc.verts++;
         const int32_t beg = a.row_ptr[u], end = a.row_ptr[u + 1];
-        for (int32_t base = beg; base < end; base += 32) {
-            const int32_t e = base + lane;
-            bool want = false;
-            int32_t v = 0;
-            if (e < end) {
-                v = a.col[e];
-                want = push_edge<SSSP>(a, v, du, SSSP ? a.w[e] : 0u, t, nxt);
-                ++scanned;
-            }
-            warp_enqueue<!SSSP>(a, want, v, nxt);
-        }
+        const uint32_t du = SSSP ? msgc[u] : 0u;
+        for (int32_t base = beg & ~3; base < end; base += kWarpSpan)
+            push_contig<SSSP>(a, base + lane * kEPT, beg, end, du, t, nxt, acc);
     }
     // small: 32 vertices per warp, edge lists concatenated
+    int32_t* s_beg = reinterpret_cast<int32_t*>(sw);
+    uint32_t* s_ex = sw + 32;  // 33 entries
+    uint32_t* s_du = sw + 65;
     for (uint32_t grp = gwarp; grp * 32u < nS; grp += nwarps) {
         const uint32_t i = grp * 32u + lane;
         int32_t beg = 0;
-        uint32_t deg = 0, du = 0;
+        uint32_t deg = 0u, du = 0u;
         if (i < nS) {
             const int32_t u = a.q[cur][1][i];
-            ++vcount;
+            acc.verts++;
             beg = a.row_ptr[u];
             deg = (uint32_t)(a.row_ptr[u + 1] - beg);
-            du = SSSP ? a.msg[u] : 0u;
+            du = SSSP ? msgc[u] : 0u;
         }
         const uint32_t incl = warp_incl_scan(deg);
-        const uint32_t excl = incl - deg;
-        const uint32_t total = __shfl_sync(kFull, incl, 31);
-        for (uint32_t base = 0; base < total; base += 32) {
-            const uint32_t j = base + lane;
-            int k = 0;
+        __syncwarp();
+        s_beg[lane] = beg;
+        s_ex[lane] = incl - deg;
+        s_du[lane] = du;
+        if (lane == 31) s_ex[32] = incl;
+        __syncwarp();
+        const uint32_t total = s_ex[32];
+        for (uint32_t base = 0; base < total; base += kWarpSpan) {
+            const uint32_t j0 = base + (uint32_t)lane * kEPT;
+            int o = owner_of(s_ex, j0);
+            int32_t v[kEPT];
+            uint32_t wt[kEPT], dv[kEPT];
+            uint32_t ok = 0u;
 #pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const uint32_t ex = __shfl_sync(kFull, excl, k + step);
-                if (ex <= j) k += step;
+            for (int k = 0; k < kEPT; ++k) {
+                const uint32_t j = j0 + k;
+                v[k] = 0;
+                wt[k] = 0u;
+                dv[k] = 0u;
+                if (j < total) {
+                    while (j >= s_ex[o + 1]) ++o;
+                    const int32_t e = s_beg[o] + (int32_t)(j - s_ex[o]);
+                    v[k] = a.col[e];
+                    if (SSSP) wt[k] = a.w[e];
+                    dv[k] = s_du[o];
+                    ok |= 1u << k;
+                }
             }
-            const int32_t bo = __shfl_sync(kFull, beg, k);
-            const uint32_t eo = __shfl_sync(kFull, excl, k);
-            const uint32_t duo = __shfl_sync(kFull, du, k);
-            bool want = false;
-            int32_t v = 0;
-            if (j < total) {
-                const int32_t e = bo + (int32_t)(j - eo);
-                v = a.col[e];
-                want = push_edge<SSSP>(a, v, duo, SSSP ? a.w[e] : 0u, t, nxt);
-                ++scanned;
-            }
-            warp_enqueue<!SSSP>(a, want, v, nxt);
+            bool want[kEPT];
+            push_relax8<SSSP>(a, v, wt, dv, ok, t, nxt, want);
+            acc.scanned += (unsigned)__popc(ok);
+            enqueue_batch<!SSSP>(a, want, v, nxt, acc);
         }
     }
 }
 
 // ---------------------------------------------------------------- pull
-// BFS: an unvisited vertex takes depth t+1 at its first in-neighbour in the
-// frontier (early exit).  SSSP: min over in-neighbours in the frontier of
-// msg[u] + w(u, v), applied with min.
+// Lane step over in-edges e0..e0+7 masked to [beg, end): BFS sets `hit` if an
+// in-neighbour is in the frontier; SSSP lowers `best` by msg[u] + w(u, v).
 template <bool SSSP>
-__device__ void pull_phase(const TravArgs& a, uint32_t t, int cur, int nxt, unsigned long long& scanned, unsigned long long& vcount) {
+__device__ __forceinline__ void pull_contig(const TravArgs& a, int32_t e0, int32_t beg, int32_t end,
+                                            const uint32_t* __restrict__ bvc, const uint32_t* __restrict__ msgc,
+                                            uint32_t& best, bool& hit, Acc& acc) {
+    if (e0 >= end) return;
+    int32_t u[kEPT];
+    uint32_t wt[kEPT];
+    load8(a.row, e0, u);
+    if (SSSP) load8(a.cw, e0, wt);
+    uint32_t ok = 0u;
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k)
+        if (e0 + k >= beg && e0 + k < end) ok |= 1u << k;
+    acc.scanned += (unsigned)__popc(ok);
+    if (SSSP) {
+        uint32_t mu[kEPT];
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) mu[k] = ((ok >> k) & 1u) ? __ldg(msgc + u[k]) : kInf;
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) best = min(best, sat_add(mu[k], wt[k]));
+    } else {
+        bool h[kEPT];
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) h[k] = ((ok >> k) & 1u) && test_bit(bvc, u[k]);
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) hit |= h[k];
+    }
+}
+
+template <bool SSSP>
+__device__ void pull_phase(const TravArgs& a, uint32_t t, int cur, int nxt, Acc& acc, uint32_t* sw,
+                           uint32_t* s_red) {
     const int lane = threadIdx.x & 31;
-    const int warp_in_cta = threadIdx.x >> 5;
+    const int wid = threadIdx.x >> 5;
     const uint32_t gwarp = (blockIdx.x * kThreads + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * kThreads) >> 5;
     const uint32_t* __restrict__ bvc = a.bv[cur];
-    __shared__ uint32_t s_red[kThreads / 32];
-    __shared__ uint32_t s_slot[kThreads / 32][32];
+    const uint32_t* __restrict__ msgc = a.msg[t & 1u];
 
-    // large: one CTA per vertex
-    {
-        const int64_t lo = a.in_off[2], hi = a.in_off[3];
-        for (int64_t i = lo + blockIdx.x; i < hi; i += gridDim.x) {
-            const int32_t v = a.in_list[i];
-            if (!SSSP && a.dist[v] != kInf) continue;  // uniform over the CTA
-            if (threadIdx.x == 0) ++vcount;
-            const int32_t beg = a.col_ptr[v], end = a.col_ptr[v + 1];
-            uint32_t best = kInf;
-            for (int32_t base = beg; base < end; base += kThreads) {
-                const int32_t e = base + threadIdx.x;
-                bool hit = false;
-                if (e < end) {
-                    const int32_t u = a.row[e];
-                    ++scanned;
-                    if (test_bit(bvc, u)) {
-                        hit = true;
-                        if (SSSP) best = min(best, sat_add(a.msg[u], a.cw[e]));
-                    }
-                }
-                if (!SSSP) {
-                    if (__syncthreads_or(hit)) { best = t + 1; break; }
-                }
-            }
-            if (SSSP) {
-                best = warp_min_u32(best);
-                if (lane == 0) s_red[warp_in_cta] = best;
-                __syncthreads();
-                if (warp_in_cta == 0) {
-                    uint32_t b2 = lane < kThreads / 32 ? s_red[lane] : kInf;
-                    best = warp_min_u32(b2);
-                }
-                __syncthreads();
-            }
-            if (warp_in_cta == 0) {
-                bool want = false;
-                if (lane == 0) {
-                    if (best < a.dist[v]) {
-                        a.dist[v] = best;
-                        atomicOr(&a.bv[nxt][v >> 5], 1u << (v & 31));
-                        want = true;
-                    }
-                }
-                warp_enqueue<!SSSP>(a, want, v, nxt);
-            }
+    // large in-degree: one CTA per 2048-edge chunk, combined through atomics
+    __shared__ uint32_t s_skip;
+    for (int64_t i = blockIdx.x; i < a.n_in_chunks; i += gridDim.x) {
+        const int2 it = a.in_chunks[i];
+        const int32_t v = it.x;
+        // Another CTA's chunk of v may claim it meanwhile, so one thread decides
+        // for the whole CTA (the decision must be uniform for the barriers below).
+        if (threadIdx.x == 0) s_skip = (!SSSP && a.dist[v] != kInf) ? 1u : 0u;
+        __syncthreads();
+        if (s_skip) {
             __syncthreads();
+            continue;
         }
-    }
-    // medium: one warp per vertex
-    {
-        const int64_t lo = a.in_off[1], hi = a.in_off[2];
-        for (int64_t i = lo + gwarp; i < hi; i += nwarps) {
-            const int32_t v = a.in_list[i];
-            if (!SSSP && a.dist[v] != kInf) continue;  // uniform over the warp
-            if (lane == 0) ++vcount;
-            const int32_t beg = a.col_ptr[v], end = a.col_ptr[v + 1];
-            uint32_t best = kInf;
-            for (int32_t base = beg; base < end; base += 32) {
-                const int32_t e = base + lane;
-                bool hit = false;
-                if (e < end) {
-                    const int32_t u = a.row[e];
-                    ++scanned;
-                    if (test_bit(bvc, u)) {
-                        hit = true;
-                        if (SSSP) best = min(best, sat_add(a.msg[u], a.cw[e]));
+        if (threadIdx.x == 0 && it.y == 0) acc.verts++;
+        const int32_t ce = a.col_ptr[v + 1];
+        const int32_t beg = a.col_ptr[v] + it.y * kChunk;
+        const int32_t end = min(ce, beg + kChunk);
+        uint32_t best = kInf;
+        bool hit = false;
+        for (int32_t base = beg & ~3; base < end; base += kCtaSpan) {
+            pull_contig<SSSP>(a, base + (int32_t)threadIdx.x * kEPT, beg, end, bvc, msgc, best, hit, acc);
+            if (!SSSP) {
+                if (__syncthreads_or(hit)) { hit = true; break; }
+            }
+        }
+        bool want = false;
+        if (SSSP) {
+            best = warp_min_u32(best);
+            if (lane == 0) s_red[wid] = best;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                best = kInf;
+                for (int w2 = 0; w2 < kWarps; ++w2) best = min(best, s_red[w2]);
+                if (best < a.dist[v]) {
+                    const uint32_t old = atomicMin(&a.dist[v], best);
+                    if (best < old) {
+                        const uint32_t bit = 1u << (v & 31);
+                        want = (atomicOr(&a.bv[nxt][v >> 5], bit) & bit) == 0u;
                     }
                 }
-                if (!SSSP && __any_sync(kFull, hit)) { best = t + 1; break; }
             }
-            if (SSSP) best = warp_min_u32(best);
-            bool want = false;
-            if (lane == 0 && best < a.dist[v]) {
-                a.dist[v] = best;
+        } else if (threadIdx.x == 0 && hit) {
+            if (atomicCAS(&a.dist[v], kInf, t + 1u) == kInf) {
                 atomicOr(&a.bv[nxt][v >> 5], 1u << (v & 31));
                 want = true;
             }
-            warp_enqueue<!SSSP>(a, want, v, nxt);
         }
+        if (wid == 0) {
+            bool wa[kEPT] = {want, false, false, false, false, false, false, false};
+            int32_t va[kEPT] = {v, 0, 0, 0, 0, 0, 0, 0};
+            enqueue_batch<!SSSP>(a, wa, va, nxt, acc);
+        }
+        __syncthreads();
     }
-    // small: 32 vertices per warp, in-edge lists concatenated
-    {
-        const int64_t lo = a.in_off[0], hi = a.in_off[1];
-        uint32_t* slot = s_slot[warp_in_cta];
-        for (int64_t g0 = lo + (int64_t)gwarp * 32; g0 < hi; g0 += (int64_t)nwarps * 32) {
-            const int64_t i = g0 + lane;
-            int32_t v = 0, beg = 0;
-            uint32_t deg = 0;
-            if (i < hi) {
-                v = a.in_list[i];
-                if (SSSP || a.dist[v] == kInf) {
-                    ++vcount;
-                    beg = a.col_ptr[v];
-                    deg = (uint32_t)(a.col_ptr[v + 1] - beg);
-                }
-            }
-            slot[lane] = kInf;
-            __syncwarp();
-            const uint32_t incl = warp_incl_scan(deg);
-            const uint32_t excl = incl - deg;
-            const uint32_t total = __shfl_sync(kFull, incl, 31);
-            for (uint32_t base = 0; base < total; base += 32) {
-                const uint32_t j = base + lane;
-                int k = 0;
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const uint32_t ex = __shfl_sync(kFull, excl, k + step);
-                    if (ex <= j) k += step;
-                }
-                const int32_t bo = __shfl_sync(kFull, beg, k);
-                const uint32_t eo = __shfl_sync(kFull, excl, k);
-                if (j < total) {
-                    const int32_t e = bo + (int32_t)(j - eo);
-                    const int32_t u = a.row[e];
-                    ++scanned;
-                    if (test_bit(bvc, u)) {
-                        if (SSSP) atomicMin(&slot[k], sat_add(a.msg[u], a.cw[e]));
-                        else slot[k] = t + 1;
-                    }
-                }
-            }
-            __syncwarp();
-            bool want = false;
-            if (i < hi && deg > 0) {
-                const uint32_t best = slot[lane];
-                if (best < a.dist[v]) {
-                    a.dist[v] = best;
-                    atomicOr(&a.bv[nxt][v >> 5], 1u << (v & 31));
-                    want = true;
-                }
-            }
-            warp_enqueue<!SSSP>(a, want, v, nxt);
-            __syncwarp();
+    // medium: one warp per vertex, the warp owns the vertex
+    for (int64_t i = a.in_s1 + gwarp; i < a.in_m1; i += nwarps) {
+        const int32_t v = a.in_list[i];
+        if (!SSSP && a.dist[v] != kInf) continue;  // uniform over the warp
+        if (lane == 0) acc.verts++;
+        const int32_t beg = a.col_ptr[v], end = a.col_ptr[v + 1];
+        uint32_t best = kInf;
+        bool hit = false;
+        for (int32_t base = beg & ~3; base < end; base += kWarpSpan) {
+            pull_contig<SSSP>(a, base + lane * kEPT, beg, end, bvc, msgc, best, hit, acc);
+            if (!SSSP && __any_sync(kFull, hit)) { hit = true; break; }
         }
+        if (SSSP) best = warp_min_u32(best);
+        bool want = false;
+        if (lane == 0) {
+            const uint32_t nv = SSSP ? best : (hit ? t + 1u : kInf);
+            if (nv < a.dist[v]) {
+                a.dist[v] = nv;
+                atomicOr(&a.bv[nxt][v >> 5], 1u << (v & 31));
+                want = true;
+            }
+        }
+        bool wa[kEPT] = {want, false, false, false, false, false, false, false};
+        int32_t va[kEPT] = {v, 0, 0, 0, 0, 0, 0, 0};
+        enqueue_batch<!SSSP>(a, wa, va, nxt, acc);
+    }
+    // small: 32 vertices per warp, in-edge lists concatenated, per-owner min in shared memory
+    int32_t* s_beg = reinterpret_cast<int32_t*>(sw);
+    uint32_t* s_ex = sw + 32;  // 33 entries
+    uint32_t* s_best = sw + 65;
+    for (int64_t g0 = a.in_s0 + (int64_t)gwarp * 32; g0 < a.in_s1; g0 += (int64_t)nwarps * 32) {
+        const int64_t i = g0 + lane;
+        int32_t v = 0, beg = 0;
+        uint32_t deg = 0u;
+        if (i < a.in_s1) {
+            v = a.in_list[i];
+            if (SSSP || a.dist[v] == kInf) {
+                acc.verts++;
+                beg = a.col_ptr[v];
+                deg = (uint32_t)(a.col_ptr[v + 1] - beg);
+            }
+        }
+        const uint32_t incl = warp_incl_scan(deg);
+        __syncwarp();
+        s_beg[lane] = beg;
+        s_ex[lane] = incl - deg;
+        s_best[lane] = kInf;
+        if (lane == 31) s_ex[32] = incl;
+        __syncwarp();
+        const uint32_t total = s_ex[32];
+        for (uint32_t base = 0; base < total; base += kWarpSpan) {
+            const uint32_t j0 = base + (uint32_t)lane * kEPT;
+            int o = owner_of(s_ex, j0);
+            int32_t u[kEPT];
+            uint32_t wt[kEPT];
+            int own[kEPT];
+            uint32_t ok = 0u;
+#pragma unroll
+            for (int k = 0; k < kEPT; ++k) {
+                const uint32_t j = j0 + k;
+                u[k] = 0;
+                wt[k] = 0u;
+                own[k] = o;
+                if (j < total) {
+                    while (j >= s_ex[o + 1]) ++o;
+                    const int32_t e = s_beg[o] + (int32_t)(j - s_ex[o]);
+                    u[k] = a.row[e];
+                    if (SSSP) wt[k] = a.cw[e];
+                    own[k] = o;
+                    ok |= 1u << k;
+                }
+            }
+            acc.scanned += (unsigned)__popc(ok);
+            uint32_t cand[kEPT];
+#pragma unroll
+            for (int k = 0; k < kEPT; ++k) {
+                if (SSSP) cand[k] = ((ok >> k) & 1u) ? sat_add(__ldg(msgc + u[k]), wt[k]) : kInf;
+                else cand[k] = (((ok >> k) & 1u) && test_bit(bvc, u[k])) ? t + 1u : kInf;
+            }
+            // lane-local runs of one owner, then one shared-memory atomic per run
+            uint32_t run = kInf;
+            int ro = own[0];
+#pragma unroll
+            for (int k = 0; k < kEPT; ++k) {
+                if (own[k] != ro) {
+                    if (run != kInf) atomicMin(&s_best[ro], run);
+                    run = kInf;
+                    ro = own[k];
+                }
+                run = min(run, cand[k]);
+            }
+            if (run != kInf) atomicMin(&s_best[ro], run);
+        }
+        __syncwarp();
+        bool want = false;
+        if (i < a.in_s1 && deg > 0u) {
+            const uint32_t b = s_best[lane];
+            if (b < a.dist[v]) {
+                a.dist[v] = b;
+                atomicOr(&a.bv[nxt][v >> 5], 1u << (v & 31));
+                want = true;
+            }
+        }
+        bool wa[kEPT] = {want, false, false, false, false, false, false, false};
+        int32_t va[kEPT] = {v, 0, 0, 0, 0, 0, 0, 0};
+        enqueue_batch<!SSSP>(a, wa, va, nxt, acc);
     }
 }
 
@@ -383,20 +526,39 @@ __global__ void __launch_bounds__(kThreads) trav_relax(TravArgs a) {
     if (cd->c.done) return;
     const uint32_t t = cd->c.iter;
     const int cur = (int)(t % 3u), nxt = (int)((t + 1u) % 3u), clr = (int)((t + 2u) % 3u);
-    {   // clear the bitvector two supersteps back (it becomes "next" in superstep t+1)
+    const int64_t gtid = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t gsize = (int64_t)gridDim.x * kThreads;
+    {   // the frontier two supersteps back: its bitvector becomes "next" in superstep t+1
         uint32_t* bz = a.bv[clr];
-        for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < a.nwords;
-             i += (int64_t)gridDim.x * kThreads)
-            bz[i] = 0u;
+        for (int64_t i = gtid; i < a.nwords; i += gsize) bz[i] = 0u;
+        if (SSSP) {  // and its messages leave msg[(t+1) & 1], which finalize refills
+            const TravCtl* c = &cd->c;
+            const uint32_t n1 = c->count[clr][1], n2 = c->count[clr][2], n3 = c->count[clr][3];
+            uint32_t* mz = a.msg[(t + 1u) & 1u];
+            for (int64_t i = gtid; i < (int64_t)n1 + n2 + n3; i += gsize) {
+                int32_t v;
+                if (i < n1) v = a.q[clr][1][i];
+                else if (i < (int64_t)n1 + n2) v = a.q[clr][2][i - n1];
+                else v = a.qc[clr][i - n1 - n2].x;
+                mz[v] = kInf;
+            }
+        }
     }
-    unsigned long long scanned = 0, vcount = 0;
-    if (cd->c.dir == 0) push_phase<SSSP>(a, t, cur, nxt, scanned, vcount);
-    else pull_phase<SSSP>(a, t, cur, nxt, scanned, vcount);
-    scanned = warp_sum_u64(scanned);
-    vcount = warp_sum_u64(vcount);
+    __shared__ uint32_t s_w[kWarps][100];
+    __shared__ uint32_t s_red[kWarps];
+    Acc acc = {0ull, 0ull, 0ull, 0ull};
+    if (cd->c.dir == 0) push_phase<SSSP>(a, t, cur, nxt, acc, s_w[threadIdx.x >> 5]);
+    else pull_phase<SSSP>(a, t, cur, nxt, acc, s_w[threadIdx.x >> 5], s_red);
+    acc.scanned = warp_sum_u64(acc.scanned);
+    acc.verts = warp_sum_u64(acc.verts);
+    acc.medges = warp_sum_u64(acc.medges);
+    acc.unvis = warp_sum_u64(acc.unvis);
     if ((threadIdx.x & 31) == 0) {
-        if (scanned) atomicAdd(&cd->c.scanned_edges, scanned);
-        if (vcount) atomicAdd(&cd->c.processed_vertices, vcount);
+        TravCtl* c = &cd->c;
+        if (acc.scanned) atomicAdd(&c->scanned_edges, acc.scanned);
+        if (acc.verts) atomicAdd(&c->processed_vertices, acc.verts);
+        if (acc.medges) atomicAdd(&c->medges[nxt], acc.medges);
+        if (!SSSP && acc.unvis) atomicAdd(&c->unvisited_in_edges, 0ull - acc.unvis);
     }
 }
 
@@ -415,15 +577,20 @@ __global__ void __launch_bounds__(kThreads) trav_finalize(TravArgs a) {
     if (s_done) return;
     const uint32_t t = s_t;
     const int nxt = (int)((t + 1u) % 3u);
-    if (SSSP) {  // messages of the next superstep: property values fixed now
+    if (SSSP) {  // messages of superstep t+1: the property values fixed now
         const uint32_t n1 = s_cnt[1], n2 = s_cnt[2], n3 = s_cnt[3];
-        const uint32_t tot = n1 + n2 + n3;
-        for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < tot; i += gridDim.x * kThreads) {
+        uint32_t* ms = a.msg[(t + 1u) & 1u];
+        for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < (int64_t)n1 + n2 + n3;
+             i += (int64_t)gridDim.x * kThreads) {
             int32_t v;
             if (i < n1) v = a.q[nxt][1][i];
-            else if (i < n1 + n2) v = a.q[nxt][2][i - n1];
-            else v = a.q[nxt][3][i - n1 - n2];
-            a.msg[v] = a.dist[v];
+            else if (i < (int64_t)n1 + n2) v = a.q[nxt][2][i - n1];
+            else {
+                const int2 it = a.qc[nxt][i - n1 - n2];
+                if (it.y != 0) continue;
+                v = it.x;
+            }
+            ms[v] = a.dist[v];
         }
     }
     __syncthreads();
@@ -478,14 +645,24 @@ __global__ void seed_frontier(TravArgs a, const int32_t* __restrict__ verts, int
     if (i < count) v = verts[i];
     if (i < count && (v < 0 || v >= a.n)) {
         atomicAdd(&a.ctl->c.bad_ids, 1u);
+        v = 0;
     } else if (i < count) {
         a.dist[v] = 0u;
-        a.msg[v] = 0u;
+        a.msg[0][v] = 0u;
         const uint32_t bit = 1u << (v & 31);
-        want = (atomicOr(&a.bv[0][v >> 5], bit) & bit) == 0;
+        want = (atomicOr(&a.bv[0][v >> 5], bit) & bit) == 0u;
     }
-    if (bfs) warp_enqueue<true>(a, want, v, 0);
-    else warp_enqueue<false>(a, want, v, 0);
+    Acc acc = {0ull, 0ull, 0ull, 0ull};
+    bool wa[kEPT] = {want, false, false, false, false, false, false, false};
+    int32_t va[kEPT] = {v, 0, 0, 0, 0, 0, 0, 0};
+    if (bfs) enqueue_batch<true>(a, wa, va, 0, acc);
+    else enqueue_batch<false>(a, wa, va, 0, acc);
+    acc.medges = warp_sum_u64(acc.medges);
+    acc.unvis = warp_sum_u64(acc.unvis);
+    if ((threadIdx.x & 31) == 0) {
+        if (acc.medges) atomicAdd(&a.ctl->c.medges[0], acc.medges);
+        if (bfs && acc.unvis) atomicAdd(&a.ctl->c.unvisited_in_edges, 0ull - acc.unvis);
+    }
 }
 
 __global__ void seed_all(TravArgs a, int bfs) {
@@ -494,11 +671,20 @@ __global__ void seed_all(TravArgs a, int bfs) {
     const int32_t v = want ? (int32_t)i : 0;
     if (want) {
         a.dist[v] = 0u;
-        a.msg[v] = 0u;
+        a.msg[0][v] = 0u;
         atomicOr(&a.bv[0][v >> 5], 1u << (v & 31));
     }
-    if (bfs) warp_enqueue<true>(a, want, v, 0);
-    else warp_enqueue<false>(a, want, v, 0);
+    Acc acc = {0ull, 0ull, 0ull, 0ull};
+    bool wa[kEPT] = {want, false, false, false, false, false, false, false};
+    int32_t va[kEPT] = {v, 0, 0, 0, 0, 0, 0, 0};
+    if (bfs) enqueue_batch<true>(a, wa, va, 0, acc);
+    else enqueue_batch<false>(a, wa, va, 0, acc);
+    acc.medges = warp_sum_u64(acc.medges);
+    acc.unvis = warp_sum_u64(acc.unvis);
+    if ((threadIdx.x & 31) == 0) {
+        if (acc.medges) atomicAdd(&a.ctl->c.medges[0], acc.medges);
+        if (bfs && acc.unvis) atomicAdd(&a.ctl->c.unvisited_in_edges, 0ull - acc.unvis);
+    }
 }
 
 __global__ void fill_u32(uint32_t* p, int64_t n, uint32_t v) {
@@ -517,35 +703,34 @@ __global__ void reached_kernel(const uint32_t* __restrict__ dist, const int32_t*
 
 // Workspace layout inside g->work for BFS/SSSP.
 struct TravWork {
-    uint32_t* msg;
+    uint32_t* msg[2];
     uint32_t* bv[3];
-    int32_t* q[3][4];
+    int32_t* q[3][3];
+    int2* qc[3];
 };
 
-TravWork work_layout(gm_graph* g) {
+int64_t chunk_capacity(int64_t n, int64_t m) { return n + m / kChunk + 2; }
+
+TravWork work_layout(gm_graph* g, size_t* total_bytes = nullptr) {
     TravWork w{};
     const int64_t n = g->n > 0 ? g->n : 1;
     const int64_t nwords = (n + 31) / 32;
     char* p = static_cast<char*>(g->work.p);
+    size_t off = 0;
     auto take = [&](size_t bytes) {
-        char* r = p;
-        p += (bytes + 255) & ~(size_t)255;
+        char* r = p ? p + off : nullptr;
+        off += (bytes + 255) & ~(size_t)255;
         return r;
     };
-    w.msg = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * n));
+    for (int s = 0; s < 2; ++s) w.msg[s] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * n));
     for (int s = 0; s < 3; ++s) w.bv[s] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * nwords));
     for (int s = 0; s < 3; ++s) {
         w.q[s][0] = nullptr;
-        for (int b = 1; b < 4; ++b) w.q[s][b] = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * n));
+        for (int b = 1; b < 3; ++b) w.q[s][b] = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * n));
+        w.qc[s] = reinterpret_cast<int2*>(take(sizeof(int2) * chunk_capacity(n, g->m)));
     }
+    if (total_bytes) *total_bytes = off;
     return w;
-}
-
-size_t work_bytes(int64_t n) {
-    n = n > 0 ? n : 1;
-    const int64_t nwords = (n + 31) / 32;
-    auto r = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    return r(sizeof(uint32_t) * n) + 3 * r(sizeof(uint32_t) * nwords) + 9 * r(sizeof(int32_t) * n);
 }
 
 TravArgs make_args(gm_graph* g) {
@@ -561,15 +746,20 @@ TravArgs make_args(gm_graph* g) {
     a.in_deg = as<int32_t>(g->in_deg);
     a.out_bin = as<uint8_t>(g->out_bin);
     a.in_list = as<int32_t>(g->in_list);
-    for (int b = 0; b < 4; ++b) a.in_off[b] = g->in_list_count[b];
+    a.in_s0 = g->in_list_count[0];
+    a.in_s1 = g->in_list_count[1];
+    a.in_m1 = g->in_list_count[2];
+    a.in_chunks = as<int2>(g->in_chunks);
+    a.n_in_chunks = g->n_in_chunks;
     a.n = g->n;
     a.m = g->m;
     a.nwords = (g->n + 31) / 32;
     a.dist = as<uint32_t>(g->state);
-    a.msg = w.msg;
+    for (int s = 0; s < 2; ++s) a.msg[s] = w.msg[s];
     for (int s = 0; s < 3; ++s) {
         a.bv[s] = w.bv[s];
-        for (int b = 0; b < 4; ++b) a.q[s][b] = w.q[s][b];
+        for (int b = 0; b < 3; ++b) a.q[s][b] = w.q[s][b];
+        a.qc[s] = w.qc[s];
     }
     a.ctl = as<TravCtlDev>(g->ctl_buf);
     a.use_cond = 0;
@@ -603,8 +793,11 @@ int finalize_grid() { return 2 * num_sms(); }
 gm_status reset_frontier(gm_graph* g) {
     cudaStream_t s = g->stream;
     TravWork w = work_layout(g);
-    const int64_t nwords = ((g->n > 0 ? g->n : 1) + 31) / 32;
+    const int64_t n = g->n > 0 ? g->n : 1;
+    const int64_t nwords = (n + 31) / 32;
     for (int k = 0; k < 3; ++k) GM_CUDA_TRY(cudaMemsetAsync(w.bv[k], 0, sizeof(uint32_t) * nwords, s));
+    if (g->kind == GM_SSSP)
+        for (int k = 0; k < 2; ++k) GM_CUDA_TRY(cudaMemsetAsync(w.msg[k], 0xFF, sizeof(uint32_t) * n, s));
     TravCtlDev h{};
     h.c.dir = g->tune.direction == 2 ? 1u : 0u;
     h.c.unvisited_in_edges = (unsigned long long)g->m;
@@ -686,8 +879,11 @@ gm_status trav_prepare(gm_graph* g) {
     cudaStream_t s = g->stream;
     const int64_t n = g->n > 0 ? g->n : 1;
     GM_TRY(dev_alloc(g->state, sizeof(uint32_t) * n, s));
-    GM_TRY(dev_alloc(g->work, work_bytes(g->n), s));
-    g->work_bytes = (int64_t)work_bytes(g->n);
+    size_t wb = 0;
+    g->work.p = nullptr;
+    work_layout(g, &wb);
+    GM_TRY(dev_alloc(g->work, wb, s));
+    g->work_bytes = (int64_t)wb;
     GM_TRY(dev_alloc(g->ctl_buf, sizeof(TravCtlDev), s));
     fill_u32<<<num_sms() * 4, 256, 0, s>>>(as<uint32_t>(g->state), g->n, kInf);
     g_launches++;
@@ -722,8 +918,7 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
         return reset_frontier(g);
     }
     TravCtlDev* hp = static_cast<TravCtlDev*>(g->host_pinned);
-    // parameters that may change between runs
-    {
+    {   // parameters that may change between runs
         int32_t params[2] = {max_iters, g->tune.direction};
         GM_CUDA_TRY(cudaMemcpyAsync(reinterpret_cast<char*>(g->ctl_buf.p) + offsetof(TravCtlDev, max_iters), params,
                                     sizeof(params), cudaMemcpyHostToDevice, s));
