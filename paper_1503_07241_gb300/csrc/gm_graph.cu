@@ -143,6 +143,26 @@ __global__ void bin_match_flags(const uint8_t* __restrict__ bins, int64_t n, uin
     if (v < n) flags[v] = bins[v] == want ? 1u : 0u;
 }
 
+__global__ void positive_flags(const int32_t* __restrict__ deg, int64_t n, uint32_t* __restrict__ flags) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) flags[v] = deg[v] > 0 ? 1u : 0u;
+}
+
+__global__ void dcsc_cp_kernel(const int32_t* __restrict__ jc, int64_t ncols, const int32_t* __restrict__ col_ptr,
+                               int64_t m, int32_t* __restrict__ cp) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncols) cp[c] = col_ptr[jc[c]];
+    if (c == ncols) cp[c] = (int32_t)m;
+}
+
+// tile[k] = the column holding edge k * kChunk (columns are non-empty, so exactly one).
+__global__ void dcsc_tile_kernel(const int32_t* __restrict__ cp, int64_t ncols, int32_t* __restrict__ tile) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    const int64_t b = cp[c], e = cp[c + 1];
+    for (int64_t k = (b + kChunk - 1) / kChunk; k * kChunk < e; ++k) tile[k] = (int32_t)c;
+}
+
 inline unsigned blocks_for(int64_t n, int t = 256) {
     int64_t b = (n + t - 1) / t;
     return (unsigned)(b > 0 ? b : 1);
@@ -230,6 +250,42 @@ gm_status build_bins(gm_graph* g) {
         GM_CUDA_TRY(cudaMemcpyAsync(g->in_chunks.p, items.data(), sizeof(int2) * items.size(),
                                     cudaMemcpyHostToDevice, s));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
+    return GM_OK;
+}
+
+// The doubly compressed CSC of the pull side and its edge tiles.
+static gm_status build_dcsc(gm_graph* g) {
+    cudaStream_t s = g->stream;
+    const int64_t n = g->n, m = g->m;
+    DevBuf flags, cnt;
+    GM_TRY(dev_alloc(g->dc_jc, sizeof(int32_t) * (n > 0 ? n : 1), s));
+    GM_TRY(dev_alloc(flags, sizeof(uint32_t) * (n > 0 ? n : 1), s));
+    gm_status st = dev_alloc(cnt, sizeof(uint32_t), s);
+    uint32_t ncols = 0;
+    if (st == GM_OK && n > 0) {
+        positive_flags<<<blocks_for(n), 256, 0, s>>>(as<int32_t>(g->in_deg), n, as<uint32_t>(flags));
+        g_launches++;
+    }
+    if (st == GM_OK) st = compact_indices(as<uint32_t>(flags), n, as<int32_t>(g->dc_jc), as<uint32_t>(cnt), s);
+    if (st == GM_OK) {
+        cudaError_t e = cudaMemcpyAsync(&ncols, cnt.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { set_error("dcsc: %s", cudaGetErrorString(e)); st = GM_ERR_CUDA; }
+    }
+    dev_free(flags, s);
+    dev_free(cnt, s);
+    if (st != GM_OK) return st;
+    g->dc_ncols = ncols;
+    g->dc_ntiles = (m + kChunk - 1) / kChunk;
+    GM_TRY(dev_alloc(g->dc_cp, sizeof(int32_t) * (ncols + 1), s));
+    GM_TRY(dev_alloc(g->dc_tile, sizeof(int32_t) * (g->dc_ntiles + 1), s));
+    dcsc_cp_kernel<<<blocks_for((int64_t)ncols + 1), 256, 0, s>>>(as<int32_t>(g->dc_jc), ncols,
+                                                                 as<int32_t>(g->col_ptr), m, as<int32_t>(g->dc_cp));
+    LAUNCH_CHECK();
+    if (ncols > 0) {
+        dcsc_tile_kernel<<<blocks_for(ncols), 256, 0, s>>>(as<int32_t>(g->dc_cp), ncols, as<int32_t>(g->dc_tile));
+        LAUNCH_CHECK();
+    }
     return GM_OK;
 }
 
@@ -396,6 +452,7 @@ static gm_status ingest(gm_graph* g, const gm_edge_list* el, uint32_t flags) {
         LAUNCH_CHECK();
     }
     GM_TRY(build_bins(g));
+    GM_TRY(build_dcsc(g));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
     return GM_OK;
 }
@@ -542,7 +599,7 @@ void release_graph(gm_graph* g) {
     trav_release(g);
     DevBuf* bufs[] = {&g->row_ptr, &g->col, &g->w, &g->col_ptr, &g->row, &g->cw, &g->csc_pos,
                       &g->out_deg, &g->in_deg, &g->out_bin, &g->in_bin, &g->in_list, &g->zero_in_list,
-                      &g->in_chunks,
+                      &g->in_chunks, &g->dc_jc, &g->dc_cp, &g->dc_tile,
                       &g->state, &g->work, &g->ctl_buf};
     for (DevBuf* b : bufs) dev_free(*b, s);
     if (g->host_pinned) cudaFreeHost(g->host_pinned);

@@ -126,6 +126,12 @@ struct gm_graph {
     int64_t in_list_count[gm::kNumBins + 1] = {0};  // offsets of bins 1..3 inside in_list
     gm::DevBuf in_chunks;            // int2 (vertex, chunk) items covering the in-edges of large-bin vertices
     int64_t n_in_chunks = 0;
+    // Doubly compressed CSC (Section 4.3.1's DCSC): non-empty columns only, and the
+    // column holding the first edge of every kChunk-edge tile of the in-edge array.
+    gm::DevBuf dc_jc;                // vertex id of each non-empty column (ascending)
+    gm::DevBuf dc_cp;                // in-edge offset of each non-empty column, plus m at the end
+    gm::DevBuf dc_tile;              // column index holding edge k * kChunk
+    int64_t dc_ncols = 0, dc_ntiles = 0;
     gm::DevBuf zero_in_list;         // vertex ids with in_deg == 0
     int64_t zero_in_count = 0;
     gm::Tuning tune;

@@ -52,6 +52,8 @@ struct TravArgs {
     const int32_t* out_deg; const int32_t* in_deg; const uint8_t* out_bin;
     const int32_t* in_list; int64_t in_s0, in_s1, in_m1;  // small bin [in_s0, in_s1), medium [in_s1, in_m1)
     const int2* in_chunks; int64_t n_in_chunks;          // large in-degree vertices as (vertex, chunk)
+    const int32_t* dc_jc; const int32_t* dc_cp; const int32_t* dc_tile;  // doubly compressed CSC + tiles
+    int64_t dc_ncols, ntiles;
     int64_t n, m, nwords;
     uint32_t* dist;
     uint32_t* msg[2];        // SSSP messages of superstep t live in msg[t & 1], infinity elsewhere
@@ -316,209 +318,124 @@ __device__ void push_phase(const TravArgs& a, uint32_t t, int cur, int nxt, Acc&
 }
 
 // ---------------------------------------------------------------- pull
-// Lane step over in-edges e0..e0+7 masked to [beg, end): BFS sets `hit` if an
-// in-neighbour is in the frontier; SSSP lowers `best` by msg[u] + w(u, v).
-template <bool SSSP>
-__device__ __forceinline__ void pull_contig(const TravArgs& a, int32_t e0, int32_t beg, int32_t end,
-                                            const uint32_t* __restrict__ bvc, const uint32_t* __restrict__ msgc,
-                                            uint32_t& best, bool& hit, Acc& acc) {
-    if (e0 >= end) return;
-    int32_t u[kEPT];
-    uint32_t wt[kEPT];
-    load8(a.row, e0, u);
-    if (SSSP) load8(a.cw, e0, wt);
-    uint32_t ok = 0u;
-#pragma unroll
-    for (int k = 0; k < kEPT; ++k)
-        if (e0 + k >= beg && e0 + k < end) ok |= 1u << k;
-    acc.scanned += (unsigned)__popc(ok);
-    if (SSSP) {
-        uint32_t mu[kEPT];
-#pragma unroll
-        for (int k = 0; k < kEPT; ++k) mu[k] = ((ok >> k) & 1u) ? __ldg(msgc + u[k]) : kInf;
-#pragma unroll
-        for (int k = 0; k < kEPT; ++k) best = min(best, sat_add(mu[k], wt[k]));
-    } else {
-        bool h[kEPT];
-#pragma unroll
-        for (int k = 0; k < kEPT; ++k) h[k] = ((ok >> k) & 1u) && test_bit(bvc, u[k]);
-#pragma unroll
-        for (int k = 0; k < kEPT; ++k) hit |= h[k];
-    }
-}
+// Pull over the doubly compressed CSC in fixed tiles of kChunk in-edges, one CTA
+// per tile: each thread reads 8 consecutive in-edges with 16-byte loads, finds
+// their columns (destination vertices) in the tile's column pointers staged in
+// shared memory, and folds runs of one column into a shared-memory minimum.
+// Columns inside the tile are owned by the CTA (plain update); a column that
+// crosses a tile border (hubs) is combined with atomicMin / atomicCAS.
+// BFS: a column's value is t+1 if any in-neighbour is in the frontier bitvector;
+// columns already visited are skipped without reading their edges.
+// SSSP: min over in-edges of msg[u] + w(u, v), msg infinity off the frontier.
+struct PullSmem {
+    int32_t cp[kChunk + 4];
+    int32_t v[kChunk + 4];
+    uint32_t best[kChunk + 4];
+    uint8_t skip[kChunk + 4];
+};
 
 template <bool SSSP>
-__device__ void pull_phase(const TravArgs& a, uint32_t t, int cur, int nxt, Acc& acc, uint32_t* sw,
-                           uint32_t* s_red) {
-    const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
-    const uint32_t gwarp = (blockIdx.x * kThreads + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * kThreads) >> 5;
+__device__ void pull_tiles(const TravArgs& a, uint32_t t, int cur, int nxt, Acc& acc, PullSmem& sm) {
     const uint32_t* __restrict__ bvc = a.bv[cur];
     const uint32_t* __restrict__ msgc = a.msg[t & 1u];
-
-    // large in-degree: one CTA per 2048-edge chunk, combined through atomics
-    __shared__ uint32_t s_skip;
-    for (int64_t i = blockIdx.x; i < a.n_in_chunks; i += gridDim.x) {
-        const int2 it = a.in_chunks[i];
-        const int32_t v = it.x;
-        // Another CTA's chunk of v may claim it meanwhile, so one thread decides
-        // for the whole CTA (the decision must be uniform for the barriers below).
-        if (threadIdx.x == 0) s_skip = (!SSSP && a.dist[v] != kInf) ? 1u : 0u;
-        __syncthreads();
-        if (s_skip) {
-            __syncthreads();
-            continue;
+    for (int64_t k = blockIdx.x; k < a.ntiles; k += gridDim.x) {
+        const int64_t eb = k * (int64_t)kChunk;
+        const int64_t ee = min(a.m, eb + (int64_t)kChunk);
+        const int32_t c0 = a.dc_tile[k];
+        const int32_t c1 = (k + 1 < a.ntiles) ? a.dc_tile[k + 1] : (int32_t)(a.dc_ncols - 1);
+        const int ncols = c1 - c0 + 1;
+        const int64_t e0 = eb + (int64_t)threadIdx.x * kEPT;
+        int32_t u[kEPT];
+        uint32_t wt[kEPT];
+        if (SSSP && e0 < ee) {  // independent of the staged columns: issue first
+            load8(a.row, (int32_t)e0, u);
+            load8(a.cw, (int32_t)e0, wt);
         }
-        if (threadIdx.x == 0 && it.y == 0) acc.verts++;
-        const int32_t ce = a.col_ptr[v + 1];
-        const int32_t beg = a.col_ptr[v] + it.y * kChunk;
-        const int32_t end = min(ce, beg + kChunk);
-        uint32_t best = kInf;
-        bool hit = false;
-        for (int32_t base = beg & ~3; base < end; base += kCtaSpan) {
-            pull_contig<SSSP>(a, base + (int32_t)threadIdx.x * kEPT, beg, end, bvc, msgc, best, hit, acc);
-            if (!SSSP) {
-                if (__syncthreads_or(hit)) { hit = true; break; }
+        for (int i = threadIdx.x; i <= ncols; i += kThreads) {
+            sm.cp[i] = a.dc_cp[c0 + i];
+            if (i < ncols) {
+                const int32_t v = a.dc_jc[c0 + i];
+                sm.v[i] = v;
+                sm.best[i] = kInf;
+                sm.skip[i] = (!SSSP && a.dist[v] != kInf) ? 1 : 0;
             }
         }
-        bool want = false;
-        if (SSSP) {
-            best = warp_min_u32(best);
-            if (lane == 0) s_red[wid] = best;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                best = kInf;
-                for (int w2 = 0; w2 < kWarps; ++w2) best = min(best, s_red[w2]);
-                if (best < a.dist[v]) {
-                    const uint32_t old = atomicMin(&a.dist[v], best);
-                    if (best < old) {
-                        const uint32_t bit = 1u << (v & 31);
-                        want = (atomicOr(&a.bv[nxt][v >> 5], bit) & bit) == 0u;
+        __syncthreads();
+        if (e0 < ee) {
+            int lo = 0, hi = ncols - 1;  // largest column whose first edge is <= e0
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sm.cp[mid] <= e0) lo = mid;
+                else hi = mid - 1;
+            }
+            int own[kEPT];
+            uint32_t ok = 0u;
+#pragma unroll
+            for (int q = 0; q < kEPT; ++q) {
+                const int64_t e = e0 + q;
+                own[q] = lo;
+                if (e < ee) {
+                    while (e >= sm.cp[lo + 1]) ++lo;
+                    own[q] = lo;
+                    if (SSSP || !sm.skip[lo]) ok |= 1u << q;
+                }
+            }
+            if (!SSSP && ok) load8(a.row, (int32_t)e0, u);
+            acc.scanned += (unsigned)__popc(ok);
+            uint32_t cand[kEPT];
+#pragma unroll
+            for (int q = 0; q < kEPT; ++q) {
+                if (SSSP) cand[q] = ((ok >> q) & 1u) ? sat_add(__ldg(msgc + u[q]), wt[q]) : kInf;
+                else cand[q] = (((ok >> q) & 1u) && test_bit(bvc, u[q])) ? t + 1u : kInf;
+            }
+            uint32_t run = kInf;
+            int ro = own[0];
+#pragma unroll
+            for (int q = 0; q < kEPT; ++q) {
+                if (own[q] != ro) {
+                    if (run != kInf) atomicMin(&sm.best[ro], run);
+                    run = kInf;
+                    ro = own[q];
+                }
+                run = min(run, cand[q]);
+            }
+            if (run != kInf) atomicMin(&sm.best[ro], run);
+        }
+        __syncthreads();
+        for (int base = 0; base < ncols; base += kThreads) {  // apply; trip count uniform over the CTA
+            const int i = base + (int)threadIdx.x;
+            bool want = false;
+            int32_t v = 0;
+            if (i < ncols) {
+                v = sm.v[i];
+                const uint32_t b = sm.best[i];
+                const int64_t cb = sm.cp[i], ce = sm.cp[i + 1];
+                if (cb >= eb && cb < ee && !sm.skip[i]) acc.verts++;
+                if (b != kInf) {
+                    const uint32_t bit = 1u << (v & 31);
+                    if (cb >= eb && ce <= ee) {  // owned by this tile
+                        if (b < a.dist[v]) {
+                            a.dist[v] = b;
+                            atomicOr(&a.bv[nxt][v >> 5], bit);
+                            want = true;
+                        }
+                    } else if (SSSP) {
+                        if (b < a.dist[v] && b < atomicMin(&a.dist[v], b))
+                            want = (atomicOr(&a.bv[nxt][v >> 5], bit) & bit) == 0u;
+                    } else if (atomicCAS(&a.dist[v], kInf, b) == kInf) {
+                        atomicOr(&a.bv[nxt][v >> 5], bit);
+                        want = true;
                     }
                 }
             }
-        } else if (threadIdx.x == 0 && hit) {
-            if (atomicCAS(&a.dist[v], kInf, t + 1u) == kInf) {
-                atomicOr(&a.bv[nxt][v >> 5], 1u << (v & 31));
-                want = true;
-            }
-        }
-        if (wid == 0) {
             bool wa[kEPT] = {want, false, false, false, false, false, false, false};
             int32_t va[kEPT] = {v, 0, 0, 0, 0, 0, 0, 0};
             enqueue_batch<!SSSP>(a, wa, va, nxt, acc);
         }
         __syncthreads();
     }
-    // medium: one warp per vertex, the warp owns the vertex
-    for (int64_t i = a.in_s1 + gwarp; i < a.in_m1; i += nwarps) {
-        const int32_t v = a.in_list[i];
-        if (!SSSP && a.dist[v] != kInf) continue;  // uniform over the warp
-        if (lane == 0) acc.verts++;
-        const int32_t beg = a.col_ptr[v], end = a.col_ptr[v + 1];
-        uint32_t best = kInf;
-        bool hit = false;
-        for (int32_t base = beg & ~3; base < end; base += kWarpSpan) {
-            pull_contig<SSSP>(a, base + lane * kEPT, beg, end, bvc, msgc, best, hit, acc);
-            if (!SSSP && __any_sync(kFull, hit)) { hit = true; break; }
-        }
-        if (SSSP) best = warp_min_u32(best);
-        bool want = false;
-        if (lane == 0) {
-            const uint32_t nv = SSSP ? best : (hit ? t + 1u : kInf);
-            if (nv < a.dist[v]) {
-                a.dist[v] = nv;
-                atomicOr(&a.bv[nxt][v >> 5], 1u << (v & 31));
-                want = true;
-            }
-        }
-        bool wa[kEPT] = {want, false, false, false, false, false, false, false};
-        int32_t va[kEPT] = {v, 0, 0, 0, 0, 0, 0, 0};
-        enqueue_batch<!SSSP>(a, wa, va, nxt, acc);
-    }
-    // small: 32 vertices per warp, in-edge lists concatenated, per-owner min in shared memory
-    int32_t* s_beg = reinterpret_cast<int32_t*>(sw);
-    uint32_t* s_ex = sw + 32;  // 33 entries
-    uint32_t* s_best = sw + 65;
-    for (int64_t g0 = a.in_s0 + (int64_t)gwarp * 32; g0 < a.in_s1; g0 += (int64_t)nwarps * 32) {
-        const int64_t i = g0 + lane;
-        int32_t v = 0, beg = 0;
-        uint32_t deg = 0u;
-        if (i < a.in_s1) {
-            v = a.in_list[i];
-            if (SSSP || a.dist[v] == kInf) {
-                acc.verts++;
-                beg = a.col_ptr[v];
-                deg = (uint32_t)(a.col_ptr[v + 1] - beg);
-            }
-        }
-        const uint32_t incl = warp_incl_scan(deg);
-        __syncwarp();
-        s_beg[lane] = beg;
-        s_ex[lane] = incl - deg;
-        s_best[lane] = kInf;
-        if (lane == 31) s_ex[32] = incl;
-        __syncwarp();
-        const uint32_t total = s_ex[32];
-        for (uint32_t base = 0; base < total; base += kWarpSpan) {
-            const uint32_t j0 = base + (uint32_t)lane * kEPT;
-            int o = owner_of(s_ex, j0);
-            int32_t u[kEPT];
-            uint32_t wt[kEPT];
-            int own[kEPT];
-            uint32_t ok = 0u;
-#pragma unroll
-            for (int k = 0; k < kEPT; ++k) {
-                const uint32_t j = j0 + k;
-                u[k] = 0;
-                wt[k] = 0u;
-                own[k] = o;
-                if (j < total) {
-                    while (j >= s_ex[o + 1]) ++o;
-                    const int32_t e = s_beg[o] + (int32_t)(j - s_ex[o]);
-                    u[k] = a.row[e];
-                    if (SSSP) wt[k] = a.cw[e];
-                    own[k] = o;
-                    ok |= 1u << k;
-                }
-            }
-            acc.scanned += (unsigned)__popc(ok);
-            uint32_t cand[kEPT];
-#pragma unroll
-            for (int k = 0; k < kEPT; ++k) {
-                if (SSSP) cand[k] = ((ok >> k) & 1u) ? sat_add(__ldg(msgc + u[k]), wt[k]) : kInf;
-                else cand[k] = (((ok >> k) & 1u) && test_bit(bvc, u[k])) ? t + 1u : kInf;
-            }
-            // lane-local runs of one owner, then one shared-memory atomic per run
-            uint32_t run = kInf;
-            int ro = own[0];
-#pragma unroll
-            for (int k = 0; k < kEPT; ++k) {
-                if (own[k] != ro) {
-                    if (run != kInf) atomicMin(&s_best[ro], run);
-                    run = kInf;
-                    ro = own[k];
-                }
-                run = min(run, cand[k]);
-            }
-            if (run != kInf) atomicMin(&s_best[ro], run);
-        }
-        __syncwarp();
-        bool want = false;
-        if (i < a.in_s1 && deg > 0u) {
-            const uint32_t b = s_best[lane];
-            if (b < a.dist[v]) {
-                a.dist[v] = b;
-                atomicOr(&a.bv[nxt][v >> 5], 1u << (v & 31));
-                want = true;
-            }
-        }
-        bool wa[kEPT] = {want, false, false, false, false, false, false, false};
-        int32_t va[kEPT] = {v, 0, 0, 0, 0, 0, 0, 0};
-        enqueue_batch<!SSSP>(a, wa, va, nxt, acc);
-    }
 }
+
 
 template <bool SSSP>
 __global__ void __launch_bounds__(kThreads) trav_relax(TravArgs a) {
@@ -545,10 +462,10 @@ __global__ void __launch_bounds__(kThreads) trav_relax(TravArgs a) {
         }
     }
     __shared__ uint32_t s_w[kWarps][100];
-    __shared__ uint32_t s_red[kWarps];
+    __shared__ PullSmem s_pull;
     Acc acc = {0ull, 0ull, 0ull, 0ull};
     if (cd->c.dir == 0) push_phase<SSSP>(a, t, cur, nxt, acc, s_w[threadIdx.x >> 5]);
-    else pull_phase<SSSP>(a, t, cur, nxt, acc, s_w[threadIdx.x >> 5], s_red);
+    else pull_tiles<SSSP>(a, t, cur, nxt, acc, s_pull);
     acc.scanned = warp_sum_u64(acc.scanned);
     acc.verts = warp_sum_u64(acc.verts);
     acc.medges = warp_sum_u64(acc.medges);
@@ -751,6 +668,11 @@ TravArgs make_args(gm_graph* g) {
     a.in_m1 = g->in_list_count[2];
     a.in_chunks = as<int2>(g->in_chunks);
     a.n_in_chunks = g->n_in_chunks;
+    a.dc_jc = as<int32_t>(g->dc_jc);
+    a.dc_cp = as<int32_t>(g->dc_cp);
+    a.dc_tile = as<int32_t>(g->dc_tile);
+    a.dc_ncols = g->dc_ncols;
+    a.ntiles = g->dc_ntiles;
     a.n = g->n;
     a.m = g->m;
     a.nwords = (g->n + 31) / 32;
