@@ -155,12 +155,12 @@ __global__ void dcsc_cp_kernel(const int32_t* __restrict__ jc, int64_t ncols, co
     if (c == ncols) cp[c] = (int32_t)m;
 }
 
-// tile[k] = the column holding edge k * kChunk (columns are non-empty, so exactly one).
+// tile[k] = the column holding edge k * kWTile (columns are non-empty, so exactly one).
 __global__ void dcsc_tile_kernel(const int32_t* __restrict__ cp, int64_t ncols, int32_t* __restrict__ tile) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncols) return;
     const int64_t b = cp[c], e = cp[c + 1];
-    for (int64_t k = (b + kChunk - 1) / kChunk; k * kChunk < e; ++k) tile[k] = (int32_t)c;
+    for (int64_t k = (b + kWTile - 1) / kWTile; k * kWTile < e; ++k) tile[k] = (int32_t)c;
 }
 
 inline unsigned blocks_for(int64_t n, int t = 256) {
@@ -276,7 +276,7 @@ static gm_status build_dcsc(gm_graph* g) {
     dev_free(cnt, s);
     if (st != GM_OK) return st;
     g->dc_ncols = ncols;
-    g->dc_ntiles = (m + kChunk - 1) / kChunk;
+    g->dc_ntiles = (m + kWTile - 1) / kWTile;
     GM_TRY(dev_alloc(g->dc_cp, sizeof(int32_t) * (ncols + 1), s));
     GM_TRY(dev_alloc(g->dc_tile, sizeof(int32_t) * (g->dc_ntiles + 1), s));
     dcsc_cp_kernel<<<blocks_for((int64_t)ncols + 1), 256, 0, s>>>(as<int32_t>(g->dc_jc), ncols,

@@ -18,6 +18,7 @@ constexpr int kNumBins = 3;             // degree bins: small (warp-cooperative)
 constexpr int kEdgePad = 16;            // per-edge arrays carry this many spare entries, so 16-byte
                                         // vector loads that start inside a row never leave the buffer
 constexpr int kChunk = 2048;            // edges of one large-vertex work item (256 threads x 8 edges)
+constexpr int kWTile = 256;             // in-edges of one warp tile of the pull side (32 lanes x 8 edges)
 
 // Library-wide count of kernel launches issued (a graph replay counts each
 // kernel node it runs).
@@ -127,10 +128,10 @@ struct gm_graph {
     gm::DevBuf in_chunks;            // int2 (vertex, chunk) items covering the in-edges of large-bin vertices
     int64_t n_in_chunks = 0;
     // Doubly compressed CSC (Section 4.3.1's DCSC): non-empty columns only, and the
-    // column holding the first edge of every kChunk-edge tile of the in-edge array.
+    // column holding the first edge of every kWTile-edge tile of the in-edge array.
     gm::DevBuf dc_jc;                // vertex id of each non-empty column (ascending)
     gm::DevBuf dc_cp;                // in-edge offset of each non-empty column, plus m at the end
-    gm::DevBuf dc_tile;              // column index holding edge k * kChunk
+    gm::DevBuf dc_tile;              // column index holding edge k * kWTile
     int64_t dc_ncols = 0, dc_ntiles = 0;
     gm::DevBuf zero_in_list;         // vertex ids with in_deg == 0
     int64_t zero_in_count = 0;

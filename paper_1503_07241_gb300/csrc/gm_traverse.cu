@@ -1,6 +1,7 @@
 // BFS and SSSP supersteps (Algorithms 1 and 2 with the min semiring).
 //
-// One superstep is two kernels:
+// One superstep is three kernels (push and pull are both launched; the one that
+// does not match the direction chosen on the device returns at once):
 //   relax     the generalized SPMV with Process_Message/Reduce fused into the
 //             update of the vertex property (Apply = min), either
 //               push: over the out-edges (CSR) of the compacted frontier queue,
@@ -18,9 +19,10 @@
 //
 // Work decomposition for HBM bandwidth: every lane handles 8 edges per step with
 // two 16-byte streaming loads per edge array, so each warp keeps 1-2 KB of edge
-// data in flight.  Vertices of small degree go 32 to a warp with their edge lists
-// concatenated, medium ones a warp each, large ones as 2048-edge chunks, one CTA
-// per chunk, combined with atomics.
+// data in flight.  Push: frontier vertices of small degree go 32 to a warp with
+// their edge lists concatenated, medium ones a warp each, large ones as 2048-edge
+// chunks, one CTA per chunk.  Pull: fixed 256-edge warp tiles over the doubly
+// compressed CSC, columns crossing tiles combined with atomics.
 //
 // BSP semantics are exact: messages come from values fixed at the start of the
 // superstep (BFS: the constant t+1; SSSP: the message array), so the property
@@ -318,49 +320,94 @@ __device__ void push_phase(const TravArgs& a, uint32_t t, int cur, int nxt, Acc&
 }
 
 // ---------------------------------------------------------------- pull
-// Pull over the doubly compressed CSC in fixed tiles of kChunk in-edges, one CTA
-// per tile: each thread reads 8 consecutive in-edges with 16-byte loads, finds
-// their columns (destination vertices) in the tile's column pointers staged in
-// shared memory, and folds runs of one column into a shared-memory minimum.
-// Columns inside the tile are owned by the CTA (plain update); a column that
-// crosses a tile border (hubs) is combined with atomicMin / atomicCAS.
-// BFS: a column's value is t+1 if any in-neighbour is in the frontier bitvector;
-// columns already visited are skipped without reading their edges.
+// Pull over the doubly compressed CSC in warp tiles of kWTile in-edges: each lane
+// reads 8 consecutive in-edges with 16-byte loads, finds their columns
+// (destination vertices) among the tile's column pointers staged in shared
+// memory, and folds runs of one column into a shared-memory minimum.  A column
+// inside the tile is owned by the warp (plain update); a column crossing a tile
+// border (hubs) is combined with atomicMin / atomicCAS.  Warps never wait for one
+// another, so a tile's load latency overlaps with the other warps' work.
+// BFS: a column's value is t+1 if an in-neighbour is in the frontier bitvector;
+// visited columns are marked 0 and their edges are not read.
 // SSSP: min over in-edges of msg[u] + w(u, v), msg infinity off the frontier.
-struct PullSmem {
-    int32_t cp[kChunk + 4];
-    int32_t v[kChunk + 4];
-    uint32_t best[kChunk + 4];
-    uint8_t skip[kChunk + 4];
+struct WarpTile {
+    int32_t cp[kWTile + 4];
+    int32_t v[kWTile + 4];
+    uint32_t best[kWTile + 4];
 };
 
+// Work every relax launch does first: clear the frontier of superstep t-1 (its
+// bitvector becomes "next" in superstep t+1) and, for SSSP, its messages in
+// msg[(t+1) & 1], which finalize refills.
 template <bool SSSP>
-__device__ void pull_tiles(const TravArgs& a, uint32_t t, int cur, int nxt, Acc& acc, PullSmem& sm) {
+__device__ __forceinline__ void relax_prologue(const TravArgs& a, const TravCtl* c, uint32_t t, int clr) {
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gsize = (int64_t)gridDim.x * blockDim.x;
+    uint32_t* bz = a.bv[clr];
+    for (int64_t i = gtid; i < a.nwords; i += gsize) bz[i] = 0u;
+    if (SSSP) {
+        const uint32_t n1 = c->count[clr][1], n2 = c->count[clr][2], n3 = c->count[clr][3];
+        uint32_t* mz = a.msg[(t + 1u) & 1u];
+        for (int64_t i = gtid; i < (int64_t)n1 + n2 + n3; i += gsize) {
+            int32_t v;
+            if (i < n1) v = a.q[clr][1][i];
+            else if (i < (int64_t)n1 + n2) v = a.q[clr][2][i - n1];
+            else v = a.qc[clr][i - n1 - n2].x;
+            mz[v] = kInf;
+        }
+    }
+}
+
+__device__ __forceinline__ void flush_acc(TravCtl* c, Acc& acc, int nxt, bool bfs) {
+    acc.scanned = warp_sum_u64(acc.scanned);
+    acc.verts = warp_sum_u64(acc.verts);
+    acc.medges = warp_sum_u64(acc.medges);
+    acc.unvis = warp_sum_u64(acc.unvis);
+    if ((threadIdx.x & 31) == 0) {
+        if (acc.scanned) atomicAdd(&c->scanned_edges, acc.scanned);
+        if (acc.verts) atomicAdd(&c->processed_vertices, acc.verts);
+        if (acc.medges) atomicAdd(&c->medges[nxt], acc.medges);
+        if (bfs && acc.unvis) atomicAdd(&c->unvisited_in_edges, 0ull - acc.unvis);
+    }
+}
+
+template <bool SSSP>
+__global__ void __launch_bounds__(kThreads, 5) trav_pull(TravArgs a) {
+    TravCtlDev* cd = a.ctl;
+    if (cd->c.done || cd->c.dir != 1u) return;
+    const uint32_t t = cd->c.iter;
+    const int cur = (int)(t % 3u), nxt = (int)((t + 1u) % 3u), clr = (int)((t + 2u) % 3u);
+    relax_prologue<SSSP>(a, &cd->c, t, clr);
+    __shared__ WarpTile s_tiles[kWarps];
+    WarpTile& sm = s_tiles[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
     const uint32_t* __restrict__ bvc = a.bv[cur];
     const uint32_t* __restrict__ msgc = a.msg[t & 1u];
-    for (int64_t k = blockIdx.x; k < a.ntiles; k += gridDim.x) {
-        const int64_t eb = k * (int64_t)kChunk;
-        const int64_t ee = min(a.m, eb + (int64_t)kChunk);
+    Acc acc = {0ull, 0ull, 0ull, 0ull};
+    for (int64_t k = gwarp; k < a.ntiles; k += nwarps) {
+        const int64_t eb = k * (int64_t)kWTile;
+        const int64_t ee = min(a.m, eb + (int64_t)kWTile);
         const int32_t c0 = a.dc_tile[k];
         const int32_t c1 = (k + 1 < a.ntiles) ? a.dc_tile[k + 1] : (int32_t)(a.dc_ncols - 1);
         const int ncols = c1 - c0 + 1;
-        const int64_t e0 = eb + (int64_t)threadIdx.x * kEPT;
+        const int64_t e0 = eb + (int64_t)lane * kEPT;
         int32_t u[kEPT];
         uint32_t wt[kEPT];
         if (SSSP && e0 < ee) {  // independent of the staged columns: issue first
             load8(a.row, (int32_t)e0, u);
             load8(a.cw, (int32_t)e0, wt);
         }
-        for (int i = threadIdx.x; i <= ncols; i += kThreads) {
-            sm.cp[i] = a.dc_cp[c0 + i];
+        for (int i = lane; i <= ncols; i += 32) {
+            sm.cp[i] = __ldg(a.dc_cp + c0 + i);
             if (i < ncols) {
-                const int32_t v = a.dc_jc[c0 + i];
+                const int32_t v = __ldg(a.dc_jc + c0 + i);
                 sm.v[i] = v;
-                sm.best[i] = kInf;
-                sm.skip[i] = (!SSSP && a.dist[v] != kInf) ? 1 : 0;
+                sm.best[i] = (!SSSP && a.dist[v] != kInf) ? 0u : kInf;  // 0 marks a visited column
             }
         }
-        __syncthreads();
+        __syncwarp();
         if (e0 < ee) {
             int lo = 0, hi = ncols - 1;  // largest column whose first edge is <= e0
             while (lo < hi) {
@@ -377,7 +424,7 @@ __device__ void pull_tiles(const TravArgs& a, uint32_t t, int cur, int nxt, Acc&
                 if (e < ee) {
                     while (e >= sm.cp[lo + 1]) ++lo;
                     own[q] = lo;
-                    if (SSSP || !sm.skip[lo]) ok |= 1u << q;
+                    if (SSSP || sm.best[lo] != 0u) ok |= 1u << q;
                 }
             }
             if (!SSSP && ok) load8(a.row, (int32_t)e0, u);
@@ -401,17 +448,17 @@ __device__ void pull_tiles(const TravArgs& a, uint32_t t, int cur, int nxt, Acc&
             }
             if (run != kInf) atomicMin(&sm.best[ro], run);
         }
-        __syncthreads();
-        for (int base = 0; base < ncols; base += kThreads) {  // apply; trip count uniform over the CTA
-            const int i = base + (int)threadIdx.x;
+        __syncwarp();
+        for (int base = 0; base < ncols; base += 32) {  // apply; trip count uniform over the warp
+            const int i = base + lane;
             bool want = false;
             int32_t v = 0;
             if (i < ncols) {
                 v = sm.v[i];
                 const uint32_t b = sm.best[i];
                 const int64_t cb = sm.cp[i], ce = sm.cp[i + 1];
-                if (cb >= eb && cb < ee && !sm.skip[i]) acc.verts++;
-                if (b != kInf) {
+                if (cb >= eb && cb < ee && b != 0u) acc.verts++;
+                if (b != kInf && b != 0u) {
                     const uint32_t bit = 1u << (v & 31);
                     if (cb >= eb && ce <= ee) {  // owned by this tile
                         if (b < a.dist[v]) {
@@ -432,51 +479,22 @@ __device__ void pull_tiles(const TravArgs& a, uint32_t t, int cur, int nxt, Acc&
             int32_t va[kEPT] = {v, 0, 0, 0, 0, 0, 0, 0};
             enqueue_batch<!SSSP>(a, wa, va, nxt, acc);
         }
-        __syncthreads();
+        __syncwarp();
     }
+    flush_acc(&cd->c, acc, nxt, !SSSP);
 }
 
-
 template <bool SSSP>
-__global__ void __launch_bounds__(kThreads) trav_relax(TravArgs a) {
+__global__ void __launch_bounds__(kThreads) trav_push(TravArgs a) {
     TravCtlDev* cd = a.ctl;
-    if (cd->c.done) return;
+    if (cd->c.done || cd->c.dir != 0u) return;
     const uint32_t t = cd->c.iter;
     const int cur = (int)(t % 3u), nxt = (int)((t + 1u) % 3u), clr = (int)((t + 2u) % 3u);
-    const int64_t gtid = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    const int64_t gsize = (int64_t)gridDim.x * kThreads;
-    {   // the frontier two supersteps back: its bitvector becomes "next" in superstep t+1
-        uint32_t* bz = a.bv[clr];
-        for (int64_t i = gtid; i < a.nwords; i += gsize) bz[i] = 0u;
-        if (SSSP) {  // and its messages leave msg[(t+1) & 1], which finalize refills
-            const TravCtl* c = &cd->c;
-            const uint32_t n1 = c->count[clr][1], n2 = c->count[clr][2], n3 = c->count[clr][3];
-            uint32_t* mz = a.msg[(t + 1u) & 1u];
-            for (int64_t i = gtid; i < (int64_t)n1 + n2 + n3; i += gsize) {
-                int32_t v;
-                if (i < n1) v = a.q[clr][1][i];
-                else if (i < (int64_t)n1 + n2) v = a.q[clr][2][i - n1];
-                else v = a.qc[clr][i - n1 - n2].x;
-                mz[v] = kInf;
-            }
-        }
-    }
+    relax_prologue<SSSP>(a, &cd->c, t, clr);
     __shared__ uint32_t s_w[kWarps][100];
-    __shared__ PullSmem s_pull;
     Acc acc = {0ull, 0ull, 0ull, 0ull};
-    if (cd->c.dir == 0) push_phase<SSSP>(a, t, cur, nxt, acc, s_w[threadIdx.x >> 5]);
-    else pull_tiles<SSSP>(a, t, cur, nxt, acc, s_pull);
-    acc.scanned = warp_sum_u64(acc.scanned);
-    acc.verts = warp_sum_u64(acc.verts);
-    acc.medges = warp_sum_u64(acc.medges);
-    acc.unvis = warp_sum_u64(acc.unvis);
-    if ((threadIdx.x & 31) == 0) {
-        TravCtl* c = &cd->c;
-        if (acc.scanned) atomicAdd(&c->scanned_edges, acc.scanned);
-        if (acc.verts) atomicAdd(&c->processed_vertices, acc.verts);
-        if (acc.medges) atomicAdd(&c->medges[nxt], acc.medges);
-        if (!SSSP && acc.unvis) atomicAdd(&c->unvisited_in_edges, 0ull - acc.unvis);
-    }
+    push_phase<SSSP>(a, t, cur, nxt, acc, s_w[threadIdx.x >> 5]);
+    flush_acc(&cd->c, acc, nxt, !SSSP);
 }
 
 template <bool SSSP>
@@ -688,15 +706,22 @@ TravArgs make_args(gm_graph* g) {
     return a;
 }
 
-int relax_grid() {
-    static int blocks = 0;
-    if (blocks == 0) {
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trav_relax<true>, kThreads, 0);
-        if (per_sm <= 0) per_sm = 1;
-        if (per_sm > 8) per_sm = 8;
-        blocks = per_sm * num_sms();
-    }
+template <typename K>
+int grid_for(K kernel) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
+    if (per_sm <= 0) per_sm = 1;
+    if (per_sm > 8) per_sm = 8;
+    return per_sm * num_sms();
+}
+
+int push_grid() {
+    static int blocks = grid_for(trav_push<true>);
+    return blocks;
+}
+
+int pull_grid() {
+    static int blocks = grid_for(trav_pull<true>);
     return blocks;
 }
 
@@ -771,12 +796,17 @@ gm_status build_loop_graph(gm_graph* g, bool sssp) {
     a.use_cond = 1;
     void* kargs[] = {&a};
     cudaKernelNodeParams kp = {};
-    kp.func = sssp ? (void*)trav_relax<true> : (void*)trav_relax<false>;
-    kp.gridDim = dim3((unsigned)relax_grid());
+    kp.func = sssp ? (void*)trav_push<true> : (void*)trav_push<false>;
+    kp.gridDim = dim3((unsigned)push_grid());
     kp.blockDim = dim3(kThreads);
     kp.kernelParams = kargs;
-    cudaGraphNode_t n1, n2;
-    e = cudaGraphAddKernelNode(&n1, body, nullptr, 0, &kp);
+    cudaGraphNode_t n0, n1, n2;
+    e = cudaGraphAddKernelNode(&n0, body, nullptr, 0, &kp);
+    if (e == cudaSuccess) {
+        kp.func = sssp ? (void*)trav_pull<true> : (void*)trav_pull<false>;
+        kp.gridDim = dim3((unsigned)pull_grid());
+        e = cudaGraphAddKernelNode(&n1, body, &n0, 1, &kp);
+    }
     if (e == cudaSuccess) {
         kp.func = sssp ? (void*)trav_finalize<true> : (void*)trav_finalize<false>;
         kp.gridDim = dim3((unsigned)finalize_grid());
@@ -854,7 +884,7 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
         GM_CUDA_TRY(cudaGraphLaunch(g->loop_exec, s));
     } else {
         TravArgs a = make_args(g);
-        const int rg = relax_grid(), fg = finalize_grid();
+        const int pg = push_grid(), lg = pull_grid(), fg = finalize_grid();
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
         if (g->tune.profile) {
             GM_CUDA_TRY(cudaEventCreate(&ev0));
@@ -872,10 +902,13 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
                                   hp->c.count[slot][3];
             }
             if (ev0) cudaEventRecord(ev0, s);
-            if (sssp) trav_relax<true><<<rg, kThreads, 0, s>>>(a);
-            else trav_relax<false><<<rg, kThreads, 0, s>>>(a);
+            // both are launched; the one not matching the device-side direction returns at once
+            if (sssp) trav_push<true><<<pg, kThreads, 0, s>>>(a);
+            else trav_push<false><<<pg, kThreads, 0, s>>>(a);
+            if (sssp) trav_pull<true><<<lg, kThreads, 0, s>>>(a);
+            else trav_pull<false><<<lg, kThreads, 0, s>>>(a);
             if (ev1) cudaEventRecord(ev1, s);
-            g_launches++;
+            g_launches += 2;
             LAUNCH_OK();
             if (sssp) trav_finalize<true><<<fg, kThreads, 0, s>>>(a);
             else trav_finalize<false><<<fg, kThreads, 0, s>>>(a);
@@ -908,7 +941,7 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
     }
     GM_CUDA_TRY(cudaMemcpyAsync(hp, g->ctl_buf.p, sizeof(TravCtlDev), cudaMemcpyDeviceToHost, s));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
-    if (!host_loop) g_launches += 2ull * hp->c.iters_done;
+    if (!host_loop) g_launches += 3ull * hp->c.iters_done;
     g->stats.supersteps = (int32_t)hp->c.iters_done;
     g->stats.pushes = (int32_t)hp->c.pushes;
     g->stats.pulls = (int32_t)hp->c.pulls;
