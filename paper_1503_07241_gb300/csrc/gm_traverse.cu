@@ -67,9 +67,20 @@ struct TravArgs {
     int use_cond;
 };
 
-// Per-thread statistics, flushed once per kernel.
+constexpr uint32_t kStage = 256;  // per-warp staging capacity of each queue bin
+
+// Per-warp staging of the next frontier in shared memory: bins 1 and 2 are
+// appended here and copied to the global queue with one atomic per flush, so
+// warps do not all serialise on the same few queue counters.
+struct WarpQ {
+    int32_t buf[2][kStage];
+    uint32_t n[2];
+};
+
+// Per-thread statistics (reduced per CTA once per kernel) and the warp's stage.
 struct Acc {
-    unsigned long long scanned, verts, medges, unvis;
+    unsigned long long scanned, verts, medges, unvis, n0;
+    WarpQ* wq;  // nullptr: enqueue straight to the global queue
 };
 
 __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) {
@@ -112,6 +123,21 @@ __device__ __forceinline__ void load8(const T* p, int32_t e0, T (&x)[kEPT]) {
     x[4] = (T)hi.x; x[5] = (T)hi.y; x[6] = (T)hi.z; x[7] = (T)hi.w;
 }
 
+// Copy a warp's staged bin (1 or 2) to the global queue of slot nxt.  Warp-collective.
+__device__ __forceinline__ void warp_flush(const TravArgs& a, WarpQ* wq, uint32_t b, int nxt) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t n = wq->n[b - 1];
+    if (n == 0u) return;
+    uint32_t base = 0u;
+    if (lane == 0) base = atomicAdd(&a.ctl->c.count[nxt][b], n);
+    base = __shfl_sync(kFull, base, 0);
+    int32_t* dst = a.q[nxt][b] + base;
+    for (uint32_t i = lane; i < n; i += 32) dst[i] = wq->buf[b - 1][i];
+    __syncwarp();
+    if (lane == 0) wq->n[b - 1] = 0u;
+    __syncwarp();
+}
+
 // Append the vertices v[k] with want[k] to the next frontier of slot `nxt`,
 // grouped by out-degree bin (large vertices as one item per chunk).  Warp-collective.
 template <bool BFS>
@@ -141,13 +167,33 @@ __device__ __forceinline__ void enqueue_batch(const TravArgs& a, const bool (&wa
     TravCtl* c = &a.ctl->c;
 #pragma unroll
     for (uint32_t b = 0; b < 4; ++b) {
+        if (b == 0u && acc.wq) {  // no out-edges: counted as active, never pushed from
+            acc.n0 += cnt[0];
+            continue;
+        }
         const uint32_t incl = warp_incl_scan(cnt[b]);
         const uint32_t tot = __shfl_sync(kFull, incl, 31);
         if (tot == 0u) continue;
+        if (acc.wq && b < 3u) {
+            WarpQ* wq = acc.wq;
+            uint32_t n = wq->n[b - 1];
+            if (n + tot > kStage) {
+                warp_flush(a, wq, b, nxt);
+                n = 0u;
+            }
+            uint32_t pos = n + incl - cnt[b];
+#pragma unroll
+            for (int k = 0; k < kEPT; ++k)
+                if (want[k] && bin[k] == b) wq->buf[b - 1][pos++] = v[k];
+            __syncwarp();
+            if (lane == 0) wq->n[b - 1] = n + tot;
+            __syncwarp();
+            continue;
+        }
         uint32_t base = 0u;
         if (lane == 31) base = atomicAdd(&c->count[nxt][b], tot);
         base = __shfl_sync(kFull, base, 31);
-        if (b == 0u) continue;  // no out-edges: counted as active, never pushed from
+        if (b == 0u) continue;
         uint32_t pos = base + incl - cnt[b];
 #pragma unroll
         for (int k = 0; k < kEPT; ++k) {
@@ -358,34 +404,63 @@ __device__ __forceinline__ void relax_prologue(const TravArgs& a, const TravCtl*
     }
 }
 
-__device__ __forceinline__ void flush_acc(TravCtl* c, Acc& acc, int nxt, bool bfs) {
-    acc.scanned = warp_sum_u64(acc.scanned);
-    acc.verts = warp_sum_u64(acc.verts);
-    acc.medges = warp_sum_u64(acc.medges);
-    acc.unvis = warp_sum_u64(acc.unvis);
-    if ((threadIdx.x & 31) == 0) {
-        if (acc.scanned) atomicAdd(&c->scanned_edges, acc.scanned);
-        if (acc.verts) atomicAdd(&c->processed_vertices, acc.verts);
-        if (acc.medges) atomicAdd(&c->medges[nxt], acc.medges);
-        if (bfs && acc.unvis) atomicAdd(&c->unvisited_in_edges, 0ull - acc.unvis);
+// End of a relax kernel: flush the warp's staged queue, then reduce the
+// statistics over the CTA and add them to the control block with one atomic each.
+// CTA-collective.
+__device__ __forceinline__ void flush_acc(const TravArgs& a, Acc& acc, int nxt, bool bfs,
+                                          unsigned long long* s_stat) {
+    TravCtl* c = &a.ctl->c;
+    if (acc.wq) {
+        warp_flush(a, acc.wq, 1u, nxt);
+        warp_flush(a, acc.wq, 2u, nxt);
+    }
+    unsigned long long vals[5] = {acc.scanned, acc.verts, acc.medges, acc.unvis, acc.n0};
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        vals[i] = warp_sum_u64(vals[i]);
+        if ((threadIdx.x & 31) == 0 && vals[i]) atomicAdd(&s_stat[i], vals[i]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_stat[0]) atomicAdd(&c->scanned_edges, s_stat[0]);
+        if (s_stat[1]) atomicAdd(&c->processed_vertices, s_stat[1]);
+        if (s_stat[2]) atomicAdd(&c->medges[nxt], s_stat[2]);
+        if (bfs && s_stat[3]) atomicAdd(&c->unvisited_in_edges, 0ull - s_stat[3]);
+        if (s_stat[4]) atomicAdd(&c->count[nxt][0], (uint32_t)s_stat[4]);
     }
 }
 
 template <bool SSSP>
-__global__ void __launch_bounds__(kThreads, 5) trav_pull(TravArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) trav_pull(TravArgs a) {
     TravCtlDev* cd = a.ctl;
     if (cd->c.done || cd->c.dir != 1u) return;
     const uint32_t t = cd->c.iter;
     const int cur = (int)(t % 3u), nxt = (int)((t + 1u) % 3u), clr = (int)((t + 2u) % 3u);
     relax_prologue<SSSP>(a, &cd->c, t, clr);
     __shared__ WarpTile s_tiles[kWarps];
+    __shared__ WarpQ s_q[kWarps];
+    __shared__ unsigned long long s_stat[5];
     WarpTile& sm = s_tiles[threadIdx.x >> 5];
+    if (threadIdx.x < 5) s_stat[threadIdx.x] = 0ull;
+    if ((threadIdx.x & 31) < 2) s_q[threadIdx.x >> 5].n[threadIdx.x & 31] = 0u;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
     const uint32_t* __restrict__ bvc = a.bv[cur];
     const uint32_t* __restrict__ msgc = a.msg[t & 1u];
-    Acc acc = {0ull, 0ull, 0ull, 0ull};
+    Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, &s_q[threadIdx.x >> 5]};
+    // SSSP: software pipeline -- the edges of the warp's next tile are loaded while
+    // the current tile is processed, so every warp keeps 2 KB of edge data in flight.
+    int32_t u[kEPT];
+    uint32_t wt[kEPT];
+    if (SSSP && gwarp < a.ntiles) {
+        const int64_t p0 = gwarp * (int64_t)kWTile + (int64_t)lane * kEPT;
+        if (p0 < a.m) {
+            load8(a.row, (int32_t)p0, u);
+            load8(a.cw, (int32_t)p0, wt);
+        }
+    }
     for (int64_t k = gwarp; k < a.ntiles; k += nwarps) {
         const int64_t eb = k * (int64_t)kWTile;
         const int64_t ee = min(a.m, eb + (int64_t)kWTile);
@@ -393,11 +468,14 @@ __global__ void __launch_bounds__(kThreads, 5) trav_pull(TravArgs a) {
         const int32_t c1 = (k + 1 < a.ntiles) ? a.dc_tile[k + 1] : (int32_t)(a.dc_ncols - 1);
         const int ncols = c1 - c0 + 1;
         const int64_t e0 = eb + (int64_t)lane * kEPT;
-        int32_t u[kEPT];
-        uint32_t wt[kEPT];
-        if (SSSP && e0 < ee) {  // independent of the staged columns: issue first
-            load8(a.row, (int32_t)e0, u);
-            load8(a.cw, (int32_t)e0, wt);
+        int32_t un[kEPT];
+        uint32_t wn[kEPT];
+        if (SSSP) {
+            const int64_t pn = (k + nwarps) * (int64_t)kWTile + (int64_t)lane * kEPT;
+            if (k + nwarps < a.ntiles && pn < a.m) {
+                load8(a.row, (int32_t)pn, un);
+                load8(a.cw, (int32_t)pn, wn);
+            }
         }
         for (int i = lane; i <= ncols; i += 32) {
             sm.cp[i] = __ldg(a.dc_cp + c0 + i);
@@ -480,8 +558,15 @@ __global__ void __launch_bounds__(kThreads, 5) trav_pull(TravArgs a) {
             enqueue_batch<!SSSP>(a, wa, va, nxt, acc);
         }
         __syncwarp();
+        if (SSSP) {
+#pragma unroll
+            for (int q = 0; q < kEPT; ++q) {
+                u[q] = un[q];
+                wt[q] = wn[q];
+            }
+        }
     }
-    flush_acc(&cd->c, acc, nxt, !SSSP);
+    flush_acc(a, acc, nxt, !SSSP, s_stat);
 }
 
 template <bool SSSP>
@@ -492,9 +577,14 @@ __global__ void __launch_bounds__(kThreads) trav_push(TravArgs a) {
     const int cur = (int)(t % 3u), nxt = (int)((t + 1u) % 3u), clr = (int)((t + 2u) % 3u);
     relax_prologue<SSSP>(a, &cd->c, t, clr);
     __shared__ uint32_t s_w[kWarps][100];
-    Acc acc = {0ull, 0ull, 0ull, 0ull};
+    __shared__ WarpQ s_q[kWarps];
+    __shared__ unsigned long long s_stat[5];
+    if (threadIdx.x < 5) s_stat[threadIdx.x] = 0ull;
+    if ((threadIdx.x & 31) < 2) s_q[threadIdx.x >> 5].n[threadIdx.x & 31] = 0u;
+    __syncthreads();
+    Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, &s_q[threadIdx.x >> 5]};
     push_phase<SSSP>(a, t, cur, nxt, acc, s_w[threadIdx.x >> 5]);
-    flush_acc(&cd->c, acc, nxt, !SSSP);
+    flush_acc(a, acc, nxt, !SSSP, s_stat);
 }
 
 template <bool SSSP>
@@ -587,7 +677,7 @@ __global__ void seed_frontier(TravArgs a, const int32_t* __restrict__ verts, int
         const uint32_t bit = 1u << (v & 31);
         want = (atomicOr(&a.bv[0][v >> 5], bit) & bit) == 0u;
     }
-    Acc acc = {0ull, 0ull, 0ull, 0ull};
+    Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, nullptr};
     bool wa[kEPT] = {want, false, false, false, false, false, false, false};
     int32_t va[kEPT] = {v, 0, 0, 0, 0, 0, 0, 0};
     if (bfs) enqueue_batch<true>(a, wa, va, 0, acc);
@@ -609,7 +699,7 @@ __global__ void seed_all(TravArgs a, int bfs) {
         a.msg[0][v] = 0u;
         atomicOr(&a.bv[0][v >> 5], 1u << (v & 31));
     }
-    Acc acc = {0ull, 0ull, 0ull, 0ull};
+    Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, nullptr};
     bool wa[kEPT] = {want, false, false, false, false, false, false, false};
     int32_t va[kEPT] = {v, 0, 0, 0, 0, 0, 0, 0};
     if (bfs) enqueue_batch<true>(a, wa, va, 0, acc);
