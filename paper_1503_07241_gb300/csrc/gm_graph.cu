@@ -163,6 +163,13 @@ __global__ void dcsc_tile_kernel(const int32_t* __restrict__ cp, int64_t ncols, 
     for (int64_t k = (b + kWTile - 1) / kWTile; k * kWTile < e; ++k) tile[k] = (int32_t)c;
 }
 
+__global__ void dcsc_head_kernel(const int32_t* __restrict__ cp, int64_t ncols, uint32_t* __restrict__ head) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    const int64_t e = cp[c];
+    atomicOr(&head[e >> 5], 1u << (e & 31));
+}
+
 inline unsigned blocks_for(int64_t n, int t = 256) {
     int64_t b = (n + t - 1) / t;
     return (unsigned)(b > 0 ? b : 1);
@@ -282,8 +289,14 @@ static gm_status build_dcsc(gm_graph* g) {
     dcsc_cp_kernel<<<blocks_for((int64_t)ncols + 1), 256, 0, s>>>(as<int32_t>(g->dc_jc), ncols,
                                                                  as<int32_t>(g->col_ptr), m, as<int32_t>(g->dc_cp));
     LAUNCH_CHECK();
+    // head bits, padded so a warp tile's words can always be read
+    const int64_t hwords = (m + 31) / 32 + kWTile / 32 + 1;
+    GM_TRY(dev_alloc(g->dc_head, sizeof(uint32_t) * hwords, s));
+    GM_CUDA_TRY(cudaMemsetAsync(g->dc_head.p, 0, sizeof(uint32_t) * hwords, s));
     if (ncols > 0) {
         dcsc_tile_kernel<<<blocks_for(ncols), 256, 0, s>>>(as<int32_t>(g->dc_cp), ncols, as<int32_t>(g->dc_tile));
+        LAUNCH_CHECK();
+        dcsc_head_kernel<<<blocks_for(ncols), 256, 0, s>>>(as<int32_t>(g->dc_cp), ncols, as<uint32_t>(g->dc_head));
         LAUNCH_CHECK();
     }
     return GM_OK;
@@ -599,7 +612,7 @@ void release_graph(gm_graph* g) {
     trav_release(g);
     DevBuf* bufs[] = {&g->row_ptr, &g->col, &g->w, &g->col_ptr, &g->row, &g->cw, &g->csc_pos,
                       &g->out_deg, &g->in_deg, &g->out_bin, &g->in_bin, &g->in_list, &g->zero_in_list,
-                      &g->in_chunks, &g->dc_jc, &g->dc_cp, &g->dc_tile,
+                      &g->in_chunks, &g->dc_jc, &g->dc_cp, &g->dc_tile, &g->dc_head,
                       &g->state, &g->work, &g->ctl_buf};
     for (DevBuf* b : bufs) dev_free(*b, s);
     if (g->host_pinned) cudaFreeHost(g->host_pinned);

@@ -132,6 +132,7 @@ struct gm_graph {
     gm::DevBuf dc_jc;                // vertex id of each non-empty column (ascending)
     gm::DevBuf dc_cp;                // in-edge offset of each non-empty column, plus m at the end
     gm::DevBuf dc_tile;              // column index holding edge k * kWTile
+    gm::DevBuf dc_head;              // bit e set iff in-edge e is the first of its column (m bits)
     int64_t dc_ncols = 0, dc_ntiles = 0;
     gm::DevBuf zero_in_list;         // vertex ids with in_deg == 0
     int64_t zero_in_count = 0;

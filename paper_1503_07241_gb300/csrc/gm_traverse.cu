@@ -1,7 +1,7 @@
 // BFS and SSSP supersteps (Algorithms 1 and 2 with the min semiring).
 //
-// One superstep is three kernels (push and pull are both launched; the one that
-// does not match the direction chosen on the device returns at once):
+// One superstep is four kernels (push, the two pull kernels and finalize; the
+// direction not chosen on the device returns at once):
 //   relax     the generalized SPMV with Process_Message/Reduce fused into the
 //             update of the vertex property (Apply = min), either
 //               push: over the out-edges (CSR) of the compacted frontier queue,
@@ -59,6 +59,8 @@ struct TravArgs {
     int64_t n, m, nwords;
     uint32_t* dist;
     uint32_t* msg[2];        // SSSP messages of superstep t live in msg[t & 1], infinity elsewhere
+    uint32_t* ycol;          // pull: reduced value per non-empty column, infinity between supersteps
+    const uint32_t* dc_head; // pull: first-edge-of-column bits
     uint32_t* bv[3];         // frontier bitvectors, rotating by superstep
     int32_t* q[3][3];        // [slot][bin], bins 1 (small) and 2 (medium)
     int2* qc[3];             // [slot] large-bin work items (vertex, chunk)
@@ -365,23 +367,6 @@ __device__ void push_phase(const TravArgs& a, uint32_t t, int cur, int nxt, Acc&
     }
 }
 
-// ---------------------------------------------------------------- pull
-// Pull over the doubly compressed CSC in warp tiles of kWTile in-edges: each lane
-// reads 8 consecutive in-edges with 16-byte loads, finds their columns
-// (destination vertices) among the tile's column pointers staged in shared
-// memory, and folds runs of one column into a shared-memory minimum.  A column
-// inside the tile is owned by the warp (plain update); a column crossing a tile
-// border (hubs) is combined with atomicMin / atomicCAS.  Warps never wait for one
-// another, so a tile's load latency overlaps with the other warps' work.
-// BFS: a column's value is t+1 if an in-neighbour is in the frontier bitvector;
-// visited columns are marked 0 and their edges are not read.
-// SSSP: min over in-edges of msg[u] + w(u, v), msg infinity off the frontier.
-struct WarpTile {
-    int32_t cp[kWTile + 4];
-    int32_t v[kWTile + 4];
-    uint32_t best[kWTile + 4];
-};
-
 // Work every relax launch does first: clear the frontier of superstep t-1 (its
 // bitvector becomes "next" in superstep t+1) and, for SSSP, its messages in
 // msg[(t+1) & 1], which finalize refills.
@@ -430,147 +415,187 @@ __device__ __forceinline__ void flush_acc(const TravArgs& a, Acc& acc, int nxt, 
     }
 }
 
+// ---------------------------------------------------------------- pull
+// Pull in two kernels over the doubly compressed CSC (non-empty columns only).
+//  pull_a  streams the in-edges in warp tiles of kWTile: each lane reads 8
+//          consecutive edges with 16-byte loads (the next tile's edges are already
+//          in flight), evaluates Process_Message for each (BFS: t+1 if the source
+//          is in the frontier bitvector; SSSP: msg[u] + w(u, v), msg infinity off
+//          the frontier), and Reduce(min)s them per column.  Columns are found
+//          without any index loads: a bit marks the first edge of every column,
+//          a warp prefix count of these bits numbers the columns, and a warp
+//          segmented min-scan joins the pieces of columns that span lanes.
+//          Complete columns are stored to y[column]; the (at most two) columns
+//          crossing the tile border are combined with atomicMin.
+//  pull_b  applies y to the vertex properties (Apply = min), makes changed
+//          vertices the next frontier and resets y to infinity.
 template <bool SSSP>
-__global__ void __launch_bounds__(kThreads, 4) trav_pull(TravArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) trav_pull_a(TravArgs a) {
     TravCtlDev* cd = a.ctl;
     if (cd->c.done || cd->c.dir != 1u) return;
     const uint32_t t = cd->c.iter;
-    const int cur = (int)(t % 3u), nxt = (int)((t + 1u) % 3u), clr = (int)((t + 2u) % 3u);
+    const int cur = (int)(t % 3u), clr = (int)((t + 2u) % 3u);
     relax_prologue<SSSP>(a, &cd->c, t, clr);
-    __shared__ WarpTile s_tiles[kWarps];
-    __shared__ WarpQ s_q[kWarps];
-    __shared__ unsigned long long s_stat[5];
-    WarpTile& sm = s_tiles[threadIdx.x >> 5];
-    if (threadIdx.x < 5) s_stat[threadIdx.x] = 0ull;
-    if ((threadIdx.x & 31) < 2) s_q[threadIdx.x >> 5].n[threadIdx.x & 31] = 0u;
-    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
     const uint32_t* __restrict__ bvc = a.bv[cur];
     const uint32_t* __restrict__ msgc = a.msg[t & 1u];
-    Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, &s_q[threadIdx.x >> 5]};
-    // SSSP: software pipeline -- the edges of the warp's next tile are loaded while
-    // the current tile is processed, so every warp keeps 2 KB of edge data in flight.
+    uint32_t* __restrict__ y = a.ycol;
+    unsigned long long scanned = 0;
+
     int32_t u[kEPT];
-    uint32_t wt[kEPT];
-    if (SSSP && gwarp < a.ntiles) {
+    uint32_t wt[kEPT], hw = 0u;
+    int32_t c0 = 0;
+    if (gwarp < a.ntiles) {  // first tile of this warp
         const int64_t p0 = gwarp * (int64_t)kWTile + (int64_t)lane * kEPT;
         if (p0 < a.m) {
             load8(a.row, (int32_t)p0, u);
-            load8(a.cw, (int32_t)p0, wt);
+            if (SSSP) load8(a.cw, (int32_t)p0, wt);
         }
+        hw = __ldcs(a.dc_head + (p0 >> 5));
+        c0 = __ldg(a.dc_tile + gwarp);
     }
     for (int64_t k = gwarp; k < a.ntiles; k += nwarps) {
-        const int64_t eb = k * (int64_t)kWTile;
-        const int64_t ee = min(a.m, eb + (int64_t)kWTile);
-        const int32_t c0 = a.dc_tile[k];
-        const int32_t c1 = (k + 1 < a.ntiles) ? a.dc_tile[k + 1] : (int32_t)(a.dc_ncols - 1);
-        const int ncols = c1 - c0 + 1;
-        const int64_t e0 = eb + (int64_t)lane * kEPT;
         int32_t un[kEPT];
-        uint32_t wn[kEPT];
-        if (SSSP) {
-            const int64_t pn = (k + nwarps) * (int64_t)kWTile + (int64_t)lane * kEPT;
-            if (k + nwarps < a.ntiles && pn < a.m) {
-                load8(a.row, (int32_t)pn, un);
-                load8(a.cw, (int32_t)pn, wn);
+        uint32_t wn[kEPT], hwn = 0u;
+        int32_t c0n = 0;
+        {   // software pipeline: issue the next tile's loads now
+            const int64_t kn = k + nwarps;
+            const int64_t pn = kn * (int64_t)kWTile + (int64_t)lane * kEPT;
+            if (kn < a.ntiles) {
+                if (pn < a.m) {
+                    load8(a.row, (int32_t)pn, un);
+                    if (SSSP) load8(a.cw, (int32_t)pn, wn);
+                }
+                hwn = __ldcs(a.dc_head + (pn >> 5));
+                c0n = __ldg(a.dc_tile + kn);
             }
         }
-        for (int i = lane; i <= ncols; i += 32) {
-            sm.cp[i] = __ldg(a.dc_cp + c0 + i);
-            if (i < ncols) {
-                const int32_t v = __ldg(a.dc_jc + c0 + i);
-                sm.v[i] = v;
-                sm.best[i] = (!SSSP && a.dist[v] != kInf) ? 0u : kInf;  // 0 marks a visited column
-            }
-        }
-        __syncwarp();
-        if (e0 < ee) {
-            int lo = 0, hi = ncols - 1;  // largest column whose first edge is <= e0
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (sm.cp[mid] <= e0) lo = mid;
-                else hi = mid - 1;
-            }
-            int own[kEPT];
-            uint32_t ok = 0u;
+        const int64_t e0 = k * (int64_t)kWTile + (int64_t)lane * kEPT;
+        uint32_t vmask = 0u;
 #pragma unroll
-            for (int q = 0; q < kEPT; ++q) {
-                const int64_t e = e0 + q;
-                own[q] = lo;
-                if (e < ee) {
-                    while (e >= sm.cp[lo + 1]) ++lo;
-                    own[q] = lo;
-                    if (SSSP || sm.best[lo] != 0u) ok |= 1u << q;
+        for (int q = 0; q < kEPT; ++q)
+            if (e0 + q < a.m) vmask |= 1u << q;
+        const uint32_t heads = (hw >> ((lane & 3) * 8)) & 0xFFu & vmask;
+        scanned += (unsigned)__popc(vmask);
+        uint32_t cand[kEPT];
+#pragma unroll
+        for (int q = 0; q < kEPT; ++q) {
+            if (SSSP) cand[q] = ((vmask >> q) & 1u) ? sat_add(__ldg(msgc + u[q]), wt[q]) : kInf;
+            else cand[q] = (((vmask >> q) & 1u) && test_bit(bvc, u[q])) ? t + 1u : kInf;
+        }
+        // column numbering: heads before this lane, and whether the tile starts a column
+        const uint32_t nh = (uint32_t)__popc(heads);
+        const uint32_t hincl = warp_incl_scan(nh);
+        const uint32_t hex = hincl - nh;
+        const uint32_t first_is_head = __shfl_sync(kFull, heads & 1u, 0);
+        // column of edge q of this lane: c0 + (heads in the tile up to and including
+        // edge q) - (1 if the tile's first edge is a head)
+        const int32_t col_base = c0 + (int32_t)hex - (int32_t)first_is_head;
+        const int32_t lane_col = col_base;  // column continued by the lane's first edges (no head at bit 0)
+        // lane runs: F before the first head, interior runs complete, L from the last head
+        uint32_t F = kInf, run = kInf;
+        int32_t run_col = lane_col;
+        bool seen = false;
+#pragma unroll
+        for (int q = 0; q < kEPT; ++q) {
+            if ((heads >> q) & 1u) {
+                if (!seen) F = run;
+                else if (run != kInf) y[run_col] = run;  // column entirely inside this lane
+                seen = true;
+                run = kInf;
+                run_col = col_base + (int32_t)__popc(heads & ((2u << q) - 1u));
+            }
+            run = min(run, cand[q]);
+        }
+        if (!seen) F = run;
+        const uint32_t L = run;
+        // segmented min-scan across lanes; a lane with a head starts a new segment
+        uint32_t R = seen ? L : F;
+        uint32_t fr = seen ? 1u : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t Ru = __shfl_up_sync(kFull, R, o);
+            const uint32_t fu = __shfl_up_sync(kFull, fr, o);
+            if (lane >= o) {
+                if (!fr) R = min(R, Ru);
+                fr |= fu;
+            }
+        }
+        uint32_t Rprev = __shfl_up_sync(kFull, R, 1);
+        uint32_t fprev = __shfl_up_sync(kFull, fr, 1);
+        if (lane == 0) { Rprev = kInf; fprev = 0u; }
+        if (seen && !(heads & 1u)) {  // this lane's first edges finish a column begun to its left
+            const uint32_t total = min(F, Rprev);
+            if (total != kInf) {
+                if (fprev) y[lane_col] = total;            // begun inside this tile: complete here
+                else atomicMin(&y[lane_col], total);       // begun in an earlier tile
+            }
+        }
+        // The segment ending with this lane is complete when the next lane starts a
+        // new column; the tile's last segment may continue in the next tile.
+        const uint32_t next_head = __shfl_down_sync(kFull, heads & 1u, 1);
+        if (R != kInf && (lane == 31 || next_head)) {
+            const int32_t end_col = c0 + (int32_t)hincl - (int32_t)first_is_head;
+            if (lane < 31 && fr) y[end_col] = R;  // its first edge lies in this tile
+            else atomicMin(&y[end_col], R);
+        }
+#pragma unroll
+        for (int q = 0; q < kEPT; ++q) {
+            u[q] = un[q];
+            wt[q] = wn[q];
+        }
+        hw = hwn;
+        c0 = c0n;
+    }
+    scanned = warp_sum_u64(scanned);
+    if (lane == 0 && scanned) atomicAdd(&cd->c.scanned_edges, scanned);
+}
+
+template <bool SSSP>
+__global__ void __launch_bounds__(kThreads) trav_pull_b(TravArgs a) {
+    TravCtlDev* cd = a.ctl;
+    if (cd->c.done || cd->c.dir != 1u) return;
+    const uint32_t t = cd->c.iter;
+    const int nxt = (int)((t + 1u) % 3u);
+    __shared__ WarpQ s_q[kWarps];
+    __shared__ unsigned long long s_stat[5];
+    if (threadIdx.x < 5) s_stat[threadIdx.x] = 0ull;
+    if ((threadIdx.x & 31) < 2) s_q[threadIdx.x >> 5].n[threadIdx.x & 31] = 0u;
+    __syncthreads();
+    Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, &s_q[threadIdx.x >> 5]};
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+    uint32_t* __restrict__ y = a.ycol;
+    for (int64_t base = gwarp * 32; base < a.dc_ncols; base += nwarps * 32) {
+        const int64_t c = base + lane;
+        bool want = false;
+        int32_t v = 0;
+        if (c < a.dc_ncols) {
+            const uint32_t b = y[c];
+            if (b != kInf) {
+                y[c] = kInf;
+                v = __ldg(a.dc_jc + c);
+                acc.verts++;
+                if (b < a.dist[v]) {
+                    a.dist[v] = b;
+                    atomicOr(&a.bv[nxt][v >> 5], 1u << (v & 31));
+                    want = true;
                 }
             }
-            if (!SSSP && ok) load8(a.row, (int32_t)e0, u);
-            acc.scanned += (unsigned)__popc(ok);
-            uint32_t cand[kEPT];
-#pragma unroll
-            for (int q = 0; q < kEPT; ++q) {
-                if (SSSP) cand[q] = ((ok >> q) & 1u) ? sat_add(__ldg(msgc + u[q]), wt[q]) : kInf;
-                else cand[q] = (((ok >> q) & 1u) && test_bit(bvc, u[q])) ? t + 1u : kInf;
-            }
-            uint32_t run = kInf;
-            int ro = own[0];
-#pragma unroll
-            for (int q = 0; q < kEPT; ++q) {
-                if (own[q] != ro) {
-                    if (run != kInf) atomicMin(&sm.best[ro], run);
-                    run = kInf;
-                    ro = own[q];
-                }
-                run = min(run, cand[q]);
-            }
-            if (run != kInf) atomicMin(&sm.best[ro], run);
         }
-        __syncwarp();
-        for (int base = 0; base < ncols; base += 32) {  // apply; trip count uniform over the warp
-            const int i = base + lane;
-            bool want = false;
-            int32_t v = 0;
-            if (i < ncols) {
-                v = sm.v[i];
-                const uint32_t b = sm.best[i];
-                const int64_t cb = sm.cp[i], ce = sm.cp[i + 1];
-                if (cb >= eb && cb < ee && b != 0u) acc.verts++;
-                if (b != kInf && b != 0u) {
-                    const uint32_t bit = 1u << (v & 31);
-                    if (cb >= eb && ce <= ee) {  // owned by this tile
-                        if (b < a.dist[v]) {
-                            a.dist[v] = b;
-                            atomicOr(&a.bv[nxt][v >> 5], bit);
-                            want = true;
-                        }
-                    } else if (SSSP) {
-                        if (b < a.dist[v] && b < atomicMin(&a.dist[v], b))
-                            want = (atomicOr(&a.bv[nxt][v >> 5], bit) & bit) == 0u;
-                    } else if (atomicCAS(&a.dist[v], kInf, b) == kInf) {
-                        atomicOr(&a.bv[nxt][v >> 5], bit);
-                        want = true;
-                    }
-                }
-            }
-            bool wa[kEPT] = {want, false, false, false, false, false, false, false};
-            int32_t va[kEPT] = {v, 0, 0, 0, 0, 0, 0, 0};
-            enqueue_batch<!SSSP>(a, wa, va, nxt, acc);
-        }
-        __syncwarp();
-        if (SSSP) {
-#pragma unroll
-            for (int q = 0; q < kEPT; ++q) {
-                u[q] = un[q];
-                wt[q] = wn[q];
-            }
-        }
+        bool wa[kEPT] = {want, false, false, false, false, false, false, false};
+        int32_t va[kEPT] = {v, 0, 0, 0, 0, 0, 0, 0};
+        enqueue_batch<!SSSP>(a, wa, va, nxt, acc);
     }
     flush_acc(a, acc, nxt, !SSSP, s_stat);
 }
 
 template <bool SSSP>
 __global__ void __launch_bounds__(kThreads) trav_push(TravArgs a) {
+
     TravCtlDev* cd = a.ctl;
     if (cd->c.done || cd->c.dir != 0u) return;
     const uint32_t t = cd->c.iter;
@@ -729,6 +754,7 @@ __global__ void reached_kernel(const uint32_t* __restrict__ dist, const int32_t*
 // Workspace layout inside g->work for BFS/SSSP.
 struct TravWork {
     uint32_t* msg[2];
+    uint32_t* ycol;
     uint32_t* bv[3];
     int32_t* q[3][3];
     int2* qc[3];
@@ -748,6 +774,7 @@ TravWork work_layout(gm_graph* g, size_t* total_bytes = nullptr) {
         return r;
     };
     for (int s = 0; s < 2; ++s) w.msg[s] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * n));
+    w.ycol = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * n));
     for (int s = 0; s < 3; ++s) w.bv[s] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * nwords));
     for (int s = 0; s < 3; ++s) {
         w.q[s][0] = nullptr;
@@ -786,6 +813,8 @@ TravArgs make_args(gm_graph* g) {
     a.nwords = (g->n + 31) / 32;
     a.dist = as<uint32_t>(g->state);
     for (int s = 0; s < 2; ++s) a.msg[s] = w.msg[s];
+    a.ycol = w.ycol;
+    a.dc_head = as<uint32_t>(g->dc_head);
     for (int s = 0; s < 3; ++s) {
         a.bv[s] = w.bv[s];
         for (int b = 0; b < 3; ++b) a.q[s][b] = w.q[s][b];
@@ -811,7 +840,7 @@ int push_grid() {
 }
 
 int pull_grid() {
-    static int blocks = grid_for(trav_pull<true>);
+    static int blocks = grid_for(trav_pull_a<true>);
     return blocks;
 }
 
@@ -892,15 +921,21 @@ gm_status build_loop_graph(gm_graph* g, bool sssp) {
     kp.kernelParams = kargs;
     cudaGraphNode_t n0, n1, n2;
     e = cudaGraphAddKernelNode(&n0, body, nullptr, 0, &kp);
+    cudaGraphNode_t n1b;
     if (e == cudaSuccess) {
-        kp.func = sssp ? (void*)trav_pull<true> : (void*)trav_pull<false>;
+        kp.func = sssp ? (void*)trav_pull_a<true> : (void*)trav_pull_a<false>;
         kp.gridDim = dim3((unsigned)pull_grid());
         e = cudaGraphAddKernelNode(&n1, body, &n0, 1, &kp);
     }
     if (e == cudaSuccess) {
+        kp.func = sssp ? (void*)trav_pull_b<true> : (void*)trav_pull_b<false>;
+        kp.gridDim = dim3((unsigned)finalize_grid());
+        e = cudaGraphAddKernelNode(&n1b, body, &n1, 1, &kp);
+    }
+    if (e == cudaSuccess) {
         kp.func = sssp ? (void*)trav_finalize<true> : (void*)trav_finalize<false>;
         kp.gridDim = dim3((unsigned)finalize_grid());
-        e = cudaGraphAddKernelNode(&n2, body, &n1, 1, &kp);
+        e = cudaGraphAddKernelNode(&n2, body, &n1b, 1, &kp);
     }
     cudaGraphExec_t exec = nullptr;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
@@ -995,10 +1030,12 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
             // both are launched; the one not matching the device-side direction returns at once
             if (sssp) trav_push<true><<<pg, kThreads, 0, s>>>(a);
             else trav_push<false><<<pg, kThreads, 0, s>>>(a);
-            if (sssp) trav_pull<true><<<lg, kThreads, 0, s>>>(a);
-            else trav_pull<false><<<lg, kThreads, 0, s>>>(a);
+            if (sssp) trav_pull_a<true><<<lg, kThreads, 0, s>>>(a);
+            else trav_pull_a<false><<<lg, kThreads, 0, s>>>(a);
+            if (sssp) trav_pull_b<true><<<fg, kThreads, 0, s>>>(a);
+            else trav_pull_b<false><<<fg, kThreads, 0, s>>>(a);
             if (ev1) cudaEventRecord(ev1, s);
-            g_launches += 2;
+            g_launches += 3;
             LAUNCH_OK();
             if (sssp) trav_finalize<true><<<fg, kThreads, 0, s>>>(a);
             else trav_finalize<false><<<fg, kThreads, 0, s>>>(a);
@@ -1031,7 +1068,7 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
     }
     GM_CUDA_TRY(cudaMemcpyAsync(hp, g->ctl_buf.p, sizeof(TravCtlDev), cudaMemcpyDeviceToHost, s));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
-    if (!host_loop) g_launches += 3ull * hp->c.iters_done;
+    if (!host_loop) g_launches += 4ull * hp->c.iters_done;
     g->stats.supersteps = (int32_t)hp->c.iters_done;
     g->stats.pushes = (int32_t)hp->c.pushes;
     g->stats.pulls = (int32_t)hp->c.pulls;
