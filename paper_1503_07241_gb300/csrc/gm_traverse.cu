@@ -965,6 +965,8 @@ gm_status trav_prepare(gm_graph* g) {
     fill_u32<<<num_sms() * 4, 256, 0, s>>>(as<uint32_t>(g->state), g->n, kInf);
     g_launches++;
     LAUNCH_OK();
+    // per-column pull results start at infinity; pull_b restores that after every use
+    GM_CUDA_TRY(cudaMemsetAsync(work_layout(g).ycol, 0xFF, sizeof(uint32_t) * n, s));
     return reset_frontier(g);
 }
 
