@@ -193,6 +193,25 @@ GM_API gm_status gm_get_scalar(gm_graph* g, int32_t which, void* out);
  */
 GM_API gm_status gm_get_trace(gm_graph* g, double* rows, int32_t max_rows, int32_t* n_rows);
 
+/*
+ * Differentiable weighted PageRank (an added form with no counterpart in the paper's
+ * programs): Eq. 1 with learnable edge weights w normalised per source row,
+ *   P_uv = w_uv / sum_v' w_uv',  x^0 = 1,  x^{t+1}_v = r + (1 - r) sum_{u->v} P_uv x^t_u.
+ * gm_wpagerank_forward runs `steps` supersteps and writes x^steps; it keeps x^t
+ * every `ckpt_every` supersteps (and the normalised weights) inside the handle.
+ * gm_wpagerank_backward takes dL/dx^steps and writes dL/dw for the same w: a
+ * reverse SpMV over the out-edges per superstep plus an edge-gradient
+ * accumulation, recomputing each checkpoint segment, then the chain rule of the
+ * row normalisation.
+ *   w, dLdw   float[m] in the CSR edge order of gm_graph_get_edges, device memory;
+ *             weights must be positive.
+ *   x, dLdx   float[n], device memory.
+ * The graph's own edge values are not used.  Calls synchronise the stream.
+ */
+GM_API gm_status gm_wpagerank_forward(gm_graph* g, const float* w, double r, int32_t steps, int32_t ckpt_every,
+                                      float* x_out);
+GM_API gm_status gm_wpagerank_backward(gm_graph* g, const float* dLdx, float* dLdw);
+
 /* Engine options (not program parameters). */
 enum {
     GM_OPT_DIRECTION = 1,     /* 0 auto push/pull switch (default), 1 push only, 2 pull only */

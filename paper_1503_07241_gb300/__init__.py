@@ -72,6 +72,8 @@ SIGNATURES = {
     "gm_get_scalar": ([_P, _I32, _P], ctypes.c_int),
     "gm_set_option": ([_P, _I32, _I64], ctypes.c_int),
     "gm_get_trace": ([_P, _P, _I32, ctypes.POINTER(_I32)], ctypes.c_int),
+    "gm_wpagerank_forward": ([_P, _P, ctypes.c_double, _I32, _I32, _P], ctypes.c_int),
+    "gm_wpagerank_backward": ([_P, _P, _P], ctypes.c_int),
     "gm_kernel_launch_count": ([], _U64),
     "gm_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "gm_last_error": ([], ctypes.c_char_p),
@@ -254,6 +256,21 @@ class Graph:
         if k.value:
             _check(lib().gm_get_trace(self._h, rows.ctypes.data, k.value, ctypes.byref(k)), "gm_get_trace")
         return rows
+
+    # -- weighted PageRank (device tensors) --------------------------------
+    def wpagerank_forward(self, w, r=0.15, steps=30, ckpt_every=5):
+        import torch
+        x = torch.empty(self.n, dtype=torch.float32, device=w.device)
+        _check(lib().gm_wpagerank_forward(self._h, w.data_ptr(), r, steps, ckpt_every, x.data_ptr()),
+               "gm_wpagerank_forward")
+        return x
+
+    def wpagerank_backward(self, dLdx):
+        import torch
+        g = torch.empty(self.m, dtype=torch.float32, device=dLdx.device)
+        _check(lib().gm_wpagerank_backward(self._h, dLdx.contiguous().data_ptr(), g.data_ptr()),
+               "gm_wpagerank_backward")
+        return g
 
     def set_option(self, option, value):
         _check(lib().gm_set_option(self._h, option, int(value)), "gm_set_option")

@@ -194,7 +194,44 @@ int bits_for(int64_t n) {
 
 }  // namespace
 
-// Rebuild degree bins and the binned in-degree vertex list for the current thresholds.
+// Compact the vertices of each degree bin 1..3 (consecutive in `list`, offsets in
+// off[0..3]) and the degree-0 vertices (into `zero`, count in *zero_count).
+static gm_status bin_lists(gm_graph* g, const uint8_t* bins, int32_t* list, int64_t* off, int32_t* zero,
+                           int64_t* zero_count) {
+    cudaStream_t s = g->stream;
+    const int64_t n = g->n;
+    DevBuf flags, cnt;
+    GM_TRY(dev_alloc(flags, sizeof(uint32_t) * (n > 0 ? n : 1), s));
+    gm_status st = dev_alloc(cnt, sizeof(uint32_t) * 4, s);
+    uint32_t hc[4] = {0, 0, 0, 0};
+    int64_t pos = 0;
+    for (int bin = 0; bin <= 3 && st == GM_OK; ++bin) {
+        if (n > 0) {
+            bin_match_flags<<<blocks_for(n), 256, 0, s>>>(bins, n, (uint8_t)bin, as<uint32_t>(flags));
+            g_launches++;
+        }
+        int32_t* dst = bin == 0 ? zero : list + pos;
+        st = compact_indices(as<uint32_t>(flags), n, dst, as<uint32_t>(cnt) + bin, s);
+        if (st != GM_OK) break;
+        cudaError_t e = cudaMemcpyAsync(&hc[bin], as<uint32_t>(cnt) + bin, sizeof(uint32_t),
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { set_error("bins: %s", cudaGetErrorString(e)); st = GM_ERR_CUDA; break; }
+        if (bin > 0) pos += hc[bin];
+    }
+    dev_free(flags, s);
+    dev_free(cnt, s);
+    if (st != GM_OK) return st;
+    *zero_count = hc[0];
+    off[0] = 0;
+    off[1] = hc[1];
+    off[2] = hc[1] + hc[2];
+    off[3] = hc[1] + hc[2] + hc[3];
+    return GM_OK;
+}
+
+// Rebuild degree bins and the binned vertex lists (by in-degree for pull-side
+// passes over the CSC, by out-degree for passes over the CSR rows).
 gm_status build_bins(gm_graph* g) {
     cudaStream_t s = g->stream;
     const int64_t n = g->n;
@@ -208,54 +245,12 @@ gm_status build_bins(gm_graph* g) {
     }
     GM_TRY(dev_alloc(g->in_list, sizeof(int32_t) * (n > 0 ? n : 1), s));
     GM_TRY(dev_alloc(g->zero_in_list, sizeof(int32_t) * (n > 0 ? n : 1), s));
-    DevBuf flags, cnt;
-    GM_TRY(dev_alloc(flags, sizeof(uint32_t) * (n > 0 ? n : 1), s));
-    gm_status st = dev_alloc(cnt, sizeof(uint32_t) * 4, s);
-    uint32_t hc[4] = {0, 0, 0, 0};
-    int64_t off = 0;
-    for (int bin = 0; bin <= 3 && st == GM_OK; ++bin) {
-        if (n > 0) {
-            bin_match_flags<<<blocks_for(n), 256, 0, s>>>(as<uint8_t>(g->in_bin), n, (uint8_t)bin,
-                                                          as<uint32_t>(flags));
-            g_launches++;
-        }
-        int32_t* dst = bin == 0 ? as<int32_t>(g->zero_in_list) : as<int32_t>(g->in_list) + off;
-        st = compact_indices(as<uint32_t>(flags), n, dst, as<uint32_t>(cnt) + bin, s);
-        if (st != GM_OK) break;
-        cudaError_t e = cudaMemcpyAsync(&hc[bin], as<uint32_t>(cnt) + bin, sizeof(uint32_t),
-                                        cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) { set_error("bins: %s", cudaGetErrorString(e)); st = GM_ERR_CUDA; break; }
-        if (bin > 0) off += hc[bin];
-    }
-    dev_free(flags, s);
-    dev_free(cnt, s);
-    if (st != GM_OK) return st;
-    g->zero_in_count = hc[0];
-    g->in_list_count[0] = 0;
-    g->in_list_count[1] = hc[1];
-    g->in_list_count[2] = hc[1] + hc[2];
-    g->in_list_count[3] = hc[1] + hc[2] + hc[3];
-    // Static work items of the pull side for large in-degree vertices: one
-    // (vertex, chunk) pair per kChunk in-edges, so a hub is spread over CTAs.
-    std::vector<int32_t> big(hc[3]);
-    std::vector<int2> items;
-    if (hc[3] > 0) {
-        GM_CUDA_TRY(cudaMemcpyAsync(big.data(), as<int32_t>(g->in_list) + g->in_list_count[2],
-                                    sizeof(int32_t) * hc[3], cudaMemcpyDeviceToHost, s));
-        std::vector<int32_t> indeg((size_t)n);
-        GM_CUDA_TRY(cudaMemcpyAsync(indeg.data(), g->in_deg.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
-        GM_CUDA_TRY(cudaStreamSynchronize(s));
-        for (size_t i = 0; i < big.size(); ++i) {
-            const int32_t d = indeg[(size_t)big[i]];
-            for (int32_t c = 0; (int64_t)c * kChunk < d; ++c) items.push_back(make_int2(big[i], c));
-        }
-    }
-    g->n_in_chunks = (int64_t)items.size();
-    GM_TRY(dev_alloc(g->in_chunks, sizeof(int2) * (items.size() + 1), s));
-    if (!items.empty())
-        GM_CUDA_TRY(cudaMemcpyAsync(g->in_chunks.p, items.data(), sizeof(int2) * items.size(),
-                                    cudaMemcpyHostToDevice, s));
+    GM_TRY(dev_alloc(g->out_list, sizeof(int32_t) * (n > 0 ? n : 1), s));
+    GM_TRY(dev_alloc(g->zero_out_list, sizeof(int32_t) * (n > 0 ? n : 1), s));
+    GM_TRY(bin_lists(g, as<uint8_t>(g->in_bin), as<int32_t>(g->in_list), g->in_list_count,
+                     as<int32_t>(g->zero_in_list), &g->zero_in_count));
+    GM_TRY(bin_lists(g, as<uint8_t>(g->out_bin), as<int32_t>(g->out_list), g->out_list_count,
+                     as<int32_t>(g->zero_out_list), &g->zero_out_count));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
     return GM_OK;
 }
@@ -610,9 +605,10 @@ gm_status expand_rows(const int32_t* ptr, int64_t n, int32_t* out, cudaStream_t 
 void release_graph(gm_graph* g) {
     cudaStream_t s = g->stream;
     trav_release(g);
+    wpr_release(g);
     DevBuf* bufs[] = {&g->row_ptr, &g->col, &g->w, &g->col_ptr, &g->row, &g->cw, &g->csc_pos,
                       &g->out_deg, &g->in_deg, &g->out_bin, &g->in_bin, &g->in_list, &g->zero_in_list,
-                      &g->in_chunks, &g->dc_jc, &g->dc_cp, &g->dc_tile, &g->dc_head,
+                      &g->out_list, &g->zero_out_list, &g->dc_jc, &g->dc_cp, &g->dc_tile, &g->dc_head,
                       &g->state, &g->work, &g->ctl_buf};
     for (DevBuf* b : bufs) dev_free(*b, s);
     if (g->host_pinned) cudaFreeHost(g->host_pinned);

@@ -125,8 +125,10 @@ struct gm_graph {
     gm::DevBuf out_bin, in_bin;      // uint8 bin of each vertex by out/in degree (0 = degree zero)
     gm::DevBuf in_list;              // vertex ids with in_deg > 0, grouped by in-degree bin
     int64_t in_list_count[gm::kNumBins + 1] = {0};  // offsets of bins 1..3 inside in_list
-    gm::DevBuf in_chunks;            // int2 (vertex, chunk) items covering the in-edges of large-bin vertices
-    int64_t n_in_chunks = 0;
+    gm::DevBuf out_list;             // vertex ids with out_deg > 0, grouped by out-degree bin
+    int64_t out_list_count[gm::kNumBins + 1] = {0};
+    gm::DevBuf zero_out_list;        // vertex ids with out_deg == 0
+    int64_t zero_out_count = 0;
     // Doubly compressed CSC (Section 4.3.1's DCSC): non-empty columns only, and the
     // column holding the first edge of every kWTile-edge tile of the in-edge array.
     gm::DevBuf dc_jc;                // vertex id of each non-empty column (ascending)
@@ -155,6 +157,7 @@ struct gm_graph {
     uint64_t loop_graph_kernels = 0;
     // results
     uint64_t tc_total = 0;
+    void* wpr = nullptr;             // weighted-PageRank buffers (gm_wpr.cu)
 };
 
 namespace gm {
@@ -170,6 +173,7 @@ gm_status cf_prepare(gm_graph* g);
 gm_status cf_run(gm_graph* g, int32_t iters, int32_t* iters_done);
 gm_status cf_loss(gm_graph* g, double* out);
 gm_status reached_edges(gm_graph* g, int64_t* out);
+void wpr_release(gm_graph* g);
 // Per-edge source ids of a CSR (out[e] = v for e in [ptr[v], ptr[v+1])).
 gm_status expand_rows(const int32_t* ptr, int64_t n, int32_t* out, cudaStream_t s);
 }  // namespace gm

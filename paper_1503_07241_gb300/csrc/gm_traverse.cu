@@ -53,7 +53,6 @@ struct TravArgs {
     const int32_t* col_ptr; const int32_t* row; const uint32_t* cw;
     const int32_t* out_deg; const int32_t* in_deg; const uint8_t* out_bin;
     const int32_t* in_list; int64_t in_s0, in_s1, in_m1;  // small bin [in_s0, in_s1), medium [in_s1, in_m1)
-    const int2* in_chunks; int64_t n_in_chunks;          // large in-degree vertices as (vertex, chunk)
     const int32_t* dc_jc; const int32_t* dc_cp; const int32_t* dc_tile;  // doubly compressed CSC + tiles
     int64_t dc_ncols, ntiles;
     int64_t n, m, nwords;
@@ -801,8 +800,6 @@ TravArgs make_args(gm_graph* g) {
     a.in_s0 = g->in_list_count[0];
     a.in_s1 = g->in_list_count[1];
     a.in_m1 = g->in_list_count[2];
-    a.in_chunks = as<int2>(g->in_chunks);
-    a.n_in_chunks = g->n_in_chunks;
     a.dc_jc = as<int32_t>(g->dc_jc);
     a.dc_cp = as<int32_t>(g->dc_cp);
     a.dc_tile = as<int32_t>(g->dc_tile);
