@@ -68,6 +68,7 @@ def _load():
         "or_cf_init": ([u64, i64, f64, P], None),
         "or_cf_loss": ([P, i32, f64, P], f64),
         "or_cf_gd": ([P, i32, f64, f64, i64, P, P], i64),
+        "or_cf_vertex_step": ([P, i32, f64, f64, P, i64, P], None),
         "or_wpr_forward": ([P, P, f64, i64, P, P], f64),
         "or_wpr_gradient": ([P, P, f64, i64, P, P], f64),
     }
@@ -159,6 +160,12 @@ class Graph:
         trace = np.empty(iters + 1, np.float64)
         _load().or_cf_gd(self._h, K, lam, gamma, iters, _p(p), _p(trace))
         return p, trace
+
+    def cf_vertex_step(self, K, lam, gamma, p, v):
+        p = np.ascontiguousarray(p, dtype=np.float64)
+        out = np.empty(K, np.float64)
+        _load().or_cf_vertex_step(self._h, K, lam, gamma, _p(p), v, _p(out))
+        return out
 
     def cf_loss(self, K, lam, p):
         p = np.ascontiguousarray(p, dtype=np.float64)

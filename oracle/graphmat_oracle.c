@@ -443,6 +443,27 @@ OR_EXPORT int64_t or_cf_gd(const or_graph* G, int32_t K, double lambda, double g
     return iters;
 }
 
+/* One Jacobi step of Eqs. 3-5 for a single vertex v from factors p (n*K):
+ * out[k] = p_v[k] + gamma (sum over ratings of v of e p_other[k] - lambda p_v[k]),
+ * where v is the user (source) or the item (destination) of each rating.
+ * Scans all ratings, so it is meant for a few sampled vertices of a large graph. */
+OR_EXPORT void or_cf_vertex_step(const or_graph* G, int32_t K, double lambda, double gamma, const double* p,
+                                 int64_t v, double* out) {
+    for (int32_t k = 0; k < K; ++k) out[k] = 0.0;
+    for (int64_t e = 0; e < G->m; ++e) {
+        int64_t u = G->src[e], w = G->dst[e];
+        if (u != v && w != v) continue;
+        const double* pu = p + u * K;
+        const double* pw = p + w * K;
+        double dot = 0.0;
+        for (int32_t k = 0; k < K; ++k) dot += pu[k] * pw[k];
+        double err = G->val[e] - dot;
+        const double* other = (u == v) ? pw : pu;
+        for (int32_t k = 0; k < K; ++k) out[k] += err * other[k];
+    }
+    for (int32_t k = 0; k < K; ++k) out[k] = p[v * K + k] + gamma * (out[k] - lambda * p[v * K + k]);
+}
+
 /* ---- Weighted PageRank (added form) ----
  * x^{t+1}_v = r + (1-r) sum_{u->v} P_uv x^t_u,  P_uv = w_uv / S_u,  S_u = sum_v w_uv,
  * x^0 = 1, loss L = sum_v (x^T_v - tau_v)^2.  `w` is per edge in the graph's

@@ -72,15 +72,28 @@ gm_status gm_program_set(gm_graph* g, int32_t kind, const gm_program_params* par
         case GM_SSSP:
             break;
         case GM_TRIANGLE_COUNT:
+            break;
         case GM_CF:
-            set_error("gm_program_set: program %d is not available in this build", kind);
-            return GM_ERR_UNSUPPORTED;
+            if (g->n_left <= 0 || g->n_left >= g->n) {
+                set_error("gm_program_set: CF needs a bipartite graph with 0 < n_left < n");
+                return GM_ERR_INVALID_ARG;
+            }
+            if (g->wtype != GM_W_U32) {
+                set_error("gm_program_set: CF needs uint32 ratings as edge values");
+                return GM_ERR_INVALID_ARG;
+            }
+            if (p.K < 1 || p.K > 64 || !(p.gamma >= 0.0) || !(p.lambda >= 0.0) || !(p.init_sigma >= 0.0)) {
+                set_error("gm_program_set: CF needs 1 <= K <= 64 and non-negative gamma, lambda, init_sigma");
+                return GM_ERR_INVALID_ARG;
+            }
+            break;
         default:
             set_error("gm_program_set: unknown program kind %d", kind);
             return GM_ERR_INVALID_ARG;
     }
     GM_TRY(ensure_pinned(g));
     trav_release(g);
+    cf_release(g);
     dev_free(g->state, g->stream);
     dev_free(g->work, g->stream);
     g->kind = kind;
@@ -92,6 +105,15 @@ gm_status gm_program_set(gm_graph* g, int32_t kind, const gm_program_params* par
         if (st == GM_OK) st = trav_prepare(g);
     } else if (kind == GM_PAGERANK) {
         st = pr_prepare(g);
+    } else if (kind == GM_TRIANGLE_COUNT) {
+        g->tc_total = 0;
+        st = dev_alloc(g->state, sizeof(uint64_t) * (g->n > 0 ? g->n : 1), g->stream);
+        if (st == GM_OK && g->n > 0) {
+            cudaError_t e = cudaMemsetAsync(g->state.p, 0, sizeof(uint64_t) * g->n, g->stream);
+            if (e != cudaSuccess) { set_error("gm_program_set: %s", cudaGetErrorString(e)); st = GM_ERR_CUDA; }
+        }
+    } else if (kind == GM_CF) {
+        st = cf_prepare(g);
     }
     if (st != GM_OK) { g->kind = -1; return st; }
     GM_CUDA_TRY(cudaStreamSynchronize(g->stream));
@@ -132,6 +154,8 @@ gm_status gm_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
         case GM_BFS:
         case GM_SSSP: return trav_run(g, max_iters, iters_done);
         case GM_PAGERANK: return pr_run(g, max_iters, iters_done);
+        case GM_TRIANGLE_COUNT: return tc_run(g, iters_done);
+        case GM_CF: return cf_run(g, max_iters, iters_done);
         default: break;
     }
     set_error("gm_run: program not available");
@@ -176,8 +200,8 @@ gm_status gm_get_scalar(gm_graph* g, int32_t which, void* out) {
             *static_cast<uint64_t*>(out) = g->tc_total;
             return GM_OK;
         case GM_SCALAR_CF_LOSS:
-            set_error("gm_get_scalar: CF not available");
-            return GM_ERR_STATE;
+            if (g->kind != GM_CF) { set_error("gm_get_scalar: not a CF program"); return GM_ERR_STATE; }
+            return cf_loss(g, static_cast<double*>(out));
         case GM_SCALAR_REACHED_EDGES:
             if (g->kind != GM_BFS && g->kind != GM_SSSP) { set_error("gm_get_scalar: not a traversal program"); return GM_ERR_STATE; }
             return reached_edges(g, static_cast<int64_t*>(out));

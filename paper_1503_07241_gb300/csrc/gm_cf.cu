@@ -1,0 +1,301 @@
+// Collaborative filtering by full-batch gradient descent (Section 3.III, Eqs. 2-5).
+//
+// Users are vertices [0, n_left), items [n_left, n); every rating is an edge
+// user -> item with its value G_uv.  One superstep (Jacobi, all factors of step t):
+//   e_uv  = G_uv - p_u . p_v                                   (Eq. 3)
+//   p_u  <- p_u + gamma [ sum_v e_uv p_v - lambda p_u ]         (Eq. 4)
+//   p_v  <- p_v + gamma [ sum_u e_uv p_u - lambda p_v ]         (Eq. 5)
+// As vertex programs: every vertex sends its factor vector, Process_Message
+// computes e_uv from the message, the rating and the receiver's own factors
+// (the destination-property access Section 4.2 highlights), Reduce sums, and
+// Apply takes the gradient step.
+//
+// Kernels: a user pass over the CSR (one warp per chunk of <= 512 ratings of a
+// user, the K factor components across the lanes, dot products by warp shuffle)
+// computes and stores e_uv and accumulates sum_v e_uv p_v; an item pass over the
+// CSC gathers the stored e_uv and accumulates sum_u e_uv p_u; an update kernel
+// applies Eqs. 4-5 to every vertex.  Chunks of one long row are combined with
+// float atomics.  Arithmetic in FP32 on CUDA cores: every product is one
+// K-wide dot product per rating, not a dense tile.
+#include <algorithm>
+#include <vector>
+
+#include "gm_internal.cuh"
+
+namespace gm {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr int kCfChunk = 512;
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Counter-based normal draws for the initial factors: SplitMix64 (Steele, Lea
+// and Flood, OOPSLA 2014) gives two 53-bit uniforms per value, combined by the
+// Box-Muller transform (cosine branch), value index i = vertex * K + k.
+__device__ __forceinline__ uint64_t sm_mix(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__global__ void cf_init(float* __restrict__ p, int64_t count, uint64_t seed, double sigma) {
+    const uint64_t key = sm_mix(seed ^ sm_mix(9ULL * 0xD1B54A32D192ED03ULL));
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t w1 = sm_mix(key ^ ((uint64_t)(2 * i) * 0x9E3779B97F4A7C15ULL));
+        const uint64_t w2 = sm_mix(key ^ ((uint64_t)(2 * i + 1) * 0x9E3779B97F4A7C15ULL));
+        const double u1 = ((double)(w1 >> 11) + 1.0) * (1.0 / 9007199254740992.0);
+        const double u2 = (double)(w2 >> 11) * (1.0 / 9007199254740992.0);
+        p[i] = (float)(sigma * sqrt(-2.0 * log(u1)) * cos(2.0 * 3.14159265358979323846 * u2));
+    }
+}
+
+// KP = factor components per lane (K <= 32 * KP).
+template <int KP>
+__global__ void __launch_bounds__(kThreads) cf_user_pass(const int4* __restrict__ chunks, int64_t nchunks,
+                                                         const int32_t* __restrict__ col,
+                                                         const uint32_t* __restrict__ rating,
+                                                         const float* __restrict__ p, int K,
+                                                         float* __restrict__ ebuf, float* __restrict__ acc,
+                                                         double* __restrict__ sq_err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+    double sq = 0.0;
+    for (int64_t c = gwarp; c < nchunks; c += nwarps) {
+        const int4 ch = chunks[c];
+        const int32_t u = ch.x;
+        float pu[KP], ac[KP];
+#pragma unroll
+        for (int j = 0; j < KP; ++j) {
+            const int k = lane + 32 * j;
+            pu[j] = k < K ? p[(int64_t)u * K + k] : 0.0f;
+            ac[j] = 0.0f;
+        }
+        for (int32_t e = ch.y; e < ch.z; ++e) {
+            const int32_t v = __ldg(col + e);
+            float pv[KP];
+            float part = 0.0f;
+#pragma unroll
+            for (int j = 0; j < KP; ++j) {
+                const int k = lane + 32 * j;
+                pv[j] = k < K ? __ldg(p + (int64_t)v * K + k) : 0.0f;
+                part += pu[j] * pv[j];
+            }
+            const float err = (float)__ldg(rating + e) - warp_sum_f(part);
+#pragma unroll
+            for (int j = 0; j < KP; ++j) ac[j] += err * pv[j];
+            if (lane == 0) {
+                if (ebuf) ebuf[e] = err;
+                sq += (double)err * (double)err;
+            }
+        }
+        if (acc) {
+#pragma unroll
+            for (int j = 0; j < KP; ++j) {
+                const int k = lane + 32 * j;
+                if (k < K) atomicAdd(&acc[(int64_t)u * K + k], ac[j]);
+            }
+        }
+    }
+    if (sq_err && lane == 0 && sq != 0.0) atomicAdd(sq_err, sq);
+}
+
+template <int KP>
+__global__ void __launch_bounds__(kThreads) cf_item_pass(const int4* __restrict__ chunks, int64_t nchunks,
+                                                         const int32_t* __restrict__ row,
+                                                         const uint32_t* __restrict__ csc_pos,
+                                                         const float* __restrict__ ebuf,
+                                                         const float* __restrict__ p, int K,
+                                                         float* __restrict__ acc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+    for (int64_t c = gwarp; c < nchunks; c += nwarps) {
+        const int4 ch = chunks[c];
+        const int32_t v = ch.x;
+        float ac[KP];
+#pragma unroll
+        for (int j = 0; j < KP; ++j) ac[j] = 0.0f;
+        for (int32_t q = ch.y; q < ch.z; ++q) {
+            const int32_t u = __ldg(row + q);
+            const float err = __ldg(ebuf + __ldg(csc_pos + q));
+#pragma unroll
+            for (int j = 0; j < KP; ++j) {
+                const int k = lane + 32 * j;
+                if (k < K) ac[j] += err * __ldg(p + (int64_t)u * K + k);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < KP; ++j) {
+            const int k = lane + 32 * j;
+            if (k < K) atomicAdd(&acc[(int64_t)v * K + k], ac[j]);
+        }
+    }
+}
+
+// p <- p + gamma (acc - lambda p); acc <- 0
+__global__ void cf_update(float* __restrict__ p, float* __restrict__ acc, int64_t count, float gamma, float lambda) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = p[i];
+        p[i] = x + gamma * (acc[i] - lambda * x);
+        acc[i] = 0.0f;
+    }
+}
+
+__global__ void sum_squares(const float* __restrict__ p, int64_t count, double* __restrict__ out) {
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        s += (double)p[i] * (double)p[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(out, s);
+}
+
+// Work items (row, first edge, end edge, 0) of at most kCfChunk edges per row.
+std::vector<int4> make_chunks(const std::vector<int32_t>& ptr, int64_t r0, int64_t r1) {
+    std::vector<int4> out;
+    for (int64_t r = r0; r < r1; ++r)
+        for (int32_t e = ptr[r]; e < ptr[r + 1]; e += kCfChunk)
+            out.push_back(make_int4((int32_t)r, e, std::min(ptr[r + 1], e + kCfChunk), 0));
+    return out;
+}
+
+struct CfState {
+    DevBuf user_chunks, item_chunks, ebuf, acc, scalar;
+    int64_t n_user_chunks = 0, n_item_chunks = 0;
+};
+
+int grid_cf() { return num_sms() * 8; }
+
+template <typename F>
+gm_status by_kp(int K, F f) {
+    if (K <= 32) return f(std::integral_constant<int, 1>());
+    return f(std::integral_constant<int, 2>());
+}
+
+}  // namespace
+
+void cf_release(gm_graph* g) {
+    CfState* c = static_cast<CfState*>(g->cf);
+    if (!c) return;
+    DevBuf* bufs[] = {&c->user_chunks, &c->item_chunks, &c->ebuf, &c->acc, &c->scalar};
+    for (DevBuf* b : bufs) dev_free(*b, g->stream);
+    delete c;
+    g->cf = nullptr;
+}
+
+gm_status cf_prepare(gm_graph* g) {
+    cudaStream_t s = g->stream;
+    const int K = g->params.K;
+    const int64_t n = g->n;
+    cf_release(g);
+    CfState* c = new (std::nothrow) CfState();
+    if (!c) { set_error("cf: host allocation failed"); return GM_ERR_OUT_OF_MEMORY; }
+    g->cf = c;
+    std::vector<int32_t> rp((size_t)n + 1), cp((size_t)n + 1);
+    GM_CUDA_TRY(cudaMemcpyAsync(rp.data(), g->row_ptr.p, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+    GM_CUDA_TRY(cudaMemcpyAsync(cp.data(), g->col_ptr.p, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+    GM_CUDA_TRY(cudaStreamSynchronize(s));
+    const std::vector<int4> uc = make_chunks(rp, 0, g->n_left);
+    const std::vector<int4> ic = make_chunks(cp, g->n_left, n);
+    c->n_user_chunks = (int64_t)uc.size();
+    c->n_item_chunks = (int64_t)ic.size();
+    GM_TRY(dev_alloc(c->user_chunks, sizeof(int4) * (uc.size() + 1), s));
+    GM_TRY(dev_alloc(c->item_chunks, sizeof(int4) * (ic.size() + 1), s));
+    if (!uc.empty())
+        GM_CUDA_TRY(cudaMemcpyAsync(c->user_chunks.p, uc.data(), sizeof(int4) * uc.size(), cudaMemcpyHostToDevice, s));
+    if (!ic.empty())
+        GM_CUDA_TRY(cudaMemcpyAsync(c->item_chunks.p, ic.data(), sizeof(int4) * ic.size(), cudaMemcpyHostToDevice, s));
+    GM_TRY(dev_alloc(c->ebuf, sizeof(float) * (g->m > 0 ? g->m : 1), s));
+    GM_TRY(dev_alloc(c->acc, sizeof(float) * (n > 0 ? n : 1) * K, s));
+    GM_TRY(dev_alloc(c->scalar, sizeof(double) * 2, s));
+    GM_CUDA_TRY(cudaMemsetAsync(c->acc.p, 0, sizeof(float) * (n > 0 ? n : 1) * K, s));
+    GM_TRY(dev_alloc(g->state, sizeof(float) * (n > 0 ? n : 1) * K, s));
+    if (n > 0) {
+        cf_init<<<num_sms() * 4, 256, 0, s>>>(as<float>(g->state), n * K, g->params.seed, g->params.init_sigma);
+        g_launches++;
+        GM_CUDA_TRY(cudaGetLastError());
+    }
+    GM_CUDA_TRY(cudaStreamSynchronize(s));
+    return GM_OK;
+}
+
+gm_status cf_run(gm_graph* g, int32_t iters, int32_t* iters_done) {
+    if (iters < 0) {
+        set_error("gm_run: CF runs a fixed number of supersteps; max_iters must be >= 0");
+        return GM_ERR_INVALID_ARG;
+    }
+    CfState* c = static_cast<CfState*>(g->cf);
+    cudaStream_t s = g->stream;
+    const int K = g->params.K;
+    const int64_t nk = g->n * K;
+    float* p = as<float>(g->state);
+    for (int32_t it = 0; it < iters; ++it) {
+        GM_TRY(by_kp(K, [&](auto kp) -> gm_status {
+            constexpr int KP = decltype(kp)::value;
+            if (c->n_user_chunks > 0) {
+                cf_user_pass<KP><<<grid_cf(), kThreads, 0, s>>>(as<int4>(c->user_chunks), c->n_user_chunks,
+                                                                 as<int32_t>(g->col), as<uint32_t>(g->w), p, K,
+                                                                 as<float>(c->ebuf), as<float>(c->acc), nullptr);
+                g_launches++;
+            }
+            if (c->n_item_chunks > 0) {
+                cf_item_pass<KP><<<grid_cf(), kThreads, 0, s>>>(as<int4>(c->item_chunks), c->n_item_chunks,
+                                                                 as<int32_t>(g->row), as<uint32_t>(g->csc_pos),
+                                                                 as<float>(c->ebuf), p, K, as<float>(c->acc));
+                g_launches++;
+            }
+            GM_CUDA_TRY(cudaGetLastError());
+            return GM_OK;
+        }));
+        if (nk > 0) {
+            cf_update<<<num_sms() * 8, 256, 0, s>>>(p, as<float>(c->acc), nk, (float)g->params.gamma,
+                                                    (float)g->params.lambda);
+            g_launches++;
+            GM_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    GM_CUDA_TRY(cudaStreamSynchronize(s));
+    g->stats = RunStats{};
+    g->stats.supersteps = iters;
+    if (iters_done) *iters_done = iters;
+    return GM_OK;
+}
+
+// Eq. 2 with the regulariser once per vertex, at the current factors, in FP64 sums.
+gm_status cf_loss(gm_graph* g, double* out) {
+    CfState* c = static_cast<CfState*>(g->cf);
+    cudaStream_t s = g->stream;
+    const int K = g->params.K;
+    double* d = as<double>(c->scalar);
+    GM_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(double) * 2, s));
+    GM_TRY(by_kp(K, [&](auto kp) -> gm_status {
+        constexpr int KP = decltype(kp)::value;
+        if (c->n_user_chunks > 0) {
+            cf_user_pass<KP><<<grid_cf(), kThreads, 0, s>>>(as<int4>(c->user_chunks), c->n_user_chunks,
+                                                             as<int32_t>(g->col), as<uint32_t>(g->w),
+                                                             as<float>(g->state), K, nullptr, nullptr, d);
+            g_launches++;
+        }
+        return GM_OK;
+    }));
+    if (g->n > 0) {
+        sum_squares<<<num_sms() * 4, 256, 0, s>>>(as<float>(g->state), g->n * K, d + 1);
+        g_launches++;
+    }
+    double h[2] = {0.0, 0.0};
+    GM_CUDA_TRY(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GM_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = h[0] + g->params.lambda * h[1];
+    return GM_OK;
+}
+
+}  // namespace gm

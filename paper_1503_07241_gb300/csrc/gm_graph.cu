@@ -606,6 +606,7 @@ void release_graph(gm_graph* g) {
     cudaStream_t s = g->stream;
     trav_release(g);
     wpr_release(g);
+    cf_release(g);
     DevBuf* bufs[] = {&g->row_ptr, &g->col, &g->w, &g->col_ptr, &g->row, &g->cw, &g->csc_pos,
                       &g->out_deg, &g->in_deg, &g->out_bin, &g->in_bin, &g->in_list, &g->zero_in_list,
                       &g->out_list, &g->zero_out_list, &g->dc_jc, &g->dc_cp, &g->dc_tile, &g->dc_head,

@@ -158,6 +158,7 @@ struct gm_graph {
     // results
     uint64_t tc_total = 0;
     void* wpr = nullptr;             // weighted-PageRank buffers (gm_wpr.cu)
+    void* cf = nullptr;              // collaborative-filtering buffers (gm_cf.cu)
 };
 
 namespace gm {
@@ -174,6 +175,7 @@ gm_status cf_run(gm_graph* g, int32_t iters, int32_t* iters_done);
 gm_status cf_loss(gm_graph* g, double* out);
 gm_status reached_edges(gm_graph* g, int64_t* out);
 void wpr_release(gm_graph* g);
+void cf_release(gm_graph* g);
 // Per-edge source ids of a CSR (out[e] = v for e in [ptr[v], ptr[v+1])).
 gm_status expand_rows(const int32_t* ptr, int64_t n, int32_t* out, cudaStream_t s);
 }  // namespace gm

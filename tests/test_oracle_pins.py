@@ -351,6 +351,17 @@ def test_cf_step_is_half_gradient_of_loss():
     np.testing.assert_allclose(step, -0.5 * grad, rtol=1e-6, atol=1e-7)
 
 
+def test_cf_vertex_step_matches_full_step():
+    rng = np.random.default_rng(13)
+    nu, ni, K = 15, 9, 4
+    u, v, r = _bipartite(rng, nu, ni, 80)
+    g = oracle.Graph(nu + ni, u, v, r)
+    p0 = rng.normal(0, 0.3, (nu + ni, K))
+    p1, _ = g.cf_gd(K, 0.05, 0.01, 1, p0)
+    for vert in range(nu + ni):
+        np.testing.assert_allclose(g.cf_vertex_step(K, 0.05, 0.01, p0, vert), p1[vert], rtol=1e-13, atol=1e-15)
+
+
 def test_cf_loss_decreases_at_small_step():
     rng = np.random.default_rng(12)
     nu, ni, K = 60, 20, 8
