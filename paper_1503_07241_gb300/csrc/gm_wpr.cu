@@ -11,11 +11,7 @@
 // for t = T-1 .. 0, recomputing each checkpoint segment's states forward first;
 // then the row-normalisation chain rule dL/dw_uv = (gbar_uv - sum_v' P_uv' gbar_uv') / S_u.
 // Every pass is a row reduction over rows binned by length (32 short rows per
-// warp, a warp per medium row, a CTA per long row), in a fixed order.  Weights
-// come in and ranks and gradients go out in FP32; the recursions run in FP64,
-// because the last step subtracts two nearly equal sums (gbar_uv and its row
-// average), which would amplify FP32 rounding of x and lambda.  The adjoint
-// is memory-bound, and FP64 adds only a few FMAs per edge.
+// warp, a warp per medium row, a CTA per long row), in FP32, in a fixed order.
 #include <algorithm>
 #include <new>
 
@@ -38,7 +34,7 @@ struct RowSet {
     int64_t nzero;
 };
 
-__device__ __forceinline__ double warp_sum_d(double v) {
+__device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
@@ -51,19 +47,19 @@ __global__ void __launch_bounds__(kThreads) row_pass(RowSet rs, F f) {
     const int wid = threadIdx.x >> 5;
     const int64_t gwarp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
-    __shared__ double s_red[kWarps];
-    __shared__ double s_acc[kWarps][32];
+    __shared__ float s_red[kWarps];
+    __shared__ float s_acc[kWarps][32];
     // long rows: one CTA each
     for (int64_t i = rs.off[2] + blockIdx.x; i < rs.off[3]; i += gridDim.x) {
         const int32_t r = rs.list[i];
         const int32_t beg = rs.ptr[r], end = rs.ptr[r + 1];
-        double s = 0.0;
+        float s = 0.0f;
         for (int32_t e = beg + threadIdx.x; e < end; e += kThreads) s += f.edge(r, e);
-        s = warp_sum_d(s);
+        s = warp_sum_f(s);
         if (lane == 0) s_red[wid] = s;
         __syncthreads();
         if (threadIdx.x == 0) {
-            double tot = 0.0;
+            float tot = 0.0f;
             for (int w2 = 0; w2 < kWarps; ++w2) tot += s_red[w2];
             f.finish(r, tot);
         }
@@ -73,13 +69,13 @@ __global__ void __launch_bounds__(kThreads) row_pass(RowSet rs, F f) {
     for (int64_t i = rs.off[1] + gwarp; i < rs.off[2]; i += nwarps) {
         const int32_t r = rs.list[i];
         const int32_t beg = rs.ptr[r], end = rs.ptr[r + 1];
-        double s = 0.0;
+        float s = 0.0f;
         for (int32_t e = beg + lane; e < end; e += 32) s += f.edge(r, e);
-        s = warp_sum_d(s);
+        s = warp_sum_f(s);
         if (lane == 0) f.finish(r, s);
     }
     // short rows: 32 per warp, entries concatenated, segmented sums in a fixed order
-    double* acc = s_acc[wid];
+    float* acc = s_acc[wid];
     for (int64_t g0 = rs.off[0] + gwarp * 32; g0 < rs.off[1]; g0 += nwarps * 32) {
         const int64_t i = g0 + lane;
         int32_t r = 0, beg = 0;
@@ -89,7 +85,7 @@ __global__ void __launch_bounds__(kThreads) row_pass(RowSet rs, F f) {
             beg = rs.ptr[r];
             len = (uint32_t)(rs.ptr[r + 1] - beg);
         }
-        acc[lane] = 0.0;
+        acc[lane] = 0.0f;
         __syncwarp();
         uint32_t incl = len;
 #pragma unroll
@@ -111,11 +107,11 @@ __global__ void __launch_bounds__(kThreads) row_pass(RowSet rs, F f) {
             const uint32_t eo = __shfl_sync(kFull, excl, k);
             const int32_t ro = __shfl_sync(kFull, r, k);
             const bool valid = j < total;
-            double val = valid ? f.edge(ro, bo + (int32_t)(j - eo)) : 0.0;
+            float val = valid ? f.edge(ro, bo + (int32_t)(j - eo)) : 0.0f;
             const int owner = valid ? k : 32 + lane;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {  // inclusive segmented scan by owner
-                const double y = __shfl_up_sync(kFull, val, o);
+                const float y = __shfl_up_sync(kFull, val, o);
                 const int ko = __shfl_up_sync(kFull, owner, o);
                 if (lane >= o && ko == owner) val += y;
             }
@@ -128,67 +124,54 @@ __global__ void __launch_bounds__(kThreads) row_pass(RowSet rs, F f) {
     }
     // rows without entries
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < rs.nzero; i += (int64_t)gridDim.x * kThreads)
-        f.finish(rs.zero[i], 0.0);
+        f.finish(rs.zero[i], 0.0f);
 }
 
 // ---- the passes -------------------------------------------------------------------
 struct RowSumF {  // S_u = sum_e w_e
-    const float* w; double* S;
-    __device__ double edge(int32_t, int32_t e) const { return (double)w[e]; }
-    __device__ void finish(int32_t u, double s) const { S[u] = s; }
+    const float* w; float* S;
+    __device__ float edge(int32_t, int32_t e) const { return w[e]; }
+    __device__ void finish(int32_t u, float s) const { S[u] = s; }
 };
 struct NormalizeF {  // P_e = w_e / S_u (CSR order)
-    const float* w; const double* S; double* P;
-    __device__ double edge(int32_t u, int32_t e) const { P[e] = (double)w[e] / S[u]; return 0.0; }
-    __device__ void finish(int32_t, double) const {}
+    const float* w; const float* S; float* P;
+    __device__ float edge(int32_t u, int32_t e) const { P[e] = w[e] / S[u]; return 0.0f; }
+    __device__ void finish(int32_t, float) const {}
 };
 struct ForwardF {  // x'_v = r + (1-r) sum_{u->v} Pc_q x_u (CSC order)
-    const int32_t* row; const double* Pc; const double* x; double* xn; double r;
-    __device__ double edge(int32_t, int32_t q) const { return Pc[q] * x[row[q]]; }
-    __device__ void finish(int32_t v, double s) const { xn[v] = r + (1.0 - r) * s; }
+    const int32_t* row; const float* Pc; const float* x; float* xn; float r;
+    __device__ float edge(int32_t, int32_t q) const { return Pc[q] * x[row[q]]; }
+    __device__ void finish(int32_t v, float s) const { xn[v] = r + (1.0f - r) * s; }
 };
 struct BackwardF {  // CSR: gbar_e += (1-r) x_u lam_v;  lam'_u = (1-r) sum_e P_e lam_v
-    const int32_t* col; const double* P; const double* x; const double* lam; double* lamn; double* gbar; double r;
-    __device__ double edge(int32_t u, int32_t e) const {
-        const double lv = lam[col[e]];
-        gbar[e] += (1.0 - r) * x[u] * lv;
+    const int32_t* col; const float* P; const float* x; const float* lam; float* lamn; float* gbar; float r;
+    __device__ float edge(int32_t u, int32_t e) const {
+        const float lv = lam[col[e]];
+        gbar[e] += (1.0f - r) * x[u] * lv;
         return P[e] * lv;
     }
-    __device__ void finish(int32_t u, double s) const { lamn[u] = (1.0 - r) * s; }
+    __device__ void finish(int32_t u, float s) const { lamn[u] = (1.0f - r) * s; }
 };
 struct RowDotF {  // d_u = sum_e P_e gbar_e
-    const double* P; const double* gbar; double* d;
-    __device__ double edge(int32_t, int32_t e) const { return P[e] * gbar[e]; }
-    __device__ void finish(int32_t u, double s) const { d[u] = s; }
+    const float* P; const float* gbar; float* d;
+    __device__ float edge(int32_t, int32_t e) const { return P[e] * gbar[e]; }
+    __device__ void finish(int32_t u, float s) const { d[u] = s; }
 };
 struct GradF {  // dL/dw_e = (gbar_e - d_u) / S_u
-    const double* gbar; const double* d; const double* S; float* grad;
-    __device__ double edge(int32_t u, int32_t e) const {
-        grad[e] = (float)((gbar[e] - d[u]) / S[u]);
-        return 0.0;
-    }
-    __device__ void finish(int32_t, double) const {}
+    const float* gbar; const float* d; const float* S; float* grad;
+    __device__ float edge(int32_t u, int32_t e) const { grad[e] = (gbar[e] - d[u]) / S[u]; return 0.0f; }
+    __device__ void finish(int32_t, float) const {}
 };
 
-__global__ void gather_f64(const double* __restrict__ in, const uint32_t* __restrict__ idx, int64_t len,
-                           double* __restrict__ out) {
+__global__ void gather_f32(const float* __restrict__ in, const uint32_t* __restrict__ idx, int64_t len,
+                           float* __restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = in[idx[i]];
 }
 
-__global__ void fill_f64(double* p, int64_t n, double v) {
+__global__ void fill_f32_k(float* p, int64_t n, float v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
-}
-
-__global__ void to_f32(const double* __restrict__ in, int64_t n, float* __restrict__ out) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = (float)in[i];
-}
-
-__global__ void to_f64(const float* __restrict__ in, int64_t n, double* __restrict__ out) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = (double)in[i];
 }
 
 template <class F>
@@ -238,7 +221,7 @@ RowSet csc_rows(const gm_graph* g) {
 struct WprState {
     DevBuf S, P, Pc, gbar, ckpt, seg, lam, d;
     int32_t steps = -1, every = 0;
-    double r = 0.15;
+    float r = 0.15f;
     bool have_forward = false;
 };
 
@@ -251,9 +234,9 @@ void wpr_release(gm_graph* g) {
     g->wpr = nullptr;
 }
 
-// x^{t+1} from x^t (both device double[n]).
-static gm_status wpr_step(gm_graph* g, WprState* w, const double* x, double* xn) {
-    ForwardF f{as<int32_t>(g->row), as<double>(w->Pc), x, xn, w->r};
+// x^{t+1} from x^t (both device float[n]).
+static gm_status wpr_step(gm_graph* g, WprState* w, const float* x, float* xn) {
+    ForwardF f{as<int32_t>(g->row), as<float>(w->Pc), x, xn, w->r};
     return launch_pass(csc_rows(g), f, g->stream);
 }
 
@@ -277,45 +260,43 @@ gm_status gm_wpagerank_forward(gm_graph* g, const float* w_dev, double r, int32_
         w = new (std::nothrow) WprState();
         if (!w) { set_error("gm_wpagerank_forward: host allocation failed"); return GM_ERR_OUT_OF_MEMORY; }
         g->wpr = w;
-        GM_TRY(dev_alloc(w->S, sizeof(double) * n, s));
-        GM_TRY(dev_alloc(w->P, sizeof(double) * m, s));
-        GM_TRY(dev_alloc(w->Pc, sizeof(double) * m, s));
-        GM_TRY(dev_alloc(w->gbar, sizeof(double) * m, s));
-        GM_TRY(dev_alloc(w->lam, sizeof(double) * 2 * n, s));
-        GM_TRY(dev_alloc(w->d, sizeof(double) * n, s));
+        GM_TRY(dev_alloc(w->S, sizeof(float) * n, s));
+        GM_TRY(dev_alloc(w->P, sizeof(float) * m, s));
+        GM_TRY(dev_alloc(w->Pc, sizeof(float) * m, s));
+        GM_TRY(dev_alloc(w->gbar, sizeof(float) * m, s));
+        GM_TRY(dev_alloc(w->lam, sizeof(float) * 2 * n, s));
+        GM_TRY(dev_alloc(w->d, sizeof(float) * n, s));
     }
     const int32_t nck = steps / ckpt_every + 1;
     if (w->every != ckpt_every || w->steps != steps) {
-        GM_TRY(dev_alloc(w->ckpt, sizeof(double) * n * nck, s));
-        GM_TRY(dev_alloc(w->seg, sizeof(double) * n * (ckpt_every + 1), s));
+        GM_TRY(dev_alloc(w->ckpt, sizeof(float) * n * nck, s));
+        GM_TRY(dev_alloc(w->seg, sizeof(float) * n * (ckpt_every + 1), s));
     }
     w->steps = steps;
     w->every = ckpt_every;
-    w->r = r;
+    w->r = (float)r;
     const RowSet rows = csr_rows(g);
-    GM_TRY(launch_pass(rows, RowSumF{w_dev, as<double>(w->S)}, s));
-    GM_TRY(launch_pass(rows, NormalizeF{w_dev, as<double>(w->S), as<double>(w->P)}, s));
+    GM_TRY(launch_pass(rows, RowSumF{w_dev, as<float>(w->S)}, s));
+    GM_TRY(launch_pass(rows, NormalizeF{w_dev, as<float>(w->S), as<float>(w->P)}, s));
     if (g->m > 0) {
-        gather_f64<<<num_sms() * 4, 256, 0, s>>>(as<double>(w->P), as<uint32_t>(g->csc_pos), g->m, as<double>(w->Pc));
+        gather_f32<<<num_sms() * 4, 256, 0, s>>>(as<float>(w->P), as<uint32_t>(g->csc_pos), g->m, as<float>(w->Pc));
         g_launches++;
     }
     // x^0 = 1 is checkpoint 0; two ping-pong vectors live in seg
-    double* ck = as<double>(w->ckpt);
-    fill_f64<<<num_sms() * 4, 256, 0, s>>>(ck, g->n, 1.0);
+    float* ck = as<float>(w->ckpt);
+    fill_f32_k<<<num_sms() * 4, 256, 0, s>>>(ck, g->n, 1.0f);
     g_launches++;
-    double* a = as<double>(w->seg);
-    double* b = a + n;
-    GM_CUDA_TRY(cudaMemcpyAsync(a, ck, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
+    float* a = as<float>(w->seg);
+    float* b = a + n;
+    GM_CUDA_TRY(cudaMemcpyAsync(a, ck, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, s));
     for (int32_t t = 0; t < steps; ++t) {
         GM_TRY(wpr_step(g, w, a, b));
         std::swap(a, b);
         if ((t + 1) % ckpt_every == 0 && (t + 1) / ckpt_every < nck)
-            GM_CUDA_TRY(cudaMemcpyAsync(ck + n * ((t + 1) / ckpt_every), a, sizeof(double) * g->n,
+            GM_CUDA_TRY(cudaMemcpyAsync(ck + n * ((t + 1) / ckpt_every), a, sizeof(float) * g->n,
                                         cudaMemcpyDeviceToDevice, s));
     }
-    to_f32<<<num_sms() * 4, 256, 0, s>>>(a, g->n, x_out_dev);
-    g_launches++;
-    GM_CUDA_TRY(cudaGetLastError());
+    GM_CUDA_TRY(cudaMemcpyAsync(x_out_dev, a, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, s));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
     w->have_forward = true;
     return GM_OK;
@@ -329,25 +310,24 @@ gm_status gm_wpagerank_backward(gm_graph* g, const float* dLdx_dev, float* dLdw_
     const int64_t n = g->n > 0 ? g->n : 1;
     const int32_t T = w->steps, k = w->every;
     const RowSet rows = csr_rows(g);
-    double* lam = as<double>(w->lam);
-    double* lamn = lam + n;
-    to_f64<<<num_sms() * 4, 256, 0, s>>>(dLdx_dev, g->n, lam);
-    g_launches++;
-    if (g->m > 0) GM_CUDA_TRY(cudaMemsetAsync(w->gbar.p, 0, sizeof(double) * g->m, s));
-    double* seg = as<double>(w->seg);
-    const double* ck = as<double>(w->ckpt);
+    float* lam = as<float>(w->lam);
+    float* lamn = lam + n;
+    GM_CUDA_TRY(cudaMemcpyAsync(lam, dLdx_dev, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, s));
+    if (g->m > 0) GM_CUDA_TRY(cudaMemsetAsync(w->gbar.p, 0, sizeof(float) * g->m, s));
+    float* seg = as<float>(w->seg);
+    const float* ck = as<float>(w->ckpt);
     for (int32_t c = ((T - 1) / k) * k; T > 0 && c >= 0; c -= k) {
         const int32_t e = std::min(c + k, T);  // segment holds x^c .. x^{e-1}
-        GM_CUDA_TRY(cudaMemcpyAsync(seg, ck + n * (c / k), sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
+        GM_CUDA_TRY(cudaMemcpyAsync(seg, ck + n * (c / k), sizeof(float) * g->n, cudaMemcpyDeviceToDevice, s));
         for (int32_t t = c; t + 1 < e; ++t) GM_TRY(wpr_step(g, w, seg + n * (t - c), seg + n * (t + 1 - c)));
         for (int32_t t = e - 1; t >= c; --t) {
-            BackwardF f{as<int32_t>(g->col), as<double>(w->P), seg + n * (t - c), lam, lamn, as<double>(w->gbar), w->r};
+            BackwardF f{as<int32_t>(g->col), as<float>(w->P), seg + n * (t - c), lam, lamn, as<float>(w->gbar), w->r};
             GM_TRY(launch_pass(rows, f, s));
             std::swap(lam, lamn);
         }
     }
-    GM_TRY(launch_pass(rows, RowDotF{as<double>(w->P), as<double>(w->gbar), as<double>(w->d)}, s));
-    GM_TRY(launch_pass(rows, GradF{as<double>(w->gbar), as<double>(w->d), as<double>(w->S), dLdw_dev}, s));
+    GM_TRY(launch_pass(rows, RowDotF{as<float>(w->P), as<float>(w->gbar), as<float>(w->d)}, s));
+    GM_TRY(launch_pass(rows, GradF{as<float>(w->gbar), as<float>(w->d), as<float>(w->S), dLdw_dev}, s));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
     return GM_OK;
 }
