@@ -47,7 +47,7 @@ def test_random_graphs(gm, seed):
 @pytest.mark.parametrize("k", [3, 5, 40, 150])
 def test_complete_graph(gm, k):
     pairs = np.array([(a, b) for a in range(k) for b in range(k) if a < b], np.int32)
-    pv, tot = _tc(gm, k, pairs[:, 0], pairs[:, 1])
+    pv, tot = _tc(gm, k, np.ascontiguousarray(pairs[:, 0]), np.ascontiguousarray(pairs[:, 1]))
     assert tot == math.comb(k, 3) and np.all(pv == math.comb(k - 1, 2))
 
 
