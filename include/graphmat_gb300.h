@@ -212,6 +212,39 @@ GM_API gm_status gm_wpagerank_forward(gm_graph* g, const float* w, double r, int
                                       float* x_out);
 GM_API gm_status gm_wpagerank_backward(gm_graph* g, const float* dLdx, float* dLdw);
 
+/*
+ * gm_bfs_csr_noalloc -- BFS over caller-provided CSR arrays that allocates no
+ * memory.  The paper has no counterpart: this is a library convenience for callers
+ * that cannot allocate device memory when they need a traversal, such as code
+ * running while a CUDA stream is being captured (cudaMalloc is not allowed there),
+ * code that manages all device memory through its own arena or caching allocator,
+ * and latency-critical loops that must not pay for cudaMalloc/cudaFree (which can
+ * synchronise the device and can fail under memory pressure).
+ *
+ * The result equals gm_run with GM_BFS from one source on the same edges
+ * (Section 3.II): depth[v] = number of edges on a shortest path from `source`,
+ * UINT32_MAX if unreachable; *iters_done (may be NULL) = supersteps executed,
+ * counting the final one that finds no new vertex.
+ *   n        vertices, 1 <= n <= gm_bfs_csr_noalloc_max_vertices() (1,048,576);
+ *            larger n returns GM_ERR_INVALID_ARG without touching the GPU.
+ *   row_ptr  device int32[n+1], col device int32[row_ptr[n]]: out-edges of each
+ *            vertex; ids in [0, n).  Read only; owned by the caller.
+ *   depth    device uint32[n], written.
+ *   stream   cudaStream_t for all work (NULL = default stream); the call
+ *            synchronises it once per superstep to read the frontier size.
+ * Scratch: two frontier queues and counters live in one fixed device array of
+ * 8 MiB + 256 bytes that each GPU holds until the library is unloaded.  Its
+ * device address is looked up (cudaGetSymbolAddress) on the first call on each
+ * device, with that device current; make that first call before any stream
+ * capture.  Every call shares the array and clears what it needs at the start,
+ * so calls that overlap on the GPU (on different streams or host threads) race
+ * and must not be issued.
+ */
+GM_API gm_status gm_bfs_csr_noalloc(int64_t n, const int32_t* row_ptr, const int32_t* col, int32_t source,
+                                    uint32_t* depth, int32_t* iters_done, void* stream);
+/* The largest n gm_bfs_csr_noalloc accepts (the size of its fixed scratch). */
+GM_API int64_t gm_bfs_csr_noalloc_max_vertices(void);
+
 /* Engine options (not program parameters). */
 enum {
     GM_OPT_DIRECTION = 1,     /* 0 auto push/pull switch (default), 1 push only, 2 pull only */

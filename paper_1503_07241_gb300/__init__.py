@@ -74,6 +74,8 @@ SIGNATURES = {
     "gm_get_trace": ([_P, _P, _I32, ctypes.POINTER(_I32)], ctypes.c_int),
     "gm_wpagerank_forward": ([_P, _P, ctypes.c_double, _I32, _I32, _P], ctypes.c_int),
     "gm_wpagerank_backward": ([_P, _P, _P], ctypes.c_int),
+    "gm_bfs_csr_noalloc": ([_I64, _P, _P, _I32, _P, ctypes.POINTER(_I32), _P], ctypes.c_int),
+    "gm_bfs_csr_noalloc_max_vertices": ([], _I64),
     "gm_kernel_launch_count": ([], _U64),
     "gm_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "gm_last_error": ([], ctypes.c_char_p),
@@ -127,6 +129,16 @@ def _stream_handle(stream):
     if stream is None:
         return None
     return getattr(stream, "cuda_stream", stream)
+
+
+def bfs_csr_noalloc(row_ptr, col, source, depth, stream=None) -> int:
+    """BFS over device CSR tensors into the device uint32 tensor `depth`, with no
+    allocation inside the library (see gm_bfs_csr_noalloc).  Returns supersteps."""
+    it = ctypes.c_int32()
+    n = int(depth.numel())
+    _check(lib().gm_bfs_csr_noalloc(n, row_ptr.data_ptr(), col.data_ptr(), int(source), depth.data_ptr(),
+                                    ctypes.byref(it), _stream_handle(stream)), "gm_bfs_csr_noalloc")
+    return it.value
 
 
 def kernel_launch_count() -> int:
