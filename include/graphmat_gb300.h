@@ -213,6 +213,33 @@ GM_API gm_status gm_wpagerank_forward(gm_graph* g, const float* w, double r, int
 GM_API gm_status gm_wpagerank_backward(gm_graph* g, const float* dLdx, float* dLdw);
 
 /*
+ * gm_run_batch -- many BFS / SSSP queries (an added form: the programs of
+ * Sections 3.II and 3.V) over one or more graphs, in one device-driven superstep
+ * loop.  All queries advance in lockstep supersteps; a device work queue hands
+ * (query, vertex, edge chunk) items of every active query's frontier to the
+ * warps; the loop is one CUDA graph whose conditional node stops when no query
+ * is active.  Each query's result and superstep count equal gm_run's for the
+ * same graph, program and single source.
+ *   graphs     n_graphs handles (their programs and states are not touched).
+ *   queries    n_queries entries: graph index, GM_BFS or GM_SSSP, source vertex.
+ *   out_state  n_queries device pointers, uint32[n of the query's graph] each:
+ *              depth / distance per vertex (UINT32_MAX = unreached).
+ *   max_iters  -1: every query until convergence; k > 0: at most k supersteps.
+ *   iters_done NULL or int32[n_queries] (host): supersteps of each query.
+ *   stream     cudaStream_t (NULL = default); the call synchronises it.
+ * Workspace (messages, queued bits, two item queues per query) is allocated for
+ * the call and released before it returns.
+ */
+typedef struct gm_query {
+    int32_t graph;   /* index into graphs */
+    int32_t kind;    /* GM_BFS or GM_SSSP */
+    int32_t source;  /* source vertex */
+    int32_t reserved;
+} gm_query;
+GM_API gm_status gm_run_batch(gm_graph* const* graphs, int32_t n_graphs, const gm_query* queries, int32_t n_queries,
+                              uint32_t* const* out_state, int32_t max_iters, int32_t* iters_done, void* stream);
+
+/*
  * gm_bfs_csr_noalloc -- BFS over caller-provided CSR arrays that allocates no
  * memory.  The paper has no counterpart: this is a library convenience for callers
  * that cannot allocate device memory when they need a traversal, such as code

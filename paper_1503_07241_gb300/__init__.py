@@ -75,6 +75,7 @@ SIGNATURES = {
     "gm_wpagerank_forward": ([_P, _P, ctypes.c_double, _I32, _I32, _P], ctypes.c_int),
     "gm_wpagerank_backward": ([_P, _P, _P], ctypes.c_int),
     "gm_bfs_csr_noalloc": ([_I64, _P, _P, _I32, _P, ctypes.POINTER(_I32), _P], ctypes.c_int),
+    "gm_run_batch": ([_P, _I32, _P, _I32, _P, _I32, _P, _P], ctypes.c_int),
     "gm_bfs_csr_noalloc_max_vertices": ([], _I64),
     "gm_kernel_launch_count": ([], _U64),
     "gm_status_string": ([ctypes.c_int], ctypes.c_char_p),
@@ -129,6 +130,25 @@ def _stream_handle(stream):
     if stream is None:
         return None
     return getattr(stream, "cuda_stream", stream)
+
+
+class gm_query(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_int32), ("kind", ctypes.c_int32), ("source", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+def run_batch(graphs, queries, outs, max_iters=-1, stream=None):
+    """Run (graph index, kind, source) queries together (gm_run_batch).  `outs`
+    are CUDA uint32/int32 tensors of each query graph's n.  Returns superstep counts."""
+    ng, nq = len(graphs), len(queries)
+    harr = (ctypes.c_void_p * max(ng, 1))(*[g._h.value for g in graphs])
+    qarr = (gm_query * max(nq, 1))(*[gm_query(int(gi), int(k), int(s), 0) for gi, k, s in queries])
+    oarr = (ctypes.c_void_p * max(nq, 1))(*[o.data_ptr() for o in outs])
+    its = (ctypes.c_int32 * max(nq, 1))()
+    _check(lib().gm_run_batch(ctypes.cast(harr, ctypes.c_void_p), ng, ctypes.cast(qarr, ctypes.c_void_p), nq,
+                              ctypes.cast(oarr, ctypes.c_void_p), max_iters, ctypes.cast(its, ctypes.c_void_p),
+                              _stream_handle(stream)), "gm_run_batch")
+    return list(its)[:nq]
 
 
 def bfs_csr_noalloc(row_ptr, col, source, depth, stream=None) -> int:
