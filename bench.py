@@ -4,13 +4,16 @@
 One step = 16 BFS + 16 SSSP queries (uint32 weights in [1, 255]) from seeded
 non-isolated sources, run one at a time through the C ABI on a graph already
 ingested into HBM (ingest is timed separately, as the paper excludes graph
-load).  The metric is GTEPS = sum over queries of the edges of reached vertices
-(Graph500 convention) / time.
+load).  The metric is GTEPS = sum over queries of the out-edges of reached
+vertices (Graph500 convention) / time.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-extras]
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own queries on
-its own GPU (weak scaling, no collective on the data path).
+its own GPU (weak scaling, replicas, no collective on the data path).  After the
+timed region, rank 0 also measures the other workloads (PageRank, the batched
+and the weighted-PageRank forms, triangle counting, CF) and reports them under
+"extras" -- each measured the same way, none inside the timed region.
 """
 from __future__ import annotations
 
@@ -51,15 +54,16 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "",
-                                 f".clocks_{os.getpid()}.csv")
+        d = os.path.join(ROOT, "gpurun_out")
+        self.path = os.path.join(d if os.path.isdir(d) else "/tmp", f".clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
         except Exception:
             self.proc = None
         return self
@@ -92,9 +96,9 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         load = [x for x in sm if x > 0.5 * smax] or sm
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
         return {"sm_mhz": statistics.median(load), "sm_max_mhz": smax, "reasons": reasons,
-                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
-                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+                "samples": len(rows), "power_w_max": max(pw) if pw else None}
 
 
 def make_workload(rank):
@@ -147,7 +151,6 @@ def reference_arm(args):
     import oracle
     og = oracle.Graph(n, s, d, w)
     both = (args.steps + args.warmup) <= 20
-    per = []
     edges_total, t_total = 0, 0.0
     for step in range(args.warmup + args.steps):
         i = step % N_QUERIES
@@ -161,7 +164,6 @@ def reference_arm(args):
         if step >= args.warmup:
             edges_total += e
             t_total += dt
-            per.append(dt)
     val = edges_total / t_total / 1e9
     sample = ("1 BFS + 1 SSSP query" if both else "1 BFS query") + " of the scale-22 workload per step"
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GTEPS", "n_gpus": args.gpus,
@@ -174,6 +176,147 @@ def reference_arm(args):
     return 0
 
 
+def pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind):
+    """trav_pull_a, the dominant kernel: CUDA events around each of its launches
+    (profile mode), algorithmic bytes = in-edges read x (4 B source id + 4 B
+    weight for SSSP) + 1 bit per in-edge (column starts)."""
+    g.set_option(gm.GM_OPT_PROFILE, 1)
+    byts, ms, launches = 0.0, 0.0, 0
+    relax_ms, relax_bytes = 0.0, 0.0
+    for kind, srcs, dev in ((gm.GM_BFS, bfs_src, src_dev[0]), (gm.GM_SSSP, sssp_src, src_dev[1])):
+        sw = 4 if kind == gm.GM_SSSP else 0
+        for i in range(len(srcs)):
+            g.program_set(kind)
+            g.set_active(dev[i:i + 1])
+            g.run(-1)
+            for row in g.trace():
+                relax_ms += row[5]
+                relax_bytes += row[3] * (4 + sw) + row[4] * 12
+                if row[1] == 1:
+                    byts += row[3] * (4 + sw) + row[3] / 8.0
+                    ms += row[7]
+                    launches += 1
+    g.set_option(gm.GM_OPT_PROFILE, 0)
+    achieved = byts / (ms / 1e3) / 1e9 if ms > 0 else None
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "kernel": "trav_pull_a", "peak_source": peak_kind,
+            "bytes_per_launch": byts / max(launches, 1), "avg_launch_us": 1e3 * ms / max(launches, 1),
+            "launches": launches,
+            "superstep_all_kernels": {"achieved_gbs": relax_bytes / (relax_ms / 1e3) / 1e9 if relax_ms else None,
+                                      "ms": relax_ms}}
+
+
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def extras(gm):
+    """The other workloads, each timed outside the main timed region."""
+    import torch
+    import synth
+    out = {}
+    ev0, ev1 = _events()
+
+    def timed(fn, reps=1):
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(reps):
+            r = fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps, r
+
+    try:  # PageRank, scale 16, 20 iterations
+        n, s, d = synth.rmat(16, 16, synth.RMAT_PARAMS["graph500"], synth.BASE_SEED)
+        g = gm.Graph(n, s, d)
+        g.program_set(gm.GM_PAGERANK)
+        g.run(20)
+        ms, _ = timed(lambda: (g.program_set(gm.GM_PAGERANK), g.run(20)), reps=5)
+        out["pagerank_s16"] = {"ms": ms, "gteps": 20 * g.m / (ms / 1e3) / 1e9, "m": g.m, "iters": 20}
+        g.close()
+    except Exception as e:  # pragma: no cover
+        out["pagerank_s16"] = {"error": str(e)}
+    try:  # batched: 64 graphs, 512 BFS + 512 SSSP, batched vs one at a time
+        scales = synth.uniform_int(64, synth.BASE_SEED + 4, 0, 12, 20)
+        graphs, queries = [], []
+        for i, sc in enumerate(scales):
+            n, s, d = synth.rmat(int(sc), 16, synth.RMAT_PARAMS["graph500"], synth.BASE_SEED + 400 + i)
+            w = synth.edge_weights_u32(s, d, synth.BASE_SEED + 1400 + i)
+            src = synth.pick_sources(n, s, d, 16, seed=401 + i)
+            graphs.append(gm.Graph(n, s, d, w))
+            queries += [(i, gm.GM_BFS, int(x)) for x in src[:8]] + [(i, gm.GM_SSSP, int(x)) for x in src[8:]]
+        outs = [torch.empty(graphs[gi].n, dtype=torch.int32, device="cuda") for gi, _, _ in queries]
+        hg = [graphs]
+        gm.run_batch(graphs, queries, outs)
+        ms_b, _ = timed(lambda: gm.run_batch(hg[0], queries, outs), reps=3)
+
+        def sequential():
+            for gi, kind, src in queries:
+                g = graphs[gi]
+                g.program_set(kind)
+                g.set_active([src])
+                g.run(-1)
+        sequential()
+        ms_s, _ = timed(sequential)
+        edges = 0
+        for (gi, kind, src), o in zip(queries, outs):
+            reached = o.cpu().numpy().view(np.uint32) != gm.INF_U32
+            od, _ = graphs[gi].degrees()
+            edges += int(od[reached].sum())
+        out["batched_64graphs_1024q"] = {"ms_batched": ms_b, "ms_sequential": ms_s, "speedup": ms_s / ms_b,
+                                         "gteps_batched": edges / (ms_b / 1e3) / 1e9,
+                                         "gteps_sequential": edges / (ms_s / 1e3) / 1e9,
+                                         "queries": len(queries), "total_m": int(sum(x.m for x in graphs))}
+        for x in graphs:
+            x.close()
+    except Exception as e:  # pragma: no cover
+        out["batched_64graphs_1024q"] = {"error": str(e)}
+    try:  # weighted PageRank, scale 20: forward vs forward + adjoint
+        n, s, d = synth.rmat(20, 16, synth.RMAT_PARAMS["graph500"], synth.BASE_SEED + 20)
+        g = gm.Graph(n, s, d)
+        w = torch.from_numpy(synth.uniform_f32(g.m, seed=20, stream=1, lo=0.5, hi=1.5)).cuda()
+        tau = torch.from_numpy(synth.uniform_f32(n, seed=20, stream=2, lo=0.5, hi=1.5)).cuda()
+        g.wpagerank_forward(w, 0.15, 30, 5)
+        ms_f, x = timed(lambda: g.wpagerank_forward(w, 0.15, 30, 5), reps=3)
+
+        def fwd_bwd():
+            xx = g.wpagerank_forward(w, 0.15, 30, 5)
+            return g.wpagerank_backward(2.0 * (xx - tau))
+        ms_fb, _ = timed(fwd_bwd, reps=3)
+        out["wpagerank_s20"] = {"ms_forward": ms_f, "ms_forward_adjoint": ms_fb, "ratio": ms_fb / ms_f,
+                                "m": g.m, "steps": 30, "ckpt_every": 5,
+                                "forward_gteps": 30 * g.m / (ms_f / 1e3) / 1e9}
+        g.close()
+    except Exception as e:  # pragma: no cover
+        out["wpagerank_s20"] = {"error": str(e)}
+    try:  # triangle counting, scale 20
+        n, s, d = synth.rmat(20, 16, synth.RMAT_PARAMS["triangle"], synth.BASE_SEED)
+        g = gm.Graph(n, s, d, flags=gm.GM_DROP_SELF_LOOPS | gm.GM_DEDUP | gm.GM_SYMMETRIZE | gm.GM_ORIENT_BY_DEGREE)
+        g.program_set(gm.GM_TRIANGLE_COUNT)
+        g.run()
+        ms, _ = timed(lambda: g.run(), reps=3)
+        out["triangles_s20"] = {"ms": ms, "oriented_m": g.m, "edges_per_s": g.m / (ms / 1e3),
+                                "triangles": g.scalar(gm.GM_SCALAR_TC_TOTAL)}
+        g.close()
+    except Exception as e:  # pragma: no cover
+        out["triangles_s20"] = {"error": str(e)}
+    try:  # collaborative filtering, 480k x 17.8k, ~1e8 ratings, K = 32, 10 iterations
+        n, s, d, r = synth.chung_lu_bipartite(480_000, 17_800, 1.1, 1e8, seed=synth.BASE_SEED + 2)
+        g = gm.Graph(n, s, d, r, n_left=480_000)
+        g.program_set(gm.GM_CF, K=32, lam=0.05, gamma=1e-3, init_sigma=0.1, seed=5)
+        g.run(1)
+        ms, _ = timed(lambda: g.run(10))
+        out["cf_100M_k32"] = {"ms_10_iters": ms, "ratings": g.m,
+                              "ratings_per_s": 10 * g.m / (ms / 1e3),
+                              "gflops": 10 * g.m * 6 * 32 / (ms / 1e3) / 1e9}
+        g.close()
+    except Exception as e:  # pragma: no cover
+        out["cf_100M_k32"] = {"error": str(e)}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -181,6 +324,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -211,6 +356,12 @@ def main():
     ingest_s = time.perf_counter() - t0
     del ts, td, tw
     src_dev = (torch.from_numpy(bfs_src).cuda(), torch.from_numpy(sssp_src).cuda())
+    tuning = None
+    if not args.no_autotune:  # on the first two sources of each kind, before any timing
+        tb = g.autotune(gm.GM_BFS, bfs_src[:2])
+        ts_ = g.autotune(gm.GM_SSSP, sssp_src[:2])
+        tuning = {"alpha": ts_["alpha"], "beta": ts_["beta"], "sssp_pull_frac": ts_["sssp_pull_frac"],
+                  "bin_small": ts_["bin_small"], "bin_large": ts_["bin_large"]}
 
     def barrier():
         torch.cuda.synchronize()
@@ -225,11 +376,13 @@ def main():
     edges = 0
     with ClockSampler(local) as clk:
         barrier()
+        torch.cuda.nvtx.range_push("timed")  # lets a profiler select exactly these launches
         ev0.record(stream)
         for _ in range(args.steps):
             edges += run_queries(gm, g, bfs_src, sssp_src, src_dev)
         ev1.record(stream)
         barrier()
+        torch.cuda.nvtx.range_pop()
     launches = gm.kernel_launch_count() - launches0
     ms = ev0.elapsed_time(ev1)
     tmax = ms
@@ -243,32 +396,8 @@ def main():
         edges_all = float(e.item())
     value = edges_all / (tmax / 1e3) / 1e9
 
-    # ---- dominant kernel: relax launches timed with CUDA events (profile mode) ----
-    g.set_option(gm.GM_OPT_PROFILE, 1)
-    relax_ms, relax_launches, scanned_e, scanned_v = 0.0, 0, 0, 0
-    bytes_alg = 0.0
-    for kind, srcs in ((gm.GM_BFS, bfs_src), (gm.GM_SSSP, sssp_src)):
-        for i in range(len(srcs)):
-            g.program_set(kind)
-            g.set_active(src_dev[0 if kind == gm.GM_BFS else 1][i:i + 1])
-            g.run(-1)
-            relax_ms += g.scalar(gm.GM_SCALAR_RELAX_MS)
-            relax_launches += g.scalar(gm.GM_SCALAR_RELAX_LAUNCHES)
-            e = g.scalar(gm.GM_SCALAR_SCANNED_EDGES)
-            v = g.scalar(gm.GM_SCALAR_PROCESSED_VERTICES)
-            scanned_e += e
-            scanned_v += v
-            # algorithmic bytes: edge stream (int32 ids + uint32 weights for SSSP)
-            # + per processed vertex an offset pair and a list/queue id
-            bytes_alg += e * (4 + (4 if kind == gm.GM_SSSP else 0)) + v * 12
-    g.set_option(gm.GM_OPT_PROFILE, 0)
     peak, peak_kind = _peaks()
-    achieved = bytes_alg / (relax_ms / 1e3) / 1e9 if relax_ms > 0 else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "kernel": "trav_relax", "peak_source": peak_kind,
-                "bytes_per_launch": bytes_alg / max(relax_launches, 1),
-                "avg_launch_us": 1e3 * relax_ms / max(relax_launches, 1), "launches": relax_launches}
+    roofline = pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind)
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -281,6 +410,10 @@ def main():
         e_edges = 0
         for _ in range(args.e2e_steps):
             g2 = gm.Graph(n, hs, hd, hw, stream=stream)
+            if tuning:
+                for opt, key, scale in ((gm.GM_OPT_ALPHA_X1000, "alpha", 1e3), (gm.GM_OPT_BETA_X1000, "beta", 1e3),
+                                        (gm.GM_OPT_SSSP_PULL_PPM, "sssp_pull_frac", 1e6)):
+                    g2.set_option(opt, round(tuning[key] * scale))
             e_edges += run_queries(gm, g2, bfs_src, sssp_src, (None, None), out_host=out)
             g2.close()
         barrier()
@@ -300,16 +433,23 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n, s, d, w, bfs_src, sssp_src, n_pairs=1)
+    m = g.m
+    g.close()
+    ext = None
+    if rank == 0 and not args.no_extras:
+        ext = extras(gm)
+    if dist:
+        dist.barrier()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tmax / max(args.steps, 1), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n": n, "m": g.m, "queries_per_step": 2 * N_QUERIES,
+                "config": {"workload": WORKLOAD, "n": n, "m": m, "queries_per_step": 2 * N_QUERIES,
                            "ingest_ms": 1e3 * ingest_s, "l2": "inputs larger than L2 (CSR+CSC+weights ~1.05 GB)",
-                           "parallelism": f"replicas{world}"},
+                           "parallelism": f"replicas{world}", "tuning": tuning},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clk.summary()}
+                "clocks": clk.summary(), "extras": ext}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

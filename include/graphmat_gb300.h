@@ -186,9 +186,10 @@ GM_API gm_status gm_get_scalar(gm_graph* g, int32_t which, void* out);
 
 /*
  * Per-superstep trace of the last gm_run in profile mode (GM_OPT_PROFILE = 1):
- * up to max_rows rows of 7 doubles -- superstep index, direction (0 push, 1 pull),
- * active vertices at its start, edges read, vertices whose edge lists were read,
- * relax-kernel time in ms (CUDA events), and the out-edges of the next frontier.
+ * up to max_rows rows of 8 doubles -- superstep index, direction (0 push, 1 pull),
+ * active work items at its start, edges read, vertices whose edge lists were read,
+ * time of the push + pull kernels in ms (CUDA events), the out-edges of the next
+ * frontier, and the time of the pull streaming kernel alone (0 in push supersteps).
  * *n_rows receives the number of rows available.
  */
 GM_API gm_status gm_get_trace(gm_graph* g, double* rows, int32_t max_rows, int32_t* n_rows);
@@ -284,6 +285,23 @@ enum {
     GM_OPT_SSSP_PULL_PPM = 8  /* SSSP: pull when frontier edges > ppm * 1e-6 * m */
 };
 GM_API gm_status gm_set_option(gm_graph* g, int32_t option, int64_t value);
+
+/*
+ * gm_autotune -- pick the push/pull switch points (BFS: GM_OPT_ALPHA_X1000 and
+ * GM_OPT_BETA_X1000; SSSP: GM_OPT_SSSP_PULL_PPM) and the degree-bin thresholds
+ * (GM_OPT_BIN_SMALL, GM_OPT_BIN_LARGE) of this handle by timing gm_program_set +
+ * gm_set_active + gm_run on the given host `sources` (coordinate descent over
+ * small candidate sets, CUDA events on the handle's stream).  The chosen values
+ * stay set on the handle and are reported in *out (may be NULL).  Tuning changes
+ * only the work decomposition, never a result.  The current program state is
+ * overwritten.
+ */
+typedef struct gm_tuning {
+    double alpha, beta, sssp_pull_frac;
+    int32_t bin_small, bin_large;
+    double best_ms;  /* time of the sample with the chosen values */
+} gm_tuning;
+GM_API gm_status gm_autotune(gm_graph* g, int32_t kind, const int32_t* sources, int32_t n_sources, gm_tuning* out);
 
 /* Number of kernel launches this library has issued since load (all handles). */
 GM_API uint64_t gm_kernel_launch_count(void);

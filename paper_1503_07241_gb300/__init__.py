@@ -76,6 +76,7 @@ SIGNATURES = {
     "gm_wpagerank_backward": ([_P, _P, _P], ctypes.c_int),
     "gm_bfs_csr_noalloc": ([_I64, _P, _P, _I32, _P, ctypes.POINTER(_I32), _P], ctypes.c_int),
     "gm_run_batch": ([_P, _I32, _P, _I32, _P, _I32, _P, _P], ctypes.c_int),
+    "gm_autotune": ([_P, _I32, _P, _I32, _P], ctypes.c_int),
     "gm_bfs_csr_noalloc_max_vertices": ([], _I64),
     "gm_kernel_launch_count": ([], _U64),
     "gm_status_string": ([ctypes.c_int], ctypes.c_char_p),
@@ -130,6 +131,11 @@ def _stream_handle(stream):
     if stream is None:
         return None
     return getattr(stream, "cuda_stream", stream)
+
+
+class gm_tuning(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("sssp_pull_frac", ctypes.c_double),
+                ("bin_small", ctypes.c_int32), ("bin_large", ctypes.c_int32), ("best_ms", ctypes.c_double)]
 
 
 class gm_query(ctypes.Structure):
@@ -284,7 +290,7 @@ class Graph:
         """Per-superstep rows of the last profiled run (see gm_get_trace)."""
         k = ctypes.c_int32()
         _check(lib().gm_get_trace(self._h, None, 0, ctypes.byref(k)), "gm_get_trace")
-        rows = np.empty((k.value, 7), np.float64)
+        rows = np.empty((k.value, 8), np.float64)
         if k.value:
             _check(lib().gm_get_trace(self._h, rows.ctypes.data, k.value, ctypes.byref(k)), "gm_get_trace")
         return rows
@@ -303,6 +309,13 @@ class Graph:
         _check(lib().gm_wpagerank_backward(self._h, dLdx.contiguous().data_ptr(), g.data_ptr()),
                "gm_wpagerank_backward")
         return g
+
+    def autotune(self, kind, sources):
+        """Tune the traversal knobs on sample host sources (gm_autotune); returns the choice."""
+        src = np.ascontiguousarray(np.atleast_1d(sources), dtype=np.int32)
+        t = gm_tuning()
+        _check(lib().gm_autotune(self._h, kind, src.ctypes.data, src.shape[0], ctypes.byref(t)), "gm_autotune")
+        return {f: getattr(t, f) for f, _ in gm_tuning._fields_}
 
     def set_option(self, option, value):
         _check(lib().gm_set_option(self._h, option, int(value)), "gm_set_option")

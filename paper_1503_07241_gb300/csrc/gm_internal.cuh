@@ -107,7 +107,7 @@ struct RunStats {
     // profile mode: one row per superstep (see gm_get_trace)
     std::vector<double> trace;
 };
-constexpr int kTraceCols = 7;
+constexpr int kTraceCols = 8;
 
 }  // namespace gm
 

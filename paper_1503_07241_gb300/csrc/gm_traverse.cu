@@ -1009,10 +1009,12 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
     } else {
         TravArgs a = make_args(g);
         const int pg = push_grid(), lg = pull_grid(), fg = finalize_grid();
-        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr, evA = nullptr, evB = nullptr;
         if (g->tune.profile) {
             GM_CUDA_TRY(cudaEventCreate(&ev0));
             GM_CUDA_TRY(cudaEventCreate(&ev1));
+            GM_CUDA_TRY(cudaEventCreate(&evA));
+            GM_CUDA_TRY(cudaEventCreate(&evB));
         }
         unsigned long long prev_e = 0, prev_v = 0;
         for (int32_t it = 0;; ++it) {
@@ -1029,8 +1031,10 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
             // both are launched; the one not matching the device-side direction returns at once
             if (sssp) trav_push<true><<<pg, kThreads, 0, s>>>(a);
             else trav_push<false><<<pg, kThreads, 0, s>>>(a);
+            if (evA) cudaEventRecord(evA, s);
             if (sssp) trav_pull_a<true><<<lg, kThreads, 0, s>>>(a);
             else trav_pull_a<false><<<lg, kThreads, 0, s>>>(a);
+            if (evB) cudaEventRecord(evB, s);
             if (sssp) trav_pull_b<true><<<fg, kThreads, 0, s>>>(a);
             else trav_pull_b<false><<<fg, kThreads, 0, s>>>(a);
             if (ev1) cudaEventRecord(ev1, s);
@@ -1044,8 +1048,9 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
                                         cudaMemcpyDeviceToHost, s));
             GM_CUDA_TRY(cudaStreamSynchronize(s));
             if (ev0) {
-                float ms = 0.f;
+                float ms = 0.f, ms_pull = 0.f;
                 cudaEventElapsedTime(&ms, ev0, ev1);
+                cudaEventElapsedTime(&ms_pull, evA, evB);
                 g->stats.relax_ms += ms;
                 g->stats.relax_launches++;
                 const uint32_t done = hp->c.done;
@@ -1054,7 +1059,7 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
                 const double row[kTraceCols] = {(double)it, (double)dir_before, (double)frontier_before,
                                                 (double)(hp->c.scanned_edges - prev_e),
                                                 (double)(hp->c.processed_vertices - prev_v), (double)ms,
-                                                (double)hp->c.medges[(it + 1) % 3]};
+                                                (double)hp->c.medges[(it + 1) % 3], (double)ms_pull};
                 prev_e = hp->c.scanned_edges;
                 prev_v = hp->c.processed_vertices;
                 g->stats.trace.insert(g->stats.trace.end(), row, row + kTraceCols);
@@ -1064,6 +1069,8 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
         }
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
+        if (evA) cudaEventDestroy(evA);
+        if (evB) cudaEventDestroy(evB);
     }
     GM_CUDA_TRY(cudaMemcpyAsync(hp, g->ctl_buf.p, sizeof(TravCtlDev), cudaMemcpyDeviceToHost, s));
     GM_CUDA_TRY(cudaStreamSynchronize(s));

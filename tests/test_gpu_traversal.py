@@ -174,3 +174,16 @@ def test_scale22_workload(gm):
     for src in srcs[1:3]:
         got, _ = _run(gm, g, gm.GM_SSSP, [src])
         check_sssp_certificate(n, cs, cd, cv.astype(np.uint32), got, np.array([src]))
+
+
+def test_autotune_keeps_results(gm):
+    n, s, d, w = rmat_case(14, weighted=True)
+    g = gm.Graph(n, s, d, w)
+    og = oracle.Graph(n, s, d, w)
+    srcs = synth.pick_sources(n, s, d, 3, seed=17)
+    for kind, ref_fn in ((gm.GM_SSSP, og.sssp), (gm.GM_BFS, og.bfs)):
+        choice = g.autotune(kind, srcs[:2])
+        assert choice["best_ms"] > 0 and 1 <= choice["bin_small"] <= choice["bin_large"]
+        got, it = _run(gm, g, kind, [srcs[2]])
+        ref, rit = ref_fn([srcs[2]])
+        assert np.array_equal(got, ref) and it == rit
