@@ -8,7 +8,10 @@
 // storing x^t every `ckpt_every` supersteps.  Backward, given lambda^T = dL/dx^T:
 //   gbar_uv  += (1 - r) x^t_u lambda^{t+1}_v                (edge gradient, SDDMM form)
 //   lambda^t_u = (1 - r) sum_v P_uv lambda^{t+1}_v           (reverse SpMV over the CSR)
-// for t = T-1 .. 0, recomputing each checkpoint segment's states forward first;
+// for t = T-1 .. 0, recomputing each checkpoint segment's states forward first.
+// Within a segment the lambda steps are pure reverse SpMVs that keep the segment's
+// lambdas vertex-major, and one edge pass per segment adds up its gbar terms, so
+// the per-edge accumulator is read and written once per segment, not per step;
 // then the row-normalisation chain rule dL/dw_uv = (gbar_uv - sum_v' P_uv' gbar_uv') / S_u.
 // Every pass is a row reduction over rows binned by length (32 short rows per
 // warp, a warp per medium row, a CTA per long row), in FP32, in a fixed order.
@@ -143,14 +146,27 @@ struct ForwardF {  // x'_v = r + (1-r) sum_{u->v} Pc_q x_u (CSC order)
     __device__ float edge(int32_t, int32_t q) const { return Pc[q] * x[row[q]]; }
     __device__ void finish(int32_t v, float s) const { xn[v] = r + (1.0f - r) * s; }
 };
-struct BackwardF {  // CSR: gbar_e += (1-r) x_u lam_v;  lam'_u = (1-r) sum_e P_e lam_v
-    const int32_t* col; const float* P; const float* x; const float* lam; float* lamn; float* gbar; float r;
+// lambda^t_u = (1-r) sum_e P_e lambda^{t+1}_v (reverse SpMV over the CSR).  The
+// lambdas of one checkpoint segment are kept vertex-major: lamT[v * kk + j].
+struct LamF {
+    const int32_t* col; const float* P; const float* lam; int kk, j_in; float* lamn; int kn, j_out; float r;
+    __device__ float edge(int32_t, int32_t e) const { return P[e] * lam[(int64_t)col[e] * kk + j_in]; }
+    __device__ void finish(int32_t u, float s) const { lamn[(int64_t)u * kn + j_out] = (1.0f - r) * s; }
+};
+// Edge gradient of one segment, supersteps t = c .. c+len-1 (SDDMM form):
+// gbar_e += (1-r) x^t_u lambda^{t+1}_v with x^t in xs[(t-c) * n + u] and
+// lambda^{t+1} in lamT[v * kk + (t - c)], added one superstep at a time from the
+// last to the first, so the rounding is the same for every checkpoint interval.
+struct GbarF {
+    const int32_t* col; const float* xs; int64_t n; const float* lamT; int kk, len; float* gbar; float r;
     __device__ float edge(int32_t u, int32_t e) const {
-        const float lv = lam[col[e]];
-        gbar[e] += (1.0f - r) * x[u] * lv;
-        return P[e] * lv;
+        const float* lv = lamT + (int64_t)col[e] * kk;
+        float acc = gbar[e];
+        for (int j = len - 1; j >= 0; --j) acc += (1.0f - r) * xs[(int64_t)j * n + u] * lv[j];
+        gbar[e] = acc;
+        return 0.0f;
     }
-    __device__ void finish(int32_t u, float s) const { lamn[u] = (1.0f - r) * s; }
+    __device__ void finish(int32_t, float) const {}
 };
 struct RowDotF {  // d_u = sum_e P_e gbar_e
     const float* P; const float* gbar; float* d;
@@ -167,6 +183,13 @@ __global__ void gather_f32(const float* __restrict__ in, const uint32_t* __restr
                            float* __restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = in[idx[i]];
+}
+
+// out[v * stride + j] = in[v]
+__global__ void scatter_strided_f32(const float* __restrict__ in, int64_t n, float* __restrict__ out,
+                                    int stride, int j) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i * stride + j] = in[i];
 }
 
 __global__ void fill_f32_k(float* p, int64_t n, float v) {
@@ -219,7 +242,7 @@ RowSet csc_rows(const gm_graph* g) {
 
 // Buffers of the weighted-PageRank forms (owned by the graph handle).
 struct WprState {
-    DevBuf S, P, Pc, gbar, ckpt, seg, lam, d;
+    DevBuf S, P, Pc, gbar, ckpt, seg, lam, lamT, d;
     int32_t steps = -1, every = 0;
     float r = 0.15f;
     bool have_forward = false;
@@ -228,7 +251,7 @@ struct WprState {
 void wpr_release(gm_graph* g) {
     WprState* w = static_cast<WprState*>(g->wpr);
     if (!w) return;
-    DevBuf* bufs[] = {&w->S, &w->P, &w->Pc, &w->gbar, &w->ckpt, &w->seg, &w->lam, &w->d};
+    DevBuf* bufs[] = {&w->S, &w->P, &w->Pc, &w->gbar, &w->ckpt, &w->seg, &w->lam, &w->lamT, &w->d};
     for (DevBuf* b : bufs) dev_free(*b, g->stream);
     delete w;
     g->wpr = nullptr;
@@ -271,6 +294,7 @@ gm_status gm_wpagerank_forward(gm_graph* g, const float* w_dev, double r, int32_
     if (w->every != ckpt_every || w->steps != steps) {
         GM_TRY(dev_alloc(w->ckpt, sizeof(float) * n * nck, s));
         GM_TRY(dev_alloc(w->seg, sizeof(float) * n * (ckpt_every + 1), s));
+        GM_TRY(dev_alloc(w->lamT, sizeof(float) * n * ckpt_every, s));
     }
     w->steps = steps;
     w->every = ckpt_every;
@@ -310,21 +334,29 @@ gm_status gm_wpagerank_backward(gm_graph* g, const float* dLdx_dev, float* dLdw_
     const int64_t n = g->n > 0 ? g->n : 1;
     const int32_t T = w->steps, k = w->every;
     const RowSet rows = csr_rows(g);
+    // lam: lambda at the current segment's end (dense, stride 1); lamT: the
+    // segment's lambda^{c+1} .. lambda^{e}, vertex-major with stride k.
     float* lam = as<float>(w->lam);
-    float* lamn = lam + n;
+    float* lamT = as<float>(w->lamT);
+    const int32_t* col = as<int32_t>(g->col);
+    const float* P = as<float>(w->P);
     GM_CUDA_TRY(cudaMemcpyAsync(lam, dLdx_dev, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, s));
     if (g->m > 0) GM_CUDA_TRY(cudaMemsetAsync(w->gbar.p, 0, sizeof(float) * g->m, s));
     float* seg = as<float>(w->seg);
     const float* ck = as<float>(w->ckpt);
     for (int32_t c = ((T - 1) / k) * k; T > 0 && c >= 0; c -= k) {
         const int32_t e = std::min(c + k, T);  // segment holds x^c .. x^{e-1}
+        const int32_t len = e - c;
         GM_CUDA_TRY(cudaMemcpyAsync(seg, ck + n * (c / k), sizeof(float) * g->n, cudaMemcpyDeviceToDevice, s));
         for (int32_t t = c; t + 1 < e; ++t) GM_TRY(wpr_step(g, w, seg + n * (t - c), seg + n * (t + 1 - c)));
-        for (int32_t t = e - 1; t >= c; --t) {
-            BackwardF f{as<int32_t>(g->col), as<float>(w->P), seg + n * (t - c), lam, lamn, as<float>(w->gbar), w->r};
-            GM_TRY(launch_pass(rows, f, s));
-            std::swap(lam, lamn);
-        }
+        // lambda^{e} into slot len-1, then lambda^{t} for t = e-1 .. c+1 into slot t-c-1
+        scatter_strided_f32<<<num_sms() * 4, 256, 0, s>>>(lam, g->n, lamT, k, len - 1);
+        g_launches++;
+        for (int32_t t = e - 1; t > c; --t)
+            GM_TRY(launch_pass(rows, LamF{col, P, lamT, k, t - c, lamT, k, t - c - 1, w->r}, s));
+        GM_TRY(launch_pass(rows, GbarF{col, seg, n, lamT, k, len, as<float>(w->gbar), w->r}, s));
+        // lambda^{c} for the next (earlier) segment
+        if (c > 0) GM_TRY(launch_pass(rows, LamF{col, P, lamT, k, 0, lam, 1, 0, w->r}, s));
     }
     GM_TRY(launch_pass(rows, RowDotF{as<float>(w->P), as<float>(w->gbar), as<float>(w->d)}, s));
     GM_TRY(launch_pass(rows, GradF{as<float>(w->gbar), as<float>(w->d), as<float>(w->S), dLdw_dev}, s));
