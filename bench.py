@@ -177,14 +177,17 @@ def reference_arm(args):
 
 
 def pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind):
-    """trav_pull_a, the dominant kernel: CUDA events around each of its launches
-    (profile mode), algorithmic bytes = in-edges read x (4 B source id + 4 B
-    weight for SSSP) + 1 bit per in-edge (column starts)."""
+    """trav_pull_a, the dominant kernel (SSSP pull): CUDA events around each of its
+    launches (profile mode); algorithmic bytes = in-edges read x (4 B source id +
+    the stored weight width) + 1 bit per in-edge (column starts).  The BFS pull
+    (trav_pull_bu, bottom-up) is timed beside it."""
+    wb = g.scalar(gm.GM_SCALAR_PULL_WEIGHT_BYTES)
     g.set_option(gm.GM_OPT_PROFILE, 1)
     byts, ms, launches = 0.0, 0.0, 0
+    bu_ms, bu_edges, bu_launches = 0.0, 0.0, 0
     relax_ms, relax_bytes = 0.0, 0.0
     for kind, srcs, dev in ((gm.GM_BFS, bfs_src, src_dev[0]), (gm.GM_SSSP, sssp_src, src_dev[1])):
-        sw = 4 if kind == gm.GM_SSSP else 0
+        sw = wb if kind == gm.GM_SSSP else 0
         for i in range(len(srcs)):
             g.program_set(kind)
             g.set_active(dev[i:i + 1])
@@ -192,19 +195,49 @@ def pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind):
             for row in g.trace():
                 relax_ms += row[5]
                 relax_bytes += row[3] * (4 + sw) + row[4] * 12
-                if row[1] == 1:
+                if row[1] == 1 and kind == gm.GM_SSSP:
                     byts += row[3] * (4 + sw) + row[3] / 8.0
                     ms += row[7]
                     launches += 1
+                elif row[1] == 1:
+                    bu_ms += row[7]
+                    bu_edges += row[3]
+                    bu_launches += 1
     g.set_option(gm.GM_OPT_PROFILE, 0)
     achieved = byts / (ms / 1e3) / 1e9 if ms > 0 else None
+    traffic = _recorded_traffic()
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "kernel": "trav_pull_a", "peak_source": peak_kind,
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "kernel": "trav_pull_a (SSSP pull)", "peak_source": peak_kind, "weight_bytes": wb,
             "bytes_per_launch": byts / max(launches, 1), "avg_launch_us": 1e3 * ms / max(launches, 1),
             "launches": launches,
+            "bfs_pull_bottom_up": {"launches": bu_launches, "avg_launch_us": 1e3 * bu_ms / max(bu_launches, 1),
+                                   "in_edges_checked_per_launch": bu_edges / max(bu_launches, 1)},
             "superstep_all_kernels": {"achieved_gbs": relax_bytes / (relax_ms / 1e3) / 1e9 if relax_ms else None,
                                       "ms": relax_ms}}
+
+
+# DRAM bytes (read + write) per trav_pull_a launch in the bench's timed step, from
+# one ncu capture of this bench command; valid only for the kernel source it was
+# taken on (hash of the traversal source files at capture time).
+PULL_A_TRAFFIC = {"source_sha256": "4001e9f5a28e96b47d166056e8bdfb90394fd69452231390d27e92c77454ed8e",
+                  "bytes_per_launch": 365.87e6}
+
+
+def _kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("gm_traverse.cu", "gm_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1503_07241_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _recorded_traffic():
+    rec = PULL_A_TRAFFIC
+    if rec["bytes_per_launch"] is None or rec["source_sha256"] != _kernel_source_hash():
+        return None
+    return rec["bytes_per_launch"]
 
 
 def _events():
@@ -331,6 +364,9 @@ def main():
     ap.add_argument("--host-loop", action="store_true",
                     help="issue every superstep's kernels from the host instead of one CUDA graph "
                          "(same kernels; profilers do not see kernels inside conditional graph nodes)")
+    ap.add_argument("--probe", choices=["bfs", "sssp"],
+                    help="build the workload graph, run one query of this kind from the first source "
+                         "with --host-loop semantics and exit (a short command for kernel profilers)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -360,14 +396,32 @@ def main():
     ingest_s = time.perf_counter() - t0
     del ts, td, tw
     src_dev = (torch.from_numpy(bfs_src).cuda(), torch.from_numpy(sssp_src).cuda())
-    if args.host_loop:
+    if args.host_loop or args.probe:
         g.set_option(gm.GM_OPT_LOOP_MODE, 1)
+    if args.probe:
+        kind, srcs = (gm.GM_BFS, bfs_src) if args.probe == "bfs" else (gm.GM_SSSP, sssp_src)
+        g.program_set(kind)
+        g.set_active(srcs[:1])
+        it = g.run(-1)
+        torch.cuda.synchronize()
+        print(json.dumps({"probe": args.probe, "source": int(srcs[0]), "supersteps": it,
+                          "pulls": g.scalar(gm.GM_SCALAR_PULL_STEPS)}), flush=True)
+        g.set_option(gm.GM_OPT_PROFILE, 1)  # the same query again, timed per superstep
+        g.program_set(kind)
+        g.set_active(srcs[:1])
+        g.run(-1)
+        for row in g.trace():
+            print(json.dumps({"t": int(row[0]), "dir": "pull" if row[1] else "push", "active": int(row[2]),
+                              "edges": int(row[3]), "vertices": int(row[4]), "relax_ms": round(row[5], 4),
+                              "pull_first_kernel_ms": round(row[7], 4)}), flush=True)
+        g.close()
+        return 0
     tuning = None
     if not args.no_autotune:  # on the first two sources of each kind, before any timing
         tb = g.autotune(gm.GM_BFS, bfs_src[:2])
         ts_ = g.autotune(gm.GM_SSSP, sssp_src[:2])
         tuning = {"alpha": ts_["alpha"], "beta": ts_["beta"], "sssp_pull_frac": ts_["sssp_pull_frac"],
-                  "bin_small": ts_["bin_small"], "bin_large": ts_["bin_large"]}
+                  "bin_small": ts_["bin_small"], "bin_large": ts_["bin_large"], "pull_stage": ts_["pull_stage"]}
 
     def barrier():
         torch.cuda.synchronize()
@@ -418,7 +472,9 @@ def main():
             g2 = gm.Graph(n, hs, hd, hw, stream=stream)
             if tuning:
                 for opt, key, scale in ((gm.GM_OPT_ALPHA_X1000, "alpha", 1e3), (gm.GM_OPT_BETA_X1000, "beta", 1e3),
-                                        (gm.GM_OPT_SSSP_PULL_PPM, "sssp_pull_frac", 1e6)):
+                                        (gm.GM_OPT_SSSP_PULL_PPM, "sssp_pull_frac", 1e6),
+                                        (gm.GM_OPT_BIN_LARGE, "bin_large", 1), (gm.GM_OPT_BIN_SMALL, "bin_small", 1),
+                                        (gm.GM_OPT_PULL_STAGE, "pull_stage", 1)):
                     g2.set_option(opt, round(tuning[key] * scale))
             e_edges += run_queries(gm, g2, bfs_src, sssp_src, (None, None), out_host=out)
             g2.close()

@@ -180,7 +180,10 @@ enum {
     GM_SCALAR_SCANNED_EDGES = 7,  /* int64: edges read by the relax kernels in the last gm_run */
     GM_SCALAR_RELAX_MS = 8,       /* double: profile mode, summed relax-kernel time (CUDA events) */
     GM_SCALAR_RELAX_LAUNCHES = 9, /* int32: profile mode, relax-kernel launches timed */
-    GM_SCALAR_PROCESSED_VERTICES = 10 /* int64: vertices whose edge lists the relax kernels read */
+    GM_SCALAR_PROCESSED_VERTICES = 10, /* int64: vertices whose edge lists the relax kernels read */
+    GM_SCALAR_PULL_WEIGHT_BYTES = 11   /* int32: bytes per in-edge weight the SSSP pull reads: 1 when
+                                          every uint32 weight is below 256 (a one-byte copy is kept),
+                                          4 otherwise, 0 for an unweighted graph; set at creation */
 };
 GM_API gm_status gm_get_scalar(gm_graph* g, int32_t which, void* out);
 
@@ -189,7 +192,8 @@ GM_API gm_status gm_get_scalar(gm_graph* g, int32_t which, void* out);
  * up to max_rows rows of 8 doubles -- superstep index, direction (0 push, 1 pull),
  * active work items at its start, edges read, vertices whose edge lists were read,
  * time of the push + pull kernels in ms (CUDA events), the out-edges of the next
- * frontier, and the time of the pull streaming kernel alone (0 in push supersteps).
+ * frontier, and the time of the pull's first kernel alone (0 in push supersteps; SSSP:
+ * the in-edge streaming kernel, BFS: the bottom-up kernel, which counts in-edges checked).
  * *n_rows receives the number of rows available.
  */
 GM_API gm_status gm_get_trace(gm_graph* g, double* rows, int32_t max_rows, int32_t* n_rows);
@@ -282,7 +286,9 @@ enum {
     GM_OPT_BIN_LARGE = 5,     /* degree from which a whole CTA processes one vertex */
     GM_OPT_ALPHA_X1000 = 6,   /* BFS push->pull switch: frontier edges > unvisited in-edges / alpha */
     GM_OPT_BETA_X1000 = 7,    /* BFS pull->push switch: frontier vertices < n / beta */
-    GM_OPT_SSSP_PULL_PPM = 8  /* SSSP: pull when frontier edges > ppm * 1e-6 * m */
+    GM_OPT_SSSP_PULL_PPM = 8, /* SSSP: pull when frontier edges > ppm * 1e-6 * m */
+    GM_OPT_PULL_STAGE = 9     /* SSSP pull: messages of the highest-out-degree sources each CTA stages in
+                                 shared memory, 0..49152 (rounded down to a multiple of 4; default 40960) */
 };
 GM_API gm_status gm_set_option(gm_graph* g, int32_t option, int64_t value);
 
@@ -300,6 +306,7 @@ typedef struct gm_tuning {
     double alpha, beta, sssp_pull_frac;
     int32_t bin_small, bin_large;
     double best_ms;  /* time of the sample with the chosen values */
+    int32_t pull_stage;  /* GM_OPT_PULL_STAGE chosen (SSSP) */
 } gm_tuning;
 GM_API gm_status gm_autotune(gm_graph* g, int32_t kind, const int32_t* sources, int32_t n_sources, gm_tuning* out);
 

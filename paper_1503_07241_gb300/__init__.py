@@ -22,9 +22,9 @@ GM_DROP_SELF_LOOPS, GM_DEDUP, GM_SYMMETRIZE, GM_ORIENT_BY_DEGREE = 1, 2, 4, 8
 GM_PAGERANK, GM_BFS, GM_SSSP, GM_TRIANGLE_COUNT, GM_CF = range(5)
 (GM_SCALAR_TC_TOTAL, GM_SCALAR_CF_LOSS, GM_SCALAR_REACHED_EDGES, GM_SCALAR_SUPERSTEPS,
  GM_SCALAR_PUSH_STEPS, GM_SCALAR_PULL_STEPS, GM_SCALAR_SCANNED_EDGES, GM_SCALAR_RELAX_MS,
- GM_SCALAR_RELAX_LAUNCHES, GM_SCALAR_PROCESSED_VERTICES) = range(1, 11)
+ GM_SCALAR_RELAX_LAUNCHES, GM_SCALAR_PROCESSED_VERTICES, GM_SCALAR_PULL_WEIGHT_BYTES) = range(1, 12)
 (GM_OPT_DIRECTION, GM_OPT_LOOP_MODE, GM_OPT_PROFILE, GM_OPT_BIN_SMALL, GM_OPT_BIN_LARGE,
- GM_OPT_ALPHA_X1000, GM_OPT_BETA_X1000, GM_OPT_SSSP_PULL_PPM) = range(1, 9)
+ GM_OPT_ALPHA_X1000, GM_OPT_BETA_X1000, GM_OPT_SSSP_PULL_PPM, GM_OPT_PULL_STAGE) = range(1, 10)
 INF_U32 = 0xFFFFFFFF
 
 _SCALAR_TYPES = {
@@ -33,6 +33,7 @@ _SCALAR_TYPES = {
     GM_SCALAR_PUSH_STEPS: ctypes.c_int32, GM_SCALAR_PULL_STEPS: ctypes.c_int32,
     GM_SCALAR_SCANNED_EDGES: ctypes.c_int64, GM_SCALAR_RELAX_MS: ctypes.c_double,
     GM_SCALAR_RELAX_LAUNCHES: ctypes.c_int32, GM_SCALAR_PROCESSED_VERTICES: ctypes.c_int64,
+    GM_SCALAR_PULL_WEIGHT_BYTES: ctypes.c_int32,
 }
 
 
@@ -135,7 +136,8 @@ def _stream_handle(stream):
 
 class gm_tuning(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("sssp_pull_frac", ctypes.c_double),
-                ("bin_small", ctypes.c_int32), ("bin_large", ctypes.c_int32), ("best_ms", ctypes.c_double)]
+                ("bin_small", ctypes.c_int32), ("bin_large", ctypes.c_int32), ("best_ms", ctypes.c_double),
+                ("pull_stage", ctypes.c_int32)]
 
 
 class gm_query(ctypes.Structure):

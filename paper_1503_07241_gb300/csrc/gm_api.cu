@@ -42,6 +42,8 @@ gm_status ensure_unit_weights(gm_graph* g) {
     fill_u32_k<<<num_sms() * 4, 256, 0, g->stream>>>(as<uint32_t>(g->cw), g->m, 1u);
     g_launches += 2;
     GM_CUDA_TRY(cudaGetLastError());
+    GM_TRY(dev_alloc(g->cw8, (size_t)m, g->stream));  // unit weights fit in one byte
+    GM_CUDA_TRY(cudaMemsetAsync(g->cw8.p, 1, (size_t)m, g->stream));
     g->wtype = GM_W_U32;
     return GM_OK;
 }
@@ -212,6 +214,9 @@ gm_status gm_get_scalar(gm_graph* g, int32_t which, void* out) {
         case GM_SCALAR_RELAX_MS: *static_cast<double*>(out) = g->stats.relax_ms; return GM_OK;
         case GM_SCALAR_RELAX_LAUNCHES: *static_cast<int32_t*>(out) = g->stats.relax_launches; return GM_OK;
         case GM_SCALAR_PROCESSED_VERTICES: *static_cast<int64_t*>(out) = g->stats.processed_vertices; return GM_OK;
+        case GM_SCALAR_PULL_WEIGHT_BYTES:
+            *static_cast<int32_t*>(out) = g->wtype == GM_W_NONE ? 0 : g->cw8.p ? 1 : 4;
+            return GM_OK;
         default: break;
     }
     set_error("gm_get_scalar: unknown scalar %d", which);
@@ -263,6 +268,11 @@ gm_status gm_set_option(gm_graph* g, int32_t option, int64_t value) {
         case GM_OPT_SSSP_PULL_PPM:
             if (value < 0 || value > 1000000) break;
             t.sssp_pull_frac = value * 1e-6;
+            return GM_OK;
+        case GM_OPT_PULL_STAGE:
+            if (value < 0 || value > 49152) break;
+            t.pull_stage = (int32_t)(value & ~(int64_t)3);
+            trav_release(g);  // the loop graph bakes the shared-memory size in
             return GM_OK;
         default:
             set_error("gm_set_option: unknown option %d", option);

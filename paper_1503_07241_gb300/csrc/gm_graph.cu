@@ -94,6 +94,18 @@ __global__ void compact_triples(const int32_t* __restrict__ a, const int32_t* __
     co[p] = c[i];
 }
 
+// out[i] = in[i] as one byte; *wide = 1 if some in[i] does not fit.
+__global__ void narrow_u8(const uint32_t* __restrict__ in, int64_t len, uint8_t* __restrict__ out,
+                          uint32_t* __restrict__ wide) {
+    bool big = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = in[i];
+        big |= x > 255u;
+        out[i] = (uint8_t)x;
+    }
+    if (__syncthreads_or(big) && threadIdx.x == 0) atomicOr(wide, 1u);
+}
+
 __global__ void gather_u32(const uint32_t* __restrict__ in, const uint32_t* __restrict__ idx, int64_t len,
                            uint32_t* __restrict__ out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -317,7 +329,8 @@ static gm_status ingest(gm_graph* g, const gm_edge_list* el, uint32_t flags) {
         ~Scope() { for (int i = 0; i < k; ++i) dev_free(*bufs[i], s); }
         void add(DevBuf& b) { bufs[k++] = &b; }
     } scope{s};
-    scope.add(d_src); scope.add(d_dst); scope.add(d_w);
+    DevBuf wide;  // flag: some weight needs more than 8 bits
+    scope.add(d_src); scope.add(d_dst); scope.add(d_w); scope.add(wide);
     if (!el->on_device && m > 0) {
         GM_TRY(dev_alloc(d_src, sizeof(int32_t) * m, s));
         GM_TRY(dev_alloc(d_dst, sizeof(int32_t) * m, s));
@@ -449,6 +462,18 @@ static gm_status ingest(gm_graph* g, const gm_edge_list* el, uint32_t flags) {
                                                       as<uint32_t>(g->cw));
             LAUNCH_CHECK();
         }
+        if (g->wtype == GM_W_U32 && mm > 0) {  // one byte per in-edge for the pull when the weights allow
+            GM_TRY(dev_alloc(wide, sizeof(uint32_t), s));
+            GM_CUDA_TRY(cudaMemsetAsync(wide.p, 0, sizeof(uint32_t), s));
+            GM_TRY(dev_alloc(g->cw8, (size_t)(mm + kEdgePad), s));
+            GM_CUDA_TRY(cudaMemsetAsync(g->cw8.p, 0, (size_t)(mm + kEdgePad), s));
+            narrow_u8<<<num_sms() * 8, 256, 0, s>>>(as<uint32_t>(g->cw), mm, as<uint8_t>(g->cw8), as<uint32_t>(wide));
+            LAUNCH_CHECK();
+            uint32_t h_wide = 1u;
+            GM_CUDA_TRY(cudaMemcpyAsync(&h_wide, wide.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            GM_CUDA_TRY(cudaStreamSynchronize(s));
+            if (h_wide) dev_free(g->cw8, s);
+        }
     }
 
     // ---- degrees and bins ----
@@ -462,6 +487,66 @@ static gm_status ingest(gm_graph* g, const gm_edge_list* el, uint32_t flags) {
     GM_TRY(build_bins(g));
     GM_TRY(build_dcsc(g));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
+    return GM_OK;
+}
+
+// ---- source ranks for the SSSP pull ----
+__global__ void rank_keys(const int32_t* __restrict__ out_deg, int64_t n, uint64_t* __restrict__ keys,
+                          uint32_t* __restrict__ vals) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        keys[i] = 0xFFFFFFFFull - (uint32_t)out_deg[i];  // ascending key = descending degree
+        vals[i] = (uint32_t)i;
+    }
+}
+
+__global__ void invert_order(const uint32_t* __restrict__ order, int64_t n, int32_t* __restrict__ rank) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        rank[order[i]] = (int32_t)i;
+}
+
+__global__ void gather_i32(const int32_t* __restrict__ idx, int64_t len, const int32_t* __restrict__ table,
+                           int32_t* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = table[idx[i]];
+}
+
+gm_status build_source_ranks(gm_graph* g) {
+    if (g->src_rank.p) return GM_OK;
+    cudaStream_t s = g->stream;
+    const int64_t n = g->n, m = g->m;
+    struct Tmp {
+        cudaStream_t s;
+        DevBuf b[4];
+        ~Tmp() { for (DevBuf& x : b) dev_free(x, s); }
+    } tmp{s};
+    DevBuf &keys = tmp.b[0], &vals = tmp.b[1], &keys2 = tmp.b[2], &vals2 = tmp.b[3];
+    const int64_t n1 = n > 0 ? n : 1;
+    GM_TRY(dev_alloc(g->src_rank, sizeof(int32_t) * n1, s));
+    GM_TRY(dev_alloc(g->row_r, sizeof(int32_t) * (m + kEdgePad), s));
+    GM_TRY(dev_alloc(g->dc_rank, sizeof(int32_t) * (g->dc_ncols > 0 ? g->dc_ncols : 1), s));
+    GM_CUDA_TRY(cudaMemsetAsync(g->row_r.p, 0, sizeof(int32_t) * (m + kEdgePad), s));
+    if (n > 0) {
+        GM_TRY(dev_alloc(keys, sizeof(uint64_t) * n, s));
+        GM_TRY(dev_alloc(vals, sizeof(uint32_t) * n, s));
+        GM_TRY(dev_alloc(keys2, sizeof(uint64_t) * n, s));
+        GM_TRY(dev_alloc(vals2, sizeof(uint32_t) * n, s));
+        rank_keys<<<blocks_for(n), 256, 0, s>>>(as<int32_t>(g->out_deg), n, as<uint64_t>(keys), as<uint32_t>(vals));
+        LAUNCH_CHECK();
+        GM_TRY(radix_sort_pairs(as<uint64_t>(keys), as<uint32_t>(vals), as<uint64_t>(keys2), as<uint32_t>(vals2), n,
+                                32, s));
+        invert_order<<<blocks_for(n), 256, 0, s>>>(as<uint32_t>(vals), n, as<int32_t>(g->src_rank));
+        LAUNCH_CHECK();
+    }
+    if (m > 0) {
+        gather_i32<<<blocks_for(m), 256, 0, s>>>(as<int32_t>(g->row), m, as<int32_t>(g->src_rank), as<int32_t>(g->row_r));
+        LAUNCH_CHECK();
+    }
+    if (g->dc_ncols > 0) {
+        gather_i32<<<blocks_for(g->dc_ncols), 256, 0, s>>>(as<int32_t>(g->dc_jc), g->dc_ncols, as<int32_t>(g->src_rank),
+                                                           as<int32_t>(g->dc_rank));
+        LAUNCH_CHECK();
+    }
+    GM_CUDA_TRY(cudaStreamSynchronize(s));  // the temporaries are freed on return
     return GM_OK;
 }
 
@@ -607,10 +692,10 @@ void release_graph(gm_graph* g) {
     trav_release(g);
     wpr_release(g);
     cf_release(g);
-    DevBuf* bufs[] = {&g->row_ptr, &g->col, &g->w, &g->col_ptr, &g->row, &g->cw, &g->csc_pos,
+    DevBuf* bufs[] = {&g->row_ptr, &g->col, &g->w, &g->col_ptr, &g->row, &g->cw, &g->cw8, &g->csc_pos,
                       &g->out_deg, &g->in_deg, &g->out_bin, &g->in_bin, &g->in_list, &g->zero_in_list,
                       &g->out_list, &g->zero_out_list, &g->dc_jc, &g->dc_cp, &g->dc_tile, &g->dc_head,
-                      &g->state, &g->work, &g->ctl_buf};
+                      &g->src_rank, &g->row_r, &g->dc_rank, &g->state, &g->work, &g->ctl_buf};
     for (DevBuf* b : bufs) dev_free(*b, s);
     if (g->host_pinned) cudaFreeHost(g->host_pinned);
     cudaStreamSynchronize(s);

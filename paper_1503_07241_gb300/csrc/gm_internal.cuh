@@ -81,7 +81,7 @@ struct TravCtl {
     uint32_t iters_done;
     uint32_t bad_ids;             // seeding saw vertex ids outside [0, n)
     uint32_t guard_hit;           // the loop passed n + 1 supersteps (impossible for valid runs)
-    uint32_t pad;
+    uint32_t stage_timeouts;      // pull CTAs whose shared-memory staging copy did not complete in time
 };
 
 // Options and tuning knobs of a graph handle.
@@ -91,6 +91,7 @@ struct Tuning {
     double alpha = 14.0;        // push -> pull when frontier edges > unvisited edges / alpha
     double beta = 24.0;         // pull -> push when frontier vertices < n / beta
     double sssp_pull_frac = 0.05;  // SSSP: pull when frontier edges > sssp_pull_frac * m
+    int32_t pull_stage = 40960;    // SSSP pull: hottest messages staged in shared memory per CTA
     int32_t direction = 0;      // 0 auto, 1 push only, 2 pull only
     int32_t loop_mode = 0;      // 0 device loop (CUDA graph with a conditional WHILE node), 1 host loop
     int32_t profile = 0;        // 1: host loop with CUDA events around every relax launch
@@ -121,6 +122,13 @@ struct gm_graph {
     gm::DevBuf row_ptr, col, w;      // w: uint32 or float per CSR edge (as wtype)
     // CSC: in-edges sorted by (dst, src)
     gm::DevBuf col_ptr, row, cw, csc_pos;  // cw: CSC copy of w; csc_pos: CSR index of each CSC edge
+    gm::DevBuf cw8;                  // uint8 copy of cw when every uint32 weight is below 256 (else empty)
+    // Sources ranked by out-degree (descending, ties by id), built on the first SSSP
+    // program_set: the SSSP messages live in rank order so that the hottest sources'
+    // messages are one contiguous prefix the pull can keep in shared memory.
+    gm::DevBuf src_rank;             // rank of each vertex (int32[n])
+    gm::DevBuf row_r;                // CSC sources as ranks (int32[m + pad])
+    gm::DevBuf dc_rank;              // rank of each non-empty column's vertex (int32[ncols])
     gm::DevBuf out_deg, in_deg;      // int32
     gm::DevBuf out_bin, in_bin;      // uint8 bin of each vertex by out/in degree (0 = degree zero)
     gm::DevBuf in_list;              // vertex ids with in_deg > 0, grouped by in-degree bin
@@ -164,6 +172,7 @@ struct gm_graph {
 namespace gm {
 // per-program entry points (implemented in gm_traverse.cu, gm_pagerank.cu, ...)
 gm_status trav_prepare(gm_graph* g);
+gm_status build_source_ranks(gm_graph* g);  // gm_graph.cu
 gm_status trav_set_active(gm_graph* g, const int32_t* vertices_dev, int64_t count);
 gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done);
 void trav_release(gm_graph* g);

@@ -1,7 +1,8 @@
 // BFS and SSSP supersteps (Algorithms 1 and 2 with the min semiring).
 //
-// One superstep is four kernels (push, the two pull kernels and finalize; the
-// direction not chosen on the device returns at once):
+// One superstep is four kernels for SSSP (push, the two pull kernels, finalize)
+// and three for BFS (push, the bottom-up pull, finalize); the direction not chosen
+// on the device returns at once:
 //   relax     the generalized SPMV with Process_Message/Reduce fused into the
 //             update of the vertex property (Apply = min), either
 //               push: over the out-edges (CSR) of the compacted frontier queue,
@@ -13,7 +14,7 @@
 //             vertices whose property changed join the next frontier (bitvector
 //             bit + binned queue, warp-aggregated) -- Algorithm 2's "mark changed
 //             vertices active" without a separate scan of the active array.
-//   finalize  SSSP: writes the messages of the next frontier; the last CTA to
+//   finalize  SSSP after a push: writes the messages of the next frontier; the last CTA to
 //             finish counts the active vertices, stops at convergence or
 //             max_iters, and picks push or pull for the next superstep.
 //
@@ -27,6 +28,8 @@
 // BSP semantics are exact: messages come from values fixed at the start of the
 // superstep (BFS: the constant t+1; SSSP: the message array), so the property
 // after each superstep and the superstep count equal Algorithm 2's.
+#include <algorithm>
+
 #include "gm_internal.cuh"
 
 namespace gm {
@@ -51,13 +54,19 @@ struct TravCtlDev {
 struct TravArgs {
     const int32_t* row_ptr; const int32_t* col; const uint32_t* w;
     const int32_t* col_ptr; const int32_t* row; const uint32_t* cw;
+    const uint8_t* cw8;      // one byte per in-edge weight when all fit (nullptr otherwise)
     const int32_t* out_deg; const int32_t* in_deg; const uint8_t* out_bin;
     const int32_t* in_list; int64_t in_s0, in_s1, in_m1;  // small bin [in_s0, in_s1), medium [in_s1, in_m1)
     const int32_t* dc_jc; const int32_t* dc_cp; const int32_t* dc_tile;  // doubly compressed CSC + tiles
     int64_t dc_ncols, ntiles;
     int64_t n, m, nwords;
     uint32_t* dist;
-    uint32_t* msg[2];        // SSSP messages of superstep t live in msg[t & 1], infinity elsewhere
+    uint32_t* msg[2];        // SSSP messages of superstep t live in msg[t & 1], infinity elsewhere,
+                             // indexed by source rank (msg[.][rank[v]] is vertex v's message)
+    const int32_t* rank;     // SSSP: rank of each vertex by out-degree (descending)
+    const int32_t* row_r;    // SSSP: CSC sources as ranks
+    const int32_t* dc_rank;  // SSSP: rank of each non-empty column's vertex
+    int32_t hot;             // SSSP pull: messages of ranks [0, hot) are staged in shared memory
     uint32_t* ycol;          // pull: reduced value per non-empty column, infinity between supersteps
     const uint32_t* dc_head; // pull: first-edge-of-column bits
     uint32_t* bv[3];         // frontier bitvectors, rotating by superstep
@@ -96,12 +105,6 @@ __device__ __forceinline__ bool test_bit(const uint32_t* bv, int32_t v) {
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
-__device__ __forceinline__ uint32_t warp_min_u32(uint32_t v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
     return v;
 }
 
@@ -301,7 +304,7 @@ __device__ void push_phase(const TravArgs& a, uint32_t t, int cur, int nxt, Acc&
         const int32_t re = a.row_ptr[u + 1];
         const int32_t beg = a.row_ptr[u] + it.y * kChunk;
         const int32_t end = min(re, beg + kChunk);
-        const uint32_t du = SSSP ? msgc[u] : 0u;
+        const uint32_t du = SSSP ? msgc[a.rank[u]] : 0u;
         for (int32_t base = beg & ~3; base < end; base += kCtaSpan)
             push_contig<SSSP>(a, base + (int32_t)threadIdx.x * kEPT, beg, end, du, t, nxt, acc);
     }
@@ -310,7 +313,7 @@ __device__ void push_phase(const TravArgs& a, uint32_t t, int cur, int nxt, Acc&
         const int32_t u = a.q[cur][2][i];
         if (lane == 0) acc.verts++;
         const int32_t beg = a.row_ptr[u], end = a.row_ptr[u + 1];
-        const uint32_t du = SSSP ? msgc[u] : 0u;
+        const uint32_t du = SSSP ? msgc[a.rank[u]] : 0u;
         for (int32_t base = beg & ~3; base < end; base += kWarpSpan)
             push_contig<SSSP>(a, base + lane * kEPT, beg, end, du, t, nxt, acc);
     }
@@ -327,7 +330,7 @@ __device__ void push_phase(const TravArgs& a, uint32_t t, int cur, int nxt, Acc&
             acc.verts++;
             beg = a.row_ptr[u];
             deg = (uint32_t)(a.row_ptr[u + 1] - beg);
-            du = SSSP ? msgc[u] : 0u;
+            du = SSSP ? msgc[a.rank[u]] : 0u;
         }
         const uint32_t incl = warp_incl_scan(deg);
         __syncwarp();
@@ -383,7 +386,7 @@ __device__ __forceinline__ void relax_prologue(const TravArgs& a, const TravCtl*
             if (i < n1) v = a.q[clr][1][i];
             else if (i < (int64_t)n1 + n2) v = a.q[clr][2][i - n1];
             else v = a.qc[clr][i - n1 - n2].x;
-            mz[v] = kInf;
+            mz[a.rank[v]] = kInf;
         }
     }
 }
@@ -414,81 +417,190 @@ __device__ __forceinline__ void flush_acc(const TravArgs& a, Acc& acc, int nxt, 
     }
 }
 
+// ---------------------------------------------------------------- bulk copy (TMA)
+constexpr int kPullThreads = 1024;
+constexpr int32_t kHotMax = 49152;      // staged messages per CTA: at most 192 KB of shared memory
+constexpr uint32_t kBulkChunk = 32768;  // bytes per cp.async.bulk instruction
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Make the initialised barrier visible to the async (TMA) proxy.
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Global -> shared bulk copy; completion is counted on the barrier in bytes.
+// dst, src and bytes are multiples of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+
+// Waits for the barrier's phase `parity` to complete, giving up after a bounded
+// number of tries (each try may suspend the thread for a short time).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < (1u << 20); ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
 // ---------------------------------------------------------------- pull
 // Pull in two kernels over the doubly compressed CSC (non-empty columns only).
-//  pull_a  streams the in-edges in warp tiles of kWTile: each lane reads 8
+//  pull_a  (SSSP) streams the in-edges in warp tiles of kWTile: each lane reads 8
 //          consecutive edges with 16-byte loads (the next tile's edges are already
-//          in flight), evaluates Process_Message for each (BFS: t+1 if the source
-//          is in the frontier bitvector; SSSP: msg[u] + w(u, v), msg infinity off
-//          the frontier), and Reduce(min)s them per column.  Columns are found
+//          in flight), evaluates Process_Message for each (msg[u] + w(u, v), msg
+//          infinity off the frontier), and Reduce(min)s them per column.  Columns are found
 //          without any index loads: a bit marks the first edge of every column,
 //          a warp prefix count of these bits numbers the columns, and a warp
 //          segmented min-scan joins the pieces of columns that span lanes.
 //          Complete columns are stored to y[column]; the (at most two) columns
-//          crossing the tile border are combined with atomicMin.
-//  pull_b  applies y to the vertex properties (Apply = min), makes changed
+//          crossing the tile border are combined with atomicMin.  Sources are
+//          read as out-degree ranks and the messages are kept in rank order, so
+//          the messages of the hottest sources (ranks [0, hot), about 60 % of the
+//          in-edges of an RMAT graph) are one contiguous block: each CTA stages it
+//          into shared memory with a bulk (TMA) copy, and only the other sources
+//          are gathered through L1/L2.
+//  pull_bu (BFS) the same reduction bottom-up: every message is t+1, so an
+//          unvisited column needs only one in-neighbour in the frontier bitvector
+//          and stops at the first; a visited column cannot change (its depth is
+//          at most t) and is skipped.  The result per column equals the full
+//          Reduce(min) wherever Apply can use it.
+//          It applies directly (one lane owns a column).
+//  pull_b  (SSSP) applies y to the vertex properties (Apply = min), makes changed
 //          vertices the next frontier and resets y to infinity.
-template <bool SSSP>
-__global__ void __launch_bounds__(kThreads, 4) trav_pull_a(TravArgs a) {
+// One warp tile's streamed inputs per lane: 8 in-edge source ranks, their
+// weights (one-byte weights stay packed in two words until used), the lane's 8
+// first-edge bits and the tile's first column.
+template <int WB>
+struct PullTile {
+    int32_t r[kEPT];
+    uint32_t w[WB == 1 ? 2 : kEPT];
+    uint32_t hw;
+    int32_t c0;
+    __device__ __forceinline__ uint32_t weight(int q) const {
+        if (WB == 1) return (w[q >> 2] >> (8 * (q & 3))) & 0xFFu;
+        return w[q];
+    }
+};
+
+template <int WB>
+__device__ __forceinline__ void pull_load_tile(const TravArgs& a, int64_t k, int lane, PullTile<WB>& x) {
+    const int64_t p = k * (int64_t)kWTile + (int64_t)lane * kEPT;
+    if (p < a.m) {
+        load8(a.row_r, (int32_t)p, x.r);
+        if (WB == 1) {
+            const uint2 v = __ldcs(reinterpret_cast<const uint2*>(a.cw8 + p));
+            x.w[0] = v.x;
+            x.w[1] = v.y;
+        } else {
+            uint32_t (&w8)[kEPT] = *reinterpret_cast<uint32_t(*)[kEPT]>(&x.w[0]);
+            load8(a.cw, (int32_t)p, w8);
+        }
+    }
+    x.hw = __ldcs(a.dc_head + (p >> 5));
+    x.c0 = __ldg(a.dc_tile + k);
+}
+
+// Messages of a tile's sources: staged ranks from shared memory, the rest from
+// global memory.  Edges at or past m read rank 0's message (present whenever
+// there is an edge) and are masked later.
+__device__ __forceinline__ void pull_gather(const uint32_t* __restrict__ msgc, const uint32_t* s_hot, int32_t hlim,
+                                            int64_t e0, int64_t m, const int32_t (&r)[kEPT], uint32_t (&mv)[kEPT]) {
+#pragma unroll
+    for (int q = 0; q < kEPT; ++q) {
+        const int32_t rq = e0 + q < m ? r[q] : 0;
+        mv[q] = rq < hlim ? s_hot[rq] : __ldg(msgc + rq);
+    }
+}
+
+// WB: bytes per in-edge weight read (1: the uint8 copy, 4: the uint32 array).
+// One CTA of kPullThreads per SM; dynamic shared memory holds a.hot messages.
+// Software pipeline per warp: while tile k is reduced, the messages of tile k+1
+// are being gathered and the sources of tile k+2 streamed in.
+template <int WB>
+__global__ void __launch_bounds__(kPullThreads, 1) trav_pull_a(TravArgs a) {
+    extern __shared__ __align__(128) uint32_t s_hot[];
+    __shared__ __align__(8) uint64_t s_bar;
     TravCtlDev* cd = a.ctl;
     if (cd->c.done || cd->c.dir != 1u) return;
     const uint32_t t = cd->c.iter;
-    const int cur = (int)(t % 3u), clr = (int)((t + 2u) % 3u);
-    relax_prologue<SSSP>(a, &cd->c, t, clr);
-    const int lane = threadIdx.x & 31;
-    const int64_t gwarp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
-    const uint32_t* __restrict__ bvc = a.bv[cur];
+    const int clr = (int)((t + 2u) % 3u);
     const uint32_t* __restrict__ msgc = a.msg[t & 1u];
+    const int32_t hot = a.hot;  // a multiple of 4, so the copy is whole 16-byte units
+    if (threadIdx.x == 0 && hot > 0) {
+        mbar_init(&s_bar, 1u);
+        fence_mbar_init();
+        const uint32_t bytes = (uint32_t)hot * 4u;
+        mbar_arrive_expect_tx(&s_bar, bytes);
+        for (uint32_t off = 0; off < bytes; off += kBulkChunk)
+            bulk_copy_g2s(reinterpret_cast<char*>(s_hot) + off, reinterpret_cast<const char*>(msgc) + off,
+                          min(kBulkChunk, bytes - off), &s_bar);
+    }
+    relax_prologue<true>(a, &cd->c, t, clr);
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * kPullThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kPullThreads) >> 5;
     uint32_t* __restrict__ y = a.ycol;
     unsigned long long scanned = 0;
 
-    int32_t u[kEPT];
-    uint32_t wt[kEPT], hw = 0u;
-    int32_t c0 = 0;
-    if (gwarp < a.ntiles) {  // first tile of this warp
-        const int64_t p0 = gwarp * (int64_t)kWTile + (int64_t)lane * kEPT;
-        if (p0 < a.m) {
-            load8(a.row, (int32_t)p0, u);
-            if (SSSP) load8(a.cw, (int32_t)p0, wt);
-        }
-        hw = __ldcs(a.dc_head + (p0 >> 5));
-        c0 = __ldg(a.dc_tile + gwarp);
-    }
+    // the warp's first two tiles stream in while the staging copy runs
+    PullTile<WB> cur, nxt;
+    if (gwarp < a.ntiles) pull_load_tile<WB>(a, gwarp, lane, cur);
+    if (gwarp + nwarps < a.ntiles) pull_load_tile<WB>(a, gwarp + nwarps, lane, nxt);
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+    bool staged = hot > 0 && mbar_wait_bounded(&s_bar, 0u);
+    staged = __syncthreads_and(staged) != 0;
+    if (!staged && hot > 0 && threadIdx.x == 0) atomicAdd(&cd->c.stage_timeouts, 1u);
+    const int32_t hlim = staged ? hot : 0;  // without the staged block every message is gathered
+    uint32_t mv[kEPT];
+    if (gwarp < a.ntiles) pull_gather(msgc, s_hot, hlim, gwarp * (int64_t)kWTile + lane * kEPT, a.m, cur.r, mv);
+
     for (int64_t k = gwarp; k < a.ntiles; k += nwarps) {
-        int32_t un[kEPT];
-        uint32_t wn[kEPT], hwn = 0u;
-        int32_t c0n = 0;
-        {   // software pipeline: issue the next tile's loads now
-            const int64_t kn = k + nwarps;
-            const int64_t pn = kn * (int64_t)kWTile + (int64_t)lane * kEPT;
-            if (kn < a.ntiles) {
-                if (pn < a.m) {
-                    load8(a.row, (int32_t)pn, un);
-                    if (SSSP) load8(a.cw, (int32_t)pn, wn);
-                }
-                hwn = __ldcs(a.dc_head + (pn >> 5));
-                c0n = __ldg(a.dc_tile + kn);
-            }
-        }
         const int64_t e0 = k * (int64_t)kWTile + (int64_t)lane * kEPT;
+        uint32_t cand[kEPT];
         uint32_t vmask = 0u;
 #pragma unroll
-        for (int q = 0; q < kEPT; ++q)
-            if (e0 + q < a.m) vmask |= 1u << q;
-        const uint32_t heads = (hw >> ((lane & 3) * 8)) & 0xFFu & vmask;
-        scanned += (unsigned)__popc(vmask);
-        uint32_t cand[kEPT];
-#pragma unroll
         for (int q = 0; q < kEPT; ++q) {
-            if (SSSP) cand[q] = ((vmask >> q) & 1u) ? sat_add(__ldg(msgc + u[q]), wt[q]) : kInf;
-            else cand[q] = (((vmask >> q) & 1u) && test_bit(bvc, u[q])) ? t + 1u : kInf;
+            const bool ok = e0 + q < a.m;
+            vmask |= (ok ? 1u : 0u) << q;
+            cand[q] = ok ? sat_add(mv[q], cur.weight(q)) : kInf;
         }
+        const uint32_t heads = (cur.hw >> ((lane & 3) * 8)) & 0xFFu & vmask;
+        const int32_t c0 = cur.c0;
+        // pipeline: gather tile k+1's messages, stream tile k+2's sources
+        const int64_t k1 = k + nwarps, k2 = k1 + nwarps;
+        if (k1 < a.ntiles) pull_gather(msgc, s_hot, hlim, k1 * (int64_t)kWTile + lane * kEPT, a.m, nxt.r, mv);
+        cur = nxt;
+        if (k2 < a.ntiles) pull_load_tile<WB>(a, k2, lane, nxt);
+        scanned += (unsigned)__popc(vmask);
+
         // column numbering: heads before this lane, and whether the tile starts a column
         const uint32_t nh = (uint32_t)__popc(heads);
         const uint32_t hincl = warp_incl_scan(nh);
         const uint32_t hex = hincl - nh;
-        const uint32_t first_is_head = __shfl_sync(kFull, heads & 1u, 0);
+        const uint32_t bal_first = __ballot_sync(kFull, heads & 1u);  // lanes whose first edge starts a column
+        const uint32_t bal_seen = __ballot_sync(kFull, heads != 0u);  // lanes holding a column start
+        const uint32_t first_is_head = bal_first & 1u;
         // column of edge q of this lane: c0 + (heads in the tile up to and including
         // edge q) - (1 if the tile's first edge is a head)
         const int32_t col_base = c0 + (int32_t)hex - (int32_t)first_is_head;
@@ -496,35 +608,34 @@ __global__ void __launch_bounds__(kThreads, 4) trav_pull_a(TravArgs a) {
         // lane runs: F before the first head, interior runs complete, L from the last head
         uint32_t F = kInf, run = kInf;
         int32_t run_col = lane_col;
-        bool seen = false;
+        const bool seen = heads != 0u;
 #pragma unroll
         for (int q = 0; q < kEPT; ++q) {
             if ((heads >> q) & 1u) {
-                if (!seen) F = run;
-                else if (run != kInf) y[run_col] = run;  // column entirely inside this lane
-                seen = true;
+                if ((heads & ((1u << q) - 1u)) != 0u) {  // an earlier head in this lane
+                    if (run != kInf) y[run_col] = run;   // column entirely inside this lane
+                } else {
+                    F = run;
+                }
                 run = kInf;
                 run_col = col_base + (int32_t)__popc(heads & ((2u << q) - 1u));
             }
             run = min(run, cand[q]);
         }
         if (!seen) F = run;
-        const uint32_t L = run;
-        // segmented min-scan across lanes; a lane with a head starts a new segment
-        uint32_t R = seen ? L : F;
-        uint32_t fr = seen ? 1u : 0u;
+        // segmented min-scan across lanes: a lane holding a column start begins a
+        // segment; its start lane comes from the ballot, so only values move
+        uint32_t R = seen ? run : F;
+        const uint32_t le = bal_seen & (0xFFFFFFFFu >> (31 - lane));  // seen lanes <= this one
+        const int seg0 = le ? 31 - __clz(le) : -1;                    // -1: began before the tile
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t Ru = __shfl_up_sync(kFull, R, o);
-            const uint32_t fu = __shfl_up_sync(kFull, fr, o);
-            if (lane >= o) {
-                if (!fr) R = min(R, Ru);
-                fr |= fu;
-            }
+            if (lane - o >= max(seg0, 0)) R = min(R, Ru);
         }
         uint32_t Rprev = __shfl_up_sync(kFull, R, 1);
-        uint32_t fprev = __shfl_up_sync(kFull, fr, 1);
-        if (lane == 0) { Rprev = kInf; fprev = 0u; }
+        const bool fprev = lane > 0 && (bal_seen & ((1u << lane) - 1u)) != 0u;  // lane-1's segment began in the tile
+        if (lane == 0) Rprev = kInf;
         if (seen && !(heads & 1u)) {  // this lane's first edges finish a column begun to its left
             const uint32_t total = min(F, Rprev);
             if (total != kInf) {
@@ -534,25 +645,117 @@ __global__ void __launch_bounds__(kThreads, 4) trav_pull_a(TravArgs a) {
         }
         // The segment ending with this lane is complete when the next lane starts a
         // new column; the tile's last segment may continue in the next tile.
-        const uint32_t next_head = __shfl_down_sync(kFull, heads & 1u, 1);
+        const bool next_head = lane < 31 && ((bal_first >> (lane + 1)) & 1u);
         if (R != kInf && (lane == 31 || next_head)) {
             const int32_t end_col = c0 + (int32_t)hincl - (int32_t)first_is_head;
-            if (lane < 31 && fr) y[end_col] = R;  // its first edge lies in this tile
+            if (lane < 31 && seg0 >= 0) y[end_col] = R;  // its first edge lies in this tile
             else atomicMin(&y[end_col], R);
         }
-#pragma unroll
-        for (int q = 0; q < kEPT; ++q) {
-            u[q] = un[q];
-            wt[q] = wn[q];
-        }
-        hw = hwn;
-        c0 = c0n;
     }
     scanned = warp_sum_u64(scanned);
     if (lane == 0 && scanned) atomicAdd(&cd->c.scanned_edges, scanned);
+    if (!staged && hot > 0) mbar_wait_bounded(&s_bar, 0u);  // let a late copy land before the CTA exits
 }
 
-template <bool SSSP>
+// Next-frontier bits of one warp's 32 columns (vertex v per lane, ascending across
+// lanes; lanes past the last column carry v = INT32_MAX): lanes sharing a bitvector
+// word are adjacent, so a segmented OR-scan leaves one atomic per word.  Warp-collective.
+__device__ __forceinline__ void warp_set_bits(uint32_t* bv, int32_t v, bool want) {
+    const int lane = threadIdx.x & 31;
+    const int32_t wd = v >> 5;
+    const int32_t wd_prev = __shfl_up_sync(kFull, wd, 1);
+    uint32_t R = want ? 1u << (v & 31) : 0u;
+    uint32_t f = (lane == 0 || wd_prev != wd) ? 1u : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t Ru = __shfl_up_sync(kFull, R, o);
+        const uint32_t fu = __shfl_up_sync(kFull, f, o);
+        if (lane >= o && !f) R |= Ru;
+        if (lane >= o) f |= fu;
+    }
+    const int32_t wd_next = __shfl_down_sync(kFull, wd, 1);
+    if (R != 0u && (lane == 31 || wd_next != wd)) atomicOr(&bv[wd], R);
+}
+
+constexpr int kBuShort = 8;  // in-edges a lane checks alone before its warp helps
+
+// BFS pull superstep in one kernel: the bottom-up search and Apply.  A column is
+// owned by one lane, so the depth is written and the vertex queued directly.
+__global__ void __launch_bounds__(kThreads, 4) trav_pull_bu(TravArgs a) {
+    TravCtlDev* cd = a.ctl;
+    if (cd->c.done || cd->c.dir != 1u) return;
+    const uint32_t t = cd->c.iter;
+    const int cur = (int)(t % 3u), nxt = (int)((t + 1u) % 3u), clr = (int)((t + 2u) % 3u);
+    relax_prologue<false>(a, &cd->c, t, clr);
+    __shared__ WarpQ s_q[kWarps];
+    __shared__ unsigned long long s_stat[5];
+    if (threadIdx.x < 5) s_stat[threadIdx.x] = 0ull;
+    if ((threadIdx.x & 31) < 2) s_q[threadIdx.x >> 5].n[threadIdx.x & 31] = 0u;
+    __syncthreads();
+    Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, &s_q[threadIdx.x >> 5]};
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+    const uint32_t* __restrict__ bvc = a.bv[cur];
+    const int32_t* __restrict__ row = a.row;
+    for (int64_t base = gwarp * 32; base < a.dc_ncols; base += nwarps * 32) {
+        const int64_t c = base + lane;
+        int32_t v = 0x7fffffff, p = 0, end = 0;
+        if (c < a.dc_ncols) {
+            v = __ldg(a.dc_jc + c);
+            if (a.dist[v] == kInf) {
+                p = __ldg(a.dc_cp + c);
+                end = __ldg(a.dc_cp + c + 1);
+                acc.verts++;
+            }
+        }
+        bool found = false;
+        // each lane alone: up to kBuShort in-edges, four independent loads at a time
+        const int32_t lim = min(end, p + kBuShort);
+        while (p < lim && !found) {
+            int32_t u[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) u[k] = (p + k < lim) ? __ldg(row + p + k) : -1;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) found |= u[k] >= 0 && test_bit(bvc, u[k]);
+            const int32_t nn = min(4, lim - p);
+            acc.scanned += (unsigned)nn;
+            p += nn;
+        }
+        // the rest of long unvisited columns, one column at a time by the whole warp
+        uint32_t rest = __ballot_sync(kFull, !found && p < end);
+        while (rest) {
+            const int L = __ffs(rest) - 1;
+            rest &= rest - 1u;
+            const int32_t pb = __shfl_sync(kFull, p, L), pe = __shfl_sync(kFull, end, L);
+            bool hit = false;
+            for (int32_t q0 = pb; q0 < pe && !hit; q0 += 128) {
+                bool h = false;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int32_t q = q0 + k * 32 + lane;
+                    if (q < pe) {
+                        h |= test_bit(bvc, __ldg(row + q));
+                        acc.scanned++;
+                    }
+                }
+                hit = __any_sync(kFull, h);
+            }
+            if (lane == L) found = hit;
+        }
+        if (found) a.dist[v] = t + 1u;
+        warp_set_bits(a.bv[nxt], v, found);
+        bool wa[kEPT] = {found, false, false, false, false, false, false, false};
+        int32_t va[kEPT] = {found ? v : 0, 0, 0, 0, 0, 0, 0, 0};
+        enqueue_batch<true>(a, wa, va, nxt, acc);
+    }
+    flush_acc(a, acc, nxt, true, s_stat);
+}
+
+// SSSP Apply after trav_pull_a: four columns per lane per step (independent loads
+// in flight), coalesced across the warp for each of the four.
+constexpr int kColsPerLane = 4;
+
 __global__ void __launch_bounds__(kThreads) trav_pull_b(TravArgs a) {
     TravCtlDev* cd = a.ctl;
     if (cd->c.done || cd->c.dir != 1u) return;
@@ -568,28 +771,38 @@ __global__ void __launch_bounds__(kThreads) trav_pull_b(TravArgs a) {
     const int64_t gwarp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
     uint32_t* __restrict__ y = a.ycol;
-    for (int64_t base = gwarp * 32; base < a.dc_ncols; base += nwarps * 32) {
-        const int64_t c = base + lane;
-        bool want = false;
-        int32_t v = 0;
-        if (c < a.dc_ncols) {
-            const uint32_t b = y[c];
-            if (b != kInf) {
-                y[c] = kInf;
-                v = __ldg(a.dc_jc + c);
+    uint32_t* __restrict__ msgn = a.msg[(t + 1u) & 1u];
+    constexpr int kSpan = 32 * kColsPerLane;
+    for (int64_t base = gwarp * kSpan; base < a.dc_ncols; base += nwarps * kSpan) {
+        uint32_t b[kColsPerLane], dv[kColsPerLane];
+        int32_t v[kColsPerLane];
+#pragma unroll
+        for (int k = 0; k < kColsPerLane; ++k) {
+            const int64_t c = base + 32 * k + lane;
+            b[k] = c < a.dc_ncols ? y[c] : kInf;
+            v[k] = c < a.dc_ncols ? __ldg(a.dc_jc + c) : 0x7fffffff;
+        }
+#pragma unroll
+        for (int k = 0; k < kColsPerLane; ++k) dv[k] = b[k] != kInf ? a.dist[v[k]] : 0u;
+        bool wa[kEPT] = {false, false, false, false, false, false, false, false};
+        int32_t va[kEPT] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int k = 0; k < kColsPerLane; ++k) {
+            if (b[k] != kInf) {
+                y[base + 32 * k + lane] = kInf;
                 acc.verts++;
-                if (b < a.dist[v]) {
-                    a.dist[v] = b;
-                    atomicOr(&a.bv[nxt][v >> 5], 1u << (v & 31));
-                    want = true;
+                if (b[k] < dv[k]) {
+                    a.dist[v[k]] = b[k];
+                    msgn[a.dc_rank[base + 32 * k + lane]] = b[k];  // superstep t+1's message (finalize skips pulls)
+                    wa[k] = true;
+                    va[k] = v[k];
                 }
             }
+            warp_set_bits(a.bv[nxt], v[k], wa[k]);
         }
-        bool wa[kEPT] = {want, false, false, false, false, false, false, false};
-        int32_t va[kEPT] = {v, 0, 0, 0, 0, 0, 0, 0};
-        enqueue_batch<!SSSP>(a, wa, va, nxt, acc);
+        enqueue_batch<false>(a, wa, va, nxt, acc);
     }
-    flush_acc(a, acc, nxt, !SSSP, s_stat);
+    flush_acc(a, acc, nxt, false, s_stat);
 }
 
 template <bool SSSP>
@@ -615,18 +828,19 @@ template <bool SSSP>
 __global__ void __launch_bounds__(kThreads) trav_finalize(TravArgs a) {
     TravCtlDev* cd = a.ctl;
     TravCtl* c = &cd->c;
-    __shared__ uint32_t s_t, s_done, s_last;
+    __shared__ uint32_t s_t, s_done, s_last, s_dir;
     __shared__ uint32_t s_cnt[4];
     if (threadIdx.x == 0) {
         s_t = c->iter;
         s_done = c->done;
+        s_dir = c->dir;
     }
     if (threadIdx.x < 4) s_cnt[threadIdx.x] = c->count[(c->iter + 1u) % 3u][threadIdx.x];
     __syncthreads();
     if (s_done) return;
     const uint32_t t = s_t;
     const int nxt = (int)((t + 1u) % 3u);
-    if (SSSP) {  // messages of superstep t+1: the property values fixed now
+    if (SSSP && s_dir == 0u) {  // messages of superstep t+1 after a push (pull_b writes its own)
         const uint32_t n1 = s_cnt[1], n2 = s_cnt[2], n3 = s_cnt[3];
         uint32_t* ms = a.msg[(t + 1u) & 1u];
         for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < (int64_t)n1 + n2 + n3;
@@ -639,7 +853,7 @@ __global__ void __launch_bounds__(kThreads) trav_finalize(TravArgs a) {
                 if (it.y != 0) continue;
                 v = it.x;
             }
-            ms[v] = a.dist[v];
+            ms[a.rank[v]] = a.dist[v];
         }
     }
     __syncthreads();
@@ -697,7 +911,7 @@ __global__ void seed_frontier(TravArgs a, const int32_t* __restrict__ verts, int
         v = 0;
     } else if (i < count) {
         a.dist[v] = 0u;
-        a.msg[0][v] = 0u;
+        if (!bfs) a.msg[0][a.rank[v]] = 0u;
         const uint32_t bit = 1u << (v & 31);
         want = (atomicOr(&a.bv[0][v >> 5], bit) & bit) == 0u;
     }
@@ -720,7 +934,7 @@ __global__ void seed_all(TravArgs a, int bfs) {
     const int32_t v = want ? (int32_t)i : 0;
     if (want) {
         a.dist[v] = 0u;
-        a.msg[0][v] = 0u;
+        if (!bfs) a.msg[0][a.rank[v]] = 0u;
         atomicOr(&a.bv[0][v >> 5], 1u << (v & 31));
     }
     Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, nullptr};
@@ -741,10 +955,20 @@ __global__ void fill_u32(uint32_t* p, int64_t n, uint32_t v) {
         p[i] = v;
 }
 
+// Sum of out-degrees of reached vertices; 16-byte loads of both arrays (both
+// start 256-byte aligned), the last n % 4 vertices one by one.
 __global__ void reached_kernel(const uint32_t* __restrict__ dist, const int32_t* __restrict__ out_deg, int64_t n,
                                unsigned long long* out) {
     unsigned long long s = 0;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n4 = n >> 2;
+    for (int64_t i = tid; i < n4; i += stride) {
+        const uint4 d = reinterpret_cast<const uint4*>(dist)[i];
+        const int4 o = __ldg(reinterpret_cast<const int4*>(out_deg) + i);
+        s += (d.x != kInf ? (uint32_t)o.x : 0u) + (unsigned long long)(d.y != kInf ? (uint32_t)o.y : 0u) +
+             (unsigned long long)(d.z != kInf ? (uint32_t)o.z : 0u) + (unsigned long long)(d.w != kInf ? (uint32_t)o.w : 0u);
+    }
+    for (int64_t v = (n4 << 2) + tid; v < n; v += stride)
         if (dist[v] != kInf) s += (unsigned long long)out_deg[v];
     s = warp_sum_u64(s);
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
@@ -793,6 +1017,7 @@ TravArgs make_args(gm_graph* g) {
     a.col_ptr = as<int32_t>(g->col_ptr);
     a.row = as<int32_t>(g->row);
     a.cw = as<uint32_t>(g->cw);
+    a.cw8 = as<uint8_t>(g->cw8);
     a.out_deg = as<int32_t>(g->out_deg);
     a.in_deg = as<int32_t>(g->in_deg);
     a.out_bin = as<uint8_t>(g->out_bin);
@@ -817,6 +1042,12 @@ TravArgs make_args(gm_graph* g) {
         for (int b = 0; b < 3; ++b) a.q[s][b] = w.q[s][b];
         a.qc[s] = w.qc[s];
     }
+    a.rank = as<int32_t>(g->src_rank);
+    a.row_r = as<int32_t>(g->row_r);
+    a.dc_rank = as<int32_t>(g->dc_rank);
+    a.hot = g->src_rank.p ? (int32_t)std::min<int64_t>(std::min<int64_t>(kHotMax, g->tune.pull_stage),
+                                                         g->n & ~(int64_t)3)
+                          : 0;
     a.ctl = as<TravCtlDev>(g->ctl_buf);
     a.use_cond = 0;
     return a;
@@ -836,12 +1067,29 @@ int push_grid() {
     return blocks;
 }
 
+// trav_pull_a runs one CTA of kPullThreads per SM with up to kHotMax * 4 bytes of
+// dynamic shared memory; the attribute is set once per process.
 int pull_grid() {
-    static int blocks = grid_for(trav_pull_a<true>);
+    static int blocks = [] {
+        const int bytes = (int)(kHotMax * sizeof(uint32_t));
+        cudaFuncSetAttribute(trav_pull_a<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaFuncSetAttribute(trav_pull_a<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        return num_sms();
+    }();
+    return blocks;
+}
+
+int pull_bu_grid() {
+    static int blocks = grid_for(trav_pull_bu);
     return blocks;
 }
 
 int finalize_grid() { return 2 * num_sms(); }
+
+int pull_b_grid() {
+    static int blocks = grid_for(trav_pull_b);
+    return blocks;
+}
 
 #define LAUNCH_OK()                                                                             \
     do {                                                                                        \
@@ -920,14 +1168,20 @@ gm_status build_loop_graph(gm_graph* g, bool sssp) {
     e = cudaGraphAddKernelNode(&n0, body, nullptr, 0, &kp);
     cudaGraphNode_t n1b;
     if (e == cudaSuccess) {
-        kp.func = sssp ? (void*)trav_pull_a<true> : (void*)trav_pull_a<false>;
-        kp.gridDim = dim3((unsigned)pull_grid());
+        kp.func = !sssp ? (void*)trav_pull_bu : a.cw8 ? (void*)trav_pull_a<1> : (void*)trav_pull_a<4>;
+        kp.gridDim = dim3((unsigned)(sssp ? pull_grid() : pull_bu_grid()));
+        kp.blockDim = dim3(sssp ? kPullThreads : kThreads);
+        kp.sharedMemBytes = sssp ? (unsigned)a.hot * 4u : 0u;
         e = cudaGraphAddKernelNode(&n1, body, &n0, 1, &kp);
+        kp.blockDim = dim3(kThreads);
+        kp.sharedMemBytes = 0u;
     }
-    if (e == cudaSuccess) {
-        kp.func = sssp ? (void*)trav_pull_b<true> : (void*)trav_pull_b<false>;
-        kp.gridDim = dim3((unsigned)finalize_grid());
+    if (e == cudaSuccess && sssp) {
+        kp.func = (void*)trav_pull_b;
+        kp.gridDim = dim3((unsigned)pull_b_grid());
         e = cudaGraphAddKernelNode(&n1b, body, &n1, 1, &kp);
+    } else {
+        n1b = n1;  // the BFS pull applies in trav_pull_bu
     }
     if (e == cudaSuccess) {
         kp.func = sssp ? (void*)trav_finalize<true> : (void*)trav_finalize<false>;
@@ -952,6 +1206,7 @@ gm_status build_loop_graph(gm_graph* g, bool sssp) {
 gm_status trav_prepare(gm_graph* g) {
     cudaStream_t s = g->stream;
     const int64_t n = g->n > 0 ? g->n : 1;
+    if (g->kind == GM_SSSP) GM_TRY(build_source_ranks(g));
     GM_TRY(dev_alloc(g->state, sizeof(uint32_t) * n, s));
     size_t wb = 0;
     g->work.p = nullptr;
@@ -1008,7 +1263,7 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
         GM_CUDA_TRY(cudaGraphLaunch(g->loop_exec, s));
     } else {
         TravArgs a = make_args(g);
-        const int pg = push_grid(), lg = pull_grid(), fg = finalize_grid();
+        const int pg = push_grid(), lg = sssp ? pull_grid() : pull_bu_grid(), fg = finalize_grid();
         cudaEvent_t ev0 = nullptr, ev1 = nullptr, evA = nullptr, evB = nullptr;
         if (g->tune.profile) {
             GM_CUDA_TRY(cudaEventCreate(&ev0));
@@ -1032,13 +1287,13 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
             if (sssp) trav_push<true><<<pg, kThreads, 0, s>>>(a);
             else trav_push<false><<<pg, kThreads, 0, s>>>(a);
             if (evA) cudaEventRecord(evA, s);
-            if (sssp) trav_pull_a<true><<<lg, kThreads, 0, s>>>(a);
-            else trav_pull_a<false><<<lg, kThreads, 0, s>>>(a);
+            if (sssp && a.cw8) trav_pull_a<1><<<lg, kPullThreads, (size_t)a.hot * 4u, s>>>(a);
+            else if (sssp) trav_pull_a<4><<<lg, kPullThreads, (size_t)a.hot * 4u, s>>>(a);
+            else trav_pull_bu<<<lg, kThreads, 0, s>>>(a);
             if (evB) cudaEventRecord(evB, s);
-            if (sssp) trav_pull_b<true><<<fg, kThreads, 0, s>>>(a);
-            else trav_pull_b<false><<<fg, kThreads, 0, s>>>(a);
+            if (sssp) trav_pull_b<<<pull_b_grid(), kThreads, 0, s>>>(a);
             if (ev1) cudaEventRecord(ev1, s);
-            g_launches += 3;
+            g_launches += sssp ? 3 : 2;
             LAUNCH_OK();
             if (sssp) trav_finalize<true><<<fg, kThreads, 0, s>>>(a);
             else trav_finalize<false><<<fg, kThreads, 0, s>>>(a);
@@ -1074,7 +1329,7 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
     }
     GM_CUDA_TRY(cudaMemcpyAsync(hp, g->ctl_buf.p, sizeof(TravCtlDev), cudaMemcpyDeviceToHost, s));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
-    if (!host_loop) g_launches += 4ull * hp->c.iters_done;
+    if (!host_loop) g_launches += (sssp ? 4ull : 3ull) * hp->c.iters_done;
     g->stats.supersteps = (int32_t)hp->c.iters_done;
     g->stats.pushes = (int32_t)hp->c.pushes;
     g->stats.pulls = (int32_t)hp->c.pulls;
@@ -1083,7 +1338,12 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
     if (iters_done) *iters_done = (int32_t)hp->c.iters_done;
     const uint32_t bad = hp->c.bad_ids;
     const uint32_t guard = hp->c.guard_hit;
+    const uint32_t stage_to = hp->c.stage_timeouts;
     GM_TRY(reset_frontier(g));
+    if (stage_to) {  // the results are still exact (those CTAs gathered every message from global memory)
+        set_error("gm_run: %u pull CTAs timed out waiting for their shared-memory staging copy", stage_to);
+        return GM_ERR_TIMEOUT;
+    }
     if (guard) {
         set_error("gm_run: superstep loop exceeded n + 1 supersteps (internal error)");
         return GM_ERR_TIMEOUT;

@@ -57,6 +57,7 @@ gm_status gm_autotune(gm_graph* g, int32_t kind, const int32_t* sources, int32_t
     std::vector<Knob> knobs;
     if (kind == GM_SSSP) {
         knobs.push_back({GM_OPT_SSSP_PULL_PPM, {5000, 20000, 50000, 100000, 200000, 350000, 1000000}});
+        knobs.push_back({GM_OPT_PULL_STAGE, {0, 16384, 32768, 40960, 49152}});
     } else {
         knobs.push_back({GM_OPT_ALPHA_X1000, {2000, 6000, 14000, 30000, 80000}});
         knobs.push_back({GM_OPT_BETA_X1000, {6000, 24000, 96000}});
@@ -71,6 +72,7 @@ gm_status gm_autotune(gm_graph* g, int32_t kind, const int32_t* sources, int32_t
             case GM_OPT_BETA_X1000: cur = (int64_t)(g->tune.beta * 1e3 + 0.5); break;
             case GM_OPT_BIN_LARGE: cur = g->tune.bin_large; break;
             case GM_OPT_BIN_SMALL: cur = g->tune.bin_small; break;
+            case GM_OPT_PULL_STAGE: cur = g->tune.pull_stage; break;
         }
         int64_t best_v = cur;
         for (int64_t v : k.vals) {
@@ -98,6 +100,7 @@ gm_status gm_autotune(gm_graph* g, int32_t kind, const int32_t* sources, int32_t
         out->bin_small = g->tune.bin_small;
         out->bin_large = g->tune.bin_large;
         out->best_ms = best;
+        out->pull_stage = g->tune.pull_stage;
     }
     return GM_OK;
 }

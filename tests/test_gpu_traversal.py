@@ -142,6 +142,44 @@ def test_saturating_weights(gm):
     assert got.tolist() == [0, 0xFFFFFFF0, gm.INF_U32]
 
 
+@pytest.mark.parametrize("direction", DIRS)
+def test_weight_width(gm, direction):
+    """Weights below 256 are read as one byte by the SSSP pull, wider ones as four;
+    both give the oracle's distances and superstep counts."""
+    rng = np.random.default_rng(77)
+    n, s, d, _ = rmat_case(12)
+    for hi, width in ((255, 1), (1 << 20, 4)):
+        w = rng.integers(1, hi + 1, len(s)).astype(np.uint32)
+        g = gm.Graph(n, s, d, w)
+        assert g.scalar(gm.GM_SCALAR_PULL_WEIGHT_BYTES) == width
+        g.set_option(gm.GM_OPT_DIRECTION, direction)
+        og = oracle.Graph(n, s, d, w)
+        for src in synth.pick_sources(n, s, d, 2, seed=78):
+            got, it = _run(gm, g, gm.GM_SSSP, [src])
+            ref, rit = og.sssp([src])
+            assert np.array_equal(got, ref) and it == rit
+    assert gm.Graph(n, s, d).scalar(gm.GM_SCALAR_PULL_WEIGHT_BYTES) == 0
+
+
+@pytest.mark.parametrize("stage", [0, 1000, 49152])
+@pytest.mark.parametrize("direction", [0, 2])
+def test_sssp_staged_and_gathered_messages(gm, direction, stage):
+    """At scale 17 (n = 131,072) the SSSP pull stages the messages of the `stage`
+    highest-out-degree sources in shared memory and gathers the rest: both kinds
+    of source, one-byte and four-byte weights, match the oracle."""
+    n, s, d, w = rmat_case(17, weighted=True, seed=synth.BASE_SEED + 17)
+    rng = np.random.default_rng(17)
+    for ww in (w, rng.integers(1, 1 << 24, len(s)).astype(np.uint32)):
+        g = gm.Graph(n, s, d, ww)
+        g.set_option(gm.GM_OPT_DIRECTION, direction)
+        g.set_option(gm.GM_OPT_PULL_STAGE, stage)
+        og = oracle.Graph(n, s, d, ww)
+        for src in synth.pick_sources(n, s, d, 2, seed=170):
+            got, it = _run(gm, g, gm.GM_SSSP, [src])
+            ref, rit = og.sssp([src])
+            assert np.array_equal(got, ref) and it == rit
+
+
 def test_symmetrized_bfs(gm):
     n, s, d, _ = rmat_case(12)
     flags = CLEAN | oracle.SYMMETRIZE
