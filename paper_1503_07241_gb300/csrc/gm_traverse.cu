@@ -93,9 +93,11 @@ struct Acc {
     WarpQ* wq;  // nullptr: enqueue straight to the global queue
 };
 
+// a + b, infinity when the sum reaches or passes UINT32_MAX (a sum equal to
+// UINT32_MAX already is infinity; one that wrapped is below b).
 __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) {
     const uint32_t s = a + b;
-    return (s < a || s == kInf) ? kInf : s;
+    return s < b ? kInf : s;
 }
 
 __device__ __forceinline__ bool test_bit(const uint32_t* bv, int32_t v) {
@@ -503,10 +505,11 @@ struct PullTile {
     }
 };
 
+// Edge positions are 32-bit: m < 2^31, and a tile position is below m + kWTile.
 template <int WB>
-__device__ __forceinline__ void pull_load_tile(const TravArgs& a, int64_t k, int lane, PullTile<WB>& x) {
-    const int64_t p = k * (int64_t)kWTile + (int64_t)lane * kEPT;
-    if (p < a.m) {
+__device__ __forceinline__ void pull_load_tile(const TravArgs& a, uint32_t k, int lane, PullTile<WB>& x) {
+    const uint32_t p = k * (uint32_t)kWTile + (uint32_t)lane * kEPT;
+    if (p < (uint32_t)a.m) {
         load8(a.row_r, (int32_t)p, x.r);
         if (WB == 1) {
             const uint2 v = __ldcs(reinterpret_cast<const uint2*>(a.cw8 + p));
@@ -521,14 +524,17 @@ __device__ __forceinline__ void pull_load_tile(const TravArgs& a, int64_t k, int
     x.c0 = __ldg(a.dc_tile + k);
 }
 
+// Number of a lane's 8 edges that lie below m.
+__device__ __forceinline__ uint32_t lane_valid(uint32_t e0, uint32_t m) { return e0 < m ? min(8u, m - e0) : 0u; }
+
 // Messages of a tile's sources: staged ranks from shared memory, the rest from
 // global memory.  Edges at or past m read rank 0's message (present whenever
 // there is an edge) and are masked later.
 __device__ __forceinline__ void pull_gather(const uint32_t* __restrict__ msgc, const uint32_t* s_hot, int32_t hlim,
-                                            int64_t e0, int64_t m, const int32_t (&r)[kEPT], uint32_t (&mv)[kEPT]) {
+                                            uint32_t nv, const int32_t (&r)[kEPT], uint32_t (&mv)[kEPT]) {
 #pragma unroll
     for (int q = 0; q < kEPT; ++q) {
-        const int32_t rq = e0 + q < m ? r[q] : 0;
+        const int32_t rq = (uint32_t)q < nv ? r[q] : 0;
         mv[q] = rq < hlim ? s_hot[rq] : __ldg(msgc + rq);
     }
 }
@@ -558,41 +564,38 @@ __global__ void __launch_bounds__(kPullThreads, 1) trav_pull_a(TravArgs a) {
     }
     relax_prologue<true>(a, &cd->c, t, clr);
     const int lane = threadIdx.x & 31;
-    const int64_t gwarp = ((int64_t)blockIdx.x * kPullThreads + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * kPullThreads) >> 5;
+    const uint32_t gwarp = (blockIdx.x * kPullThreads + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * kPullThreads) >> 5;
+    const uint32_t ntiles = (uint32_t)a.ntiles, m = (uint32_t)a.m;
     uint32_t* __restrict__ y = a.ycol;
     unsigned long long scanned = 0;
 
     // the warp's first two tiles stream in while the staging copy runs
     PullTile<WB> cur, nxt;
-    if (gwarp < a.ntiles) pull_load_tile<WB>(a, gwarp, lane, cur);
-    if (gwarp + nwarps < a.ntiles) pull_load_tile<WB>(a, gwarp + nwarps, lane, nxt);
+    if (gwarp < ntiles) pull_load_tile<WB>(a, gwarp, lane, cur);
+    if (gwarp + nwarps < ntiles) pull_load_tile<WB>(a, gwarp + nwarps, lane, nxt);
     __syncthreads();  // the barrier is initialised before anyone waits on it
     bool staged = hot > 0 && mbar_wait_bounded(&s_bar, 0u);
     staged = __syncthreads_and(staged) != 0;
     if (!staged && hot > 0 && threadIdx.x == 0) atomicAdd(&cd->c.stage_timeouts, 1u);
     const int32_t hlim = staged ? hot : 0;  // without the staged block every message is gathered
     uint32_t mv[kEPT];
-    if (gwarp < a.ntiles) pull_gather(msgc, s_hot, hlim, gwarp * (int64_t)kWTile + lane * kEPT, a.m, cur.r, mv);
+    if (gwarp < ntiles) pull_gather(msgc, s_hot, hlim, lane_valid(gwarp * kWTile + lane * kEPT, m), cur.r, mv);
 
-    for (int64_t k = gwarp; k < a.ntiles; k += nwarps) {
-        const int64_t e0 = k * (int64_t)kWTile + (int64_t)lane * kEPT;
+    for (uint32_t k = gwarp; k < ntiles; k += nwarps) {
+        const uint32_t nv = lane_valid(k * kWTile + lane * kEPT, m);
+        const uint32_t vmask = (1u << nv) - 1u;
         uint32_t cand[kEPT];
-        uint32_t vmask = 0u;
 #pragma unroll
-        for (int q = 0; q < kEPT; ++q) {
-            const bool ok = e0 + q < a.m;
-            vmask |= (ok ? 1u : 0u) << q;
-            cand[q] = ok ? sat_add(mv[q], cur.weight(q)) : kInf;
-        }
-        const uint32_t heads = (cur.hw >> ((lane & 3) * 8)) & 0xFFu & vmask;
+        for (int q = 0; q < kEPT; ++q) cand[q] = (uint32_t)q < nv ? sat_add(mv[q], cur.weight(q)) : kInf;
+        const uint32_t heads = (cur.hw >> ((lane & 3) * 8)) & vmask;
         const int32_t c0 = cur.c0;
         // pipeline: gather tile k+1's messages, stream tile k+2's sources
-        const int64_t k1 = k + nwarps, k2 = k1 + nwarps;
-        if (k1 < a.ntiles) pull_gather(msgc, s_hot, hlim, k1 * (int64_t)kWTile + lane * kEPT, a.m, nxt.r, mv);
+        const uint32_t k1 = k + nwarps, k2 = k1 + nwarps;
+        if (k1 < ntiles) pull_gather(msgc, s_hot, hlim, lane_valid(k1 * kWTile + lane * kEPT, m), nxt.r, mv);
         cur = nxt;
-        if (k2 < a.ntiles) pull_load_tile<WB>(a, k2, lane, nxt);
-        scanned += (unsigned)__popc(vmask);
+        if (k2 < ntiles) pull_load_tile<WB>(a, k2, lane, nxt);
+        scanned += nv;
 
         // column numbering: heads before this lane, and whether the tile starts a column
         const uint32_t nh = (uint32_t)__popc(heads);
@@ -677,7 +680,8 @@ __device__ __forceinline__ void warp_set_bits(uint32_t* bv, int32_t v, bool want
     if (R != 0u && (lane == 31 || wd_next != wd)) atomicOr(&bv[wd], R);
 }
 
-constexpr int kBuShort = 8;  // in-edges a lane checks alone before its warp helps
+constexpr int kBuShort = 8;      // in-edges a lane checks alone before its warp helps
+constexpr int kColsPerLane = 4;  // columns a lane handles per step in the pull-side column kernels
 
 // BFS pull superstep in one kernel: the bottom-up search and Apply.  A column is
 // owned by one lane, so the depth is written and the vertex queued directly.
@@ -698,55 +702,85 @@ __global__ void __launch_bounds__(kThreads, 4) trav_pull_bu(TravArgs a) {
     const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
     const uint32_t* __restrict__ bvc = a.bv[cur];
     const int32_t* __restrict__ row = a.row;
-    for (int64_t base = gwarp * 32; base < a.dc_ncols; base += nwarps * 32) {
-        const int64_t c = base + lane;
-        int32_t v = 0x7fffffff, p = 0, end = 0;
-        if (c < a.dc_ncols) {
-            v = __ldg(a.dc_jc + c);
-            if (a.dist[v] == kInf) {
-                p = __ldg(a.dc_cp + c);
-                end = __ldg(a.dc_cp + c + 1);
+    constexpr int kSpan = 32 * kColsPerLane;
+    // kColsPerLane columns per lane (32 apart, so each group is coalesced and
+    // ascending across the warp), their loads issued together
+    for (int64_t base = gwarp * kSpan; base < a.dc_ncols; base += nwarps * kSpan) {
+        int32_t v[kColsPerLane], p[kColsPerLane], end[kColsPerLane];
+        uint32_t dv[kColsPerLane];
+#pragma unroll
+        for (int k = 0; k < kColsPerLane; ++k) {
+            const int64_t c = base + 32 * k + lane;
+            v[k] = c < a.dc_ncols ? __ldg(a.dc_jc + c) : 0x7fffffff;  // past the last column: a word of its own
+        }
+#pragma unroll
+        for (int k = 0; k < kColsPerLane; ++k) dv[k] = v[k] != 0x7fffffff ? a.dist[v[k]] : 0u;
+#pragma unroll
+        for (int k = 0; k < kColsPerLane; ++k) {
+            p[k] = end[k] = 0;
+            if (dv[k] == kInf) {
+                const int64_t c = base + 32 * k + lane;
+                p[k] = __ldg(a.dc_cp + c);
+                end[k] = __ldg(a.dc_cp + c + 1);
                 acc.verts++;
             }
         }
-        bool found = false;
-        // each lane alone: up to kBuShort in-edges, four independent loads at a time
-        const int32_t lim = min(end, p + kBuShort);
-        while (p < lim && !found) {
-            int32_t u[4];
+        // each lane alone: up to kBuShort in-edges per column, in rounds of four
+        // edges of every column (independent loads)
+        bool found[kColsPerLane];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) u[k] = (p + k < lim) ? __ldg(row + p + k) : -1;
+        for (int k = 0; k < kColsPerLane; ++k) found[k] = false;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) found |= u[k] >= 0 && test_bit(bvc, u[k]);
-            const int32_t nn = min(4, lim - p);
-            acc.scanned += (unsigned)nn;
-            p += nn;
+        for (int rnd = 0; rnd < kBuShort / 4; ++rnd) {
+            int32_t u[kColsPerLane][4];
+#pragma unroll
+            for (int k = 0; k < kColsPerLane; ++k)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) u[k][j] = (!found[k] && p[k] + j < end[k]) ? __ldg(row + p[k] + j) : -1;
+#pragma unroll
+            for (int k = 0; k < kColsPerLane; ++k) {
+                const int32_t nn = found[k] ? 0 : min(4, end[k] - p[k]);  // edges loaded this round
+                if (nn > 0) {
+                    acc.scanned += (unsigned)nn;
+                    p[k] += nn;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) found[k] |= u[k][j] >= 0 && test_bit(bvc, u[k][j]);
+            }
         }
         // the rest of long unvisited columns, one column at a time by the whole warp
-        uint32_t rest = __ballot_sync(kFull, !found && p < end);
-        while (rest) {
-            const int L = __ffs(rest) - 1;
-            rest &= rest - 1u;
-            const int32_t pb = __shfl_sync(kFull, p, L), pe = __shfl_sync(kFull, end, L);
-            bool hit = false;
-            for (int32_t q0 = pb; q0 < pe && !hit; q0 += 128) {
-                bool h = false;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int32_t q = q0 + k * 32 + lane;
-                    if (q < pe) {
-                        h |= test_bit(bvc, __ldg(row + q));
-                        acc.scanned++;
+        for (int k = 0; k < kColsPerLane; ++k) {
+            uint32_t rest = __ballot_sync(kFull, !found[k] && p[k] < end[k]);
+            while (rest) {
+                const int L = __ffs(rest) - 1;
+                rest &= rest - 1u;
+                const int32_t pb = __shfl_sync(kFull, p[k], L), pe = __shfl_sync(kFull, end[k], L);
+                bool hit = false;
+                for (int32_t q0 = pb; q0 < pe && !hit; q0 += 128) {
+                    bool h = false;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int32_t q = q0 + j * 32 + lane;
+                        if (q < pe) {
+                            h |= test_bit(bvc, __ldg(row + q));
+                            acc.scanned++;
+                        }
                     }
+                    hit = __any_sync(kFull, h);
                 }
-                hit = __any_sync(kFull, h);
+                if (lane == L) found[k] = hit;
             }
-            if (lane == L) found = hit;
         }
-        if (found) a.dist[v] = t + 1u;
-        warp_set_bits(a.bv[nxt], v, found);
-        bool wa[kEPT] = {found, false, false, false, false, false, false, false};
-        int32_t va[kEPT] = {found ? v : 0, 0, 0, 0, 0, 0, 0, 0};
+        bool wa[kEPT] = {false, false, false, false, false, false, false, false};
+        int32_t va[kEPT] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int k = 0; k < kColsPerLane; ++k) {
+            if (found[k]) a.dist[v[k]] = t + 1u;
+            warp_set_bits(a.bv[nxt], v[k], found[k]);
+            wa[k] = found[k];
+            va[k] = found[k] ? v[k] : 0;
+        }
         enqueue_batch<true>(a, wa, va, nxt, acc);
     }
     flush_acc(a, acc, nxt, true, s_stat);
@@ -754,7 +788,6 @@ __global__ void __launch_bounds__(kThreads, 4) trav_pull_bu(TravArgs a) {
 
 // SSSP Apply after trav_pull_a: four columns per lane per step (independent loads
 // in flight), coalesced across the warp for each of the four.
-constexpr int kColsPerLane = 4;
 
 __global__ void __launch_bounds__(kThreads) trav_pull_b(TravArgs a) {
     TravCtlDev* cd = a.ctl;
