@@ -206,10 +206,38 @@ int bits_for(int64_t n) {
 
 }  // namespace
 
+__global__ void degree_keys(const int32_t* __restrict__ list, int64_t len, const int32_t* __restrict__ deg,
+                            uint64_t* __restrict__ keys) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        keys[i] = (uint64_t)(uint32_t)deg[list[i]];
+}
+
+// Sort list[0, len) by deg (stable: ties keep ascending ids), so that 32
+// consecutive small-bin rows, which row passes give one lane each, have about
+// the same length.
+static gm_status sort_by_degree(int32_t* list, int64_t len, const int32_t* deg, int bits, cudaStream_t s) {
+    if (len < 2) return GM_OK;
+    struct Tmp {
+        cudaStream_t s;
+        DevBuf b[3];
+        ~Tmp() { for (DevBuf& x : b) dev_free(x, s); }
+    } tmp{s};
+    GM_TRY(dev_alloc(tmp.b[0], sizeof(uint64_t) * len, s));
+    GM_TRY(dev_alloc(tmp.b[1], sizeof(uint64_t) * len, s));
+    GM_TRY(dev_alloc(tmp.b[2], sizeof(uint32_t) * len, s));
+    degree_keys<<<blocks_for(len), 256, 0, s>>>(list, len, deg, as<uint64_t>(tmp.b[0]));
+    LAUNCH_CHECK();
+    GM_TRY(radix_sort_pairs(as<uint64_t>(tmp.b[0]), reinterpret_cast<uint32_t*>(list), as<uint64_t>(tmp.b[1]),
+                            as<uint32_t>(tmp.b[2]), len, bits, s));
+    GM_CUDA_TRY(cudaStreamSynchronize(s));  // the temporaries are freed on return
+    return GM_OK;
+}
+
 // Compact the vertices of each degree bin 1..3 (consecutive in `list`, offsets in
-// off[0..3]) and the degree-0 vertices (into `zero`, count in *zero_count).
-static gm_status bin_lists(gm_graph* g, const uint8_t* bins, int32_t* list, int64_t* off, int32_t* zero,
-                           int64_t* zero_count) {
+// off[0..3]) and the degree-0 vertices (into `zero`, count in *zero_count).  Bin 1
+// is ordered by degree (see sort_by_degree); bins 2 and 3 by id.
+static gm_status bin_lists(gm_graph* g, const uint8_t* bins, const int32_t* deg, int32_t* list, int64_t* off,
+                           int32_t* zero, int64_t* zero_count) {
     cudaStream_t s = g->stream;
     const int64_t n = g->n;
     DevBuf flags, cnt;
@@ -229,6 +257,7 @@ static gm_status bin_lists(gm_graph* g, const uint8_t* bins, int32_t* list, int6
                                         cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { set_error("bins: %s", cudaGetErrorString(e)); st = GM_ERR_CUDA; break; }
+        if (bin == 1) st = sort_by_degree(list, hc[1], deg, bits_for((int64_t)g->tune.bin_small + 1), s);
         if (bin > 0) pos += hc[bin];
     }
     dev_free(flags, s);
@@ -259,10 +288,10 @@ gm_status build_bins(gm_graph* g) {
     GM_TRY(dev_alloc(g->zero_in_list, sizeof(int32_t) * (n > 0 ? n : 1), s));
     GM_TRY(dev_alloc(g->out_list, sizeof(int32_t) * (n > 0 ? n : 1), s));
     GM_TRY(dev_alloc(g->zero_out_list, sizeof(int32_t) * (n > 0 ? n : 1), s));
-    GM_TRY(bin_lists(g, as<uint8_t>(g->in_bin), as<int32_t>(g->in_list), g->in_list_count,
+    GM_TRY(bin_lists(g, as<uint8_t>(g->in_bin), as<int32_t>(g->in_deg), as<int32_t>(g->in_list), g->in_list_count,
                      as<int32_t>(g->zero_in_list), &g->zero_in_count));
-    GM_TRY(bin_lists(g, as<uint8_t>(g->out_bin), as<int32_t>(g->out_list), g->out_list_count,
-                     as<int32_t>(g->zero_out_list), &g->zero_out_count));
+    GM_TRY(bin_lists(g, as<uint8_t>(g->out_bin), as<int32_t>(g->out_deg), as<int32_t>(g->out_list),
+                     g->out_list_count, as<int32_t>(g->zero_out_list), &g->zero_out_count));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
     return GM_OK;
 }
