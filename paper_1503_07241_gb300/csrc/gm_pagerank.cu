@@ -2,9 +2,11 @@
 //   x_{t+1}(v) = r + (1 - r) * sum_{u -> v} c_t(u),   c_t(u) = x_t(u) / deg(u).
 // Every vertex is active in every superstep, so the sparse vector is dense and
 // the pull form needs no frontier test and no atomics: each destination is
-// reduced by exactly one thread group (warp-cooperative for in-degree < bin_small,
-// a warp up to bin_large, a CTA beyond), in a fixed order, in FP32.  The Apply
-// step writes both the new rank and the next contribution c_{t+1}(v).
+// reduced by exactly one thread group (a lane for in-degree < bin_small -- that bin
+// is stored ordered by degree, so a warp's 32 destinations have about the same
+// length -- a warp up to bin_large, a CTA beyond), four in-edges in flight per
+// thread, in a fixed order, in FP32.  The Apply step writes both the new rank and
+// the next contribution c_{t+1}(v).
 #include "gm_internal.cuh"
 
 namespace gm {
@@ -42,15 +44,21 @@ __global__ void __launch_bounds__(kThreads) pr_step(PrArgs a) {
     const uint32_t gwarp = (blockIdx.x * kThreads + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * kThreads) >> 5;
     __shared__ float s_red[kThreads / 32];
-    __shared__ float s_acc[kThreads / 32][32];
 
     // large in-degree: one CTA per vertex
     for (int64_t i = a.in_off[2] + blockIdx.x; i < a.in_off[3]; i += gridDim.x) {
         const int32_t v = a.in_list[i];
         const int32_t beg = a.col_ptr[v], end = a.col_ptr[v + 1];
-        float s = 0.0f;
-        for (int32_t e = beg + threadIdx.x; e < end; e += kThreads) s += a.c_cur[a.row[e]];
-        s = warp_sum_f(s);
+        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+        int32_t e = beg + threadIdx.x;
+        for (; e + 3 * kThreads < end; e += 4 * kThreads) {
+            s0 += a.c_cur[a.row[e]];
+            s1 += a.c_cur[a.row[e + kThreads]];
+            s2 += a.c_cur[a.row[e + 2 * kThreads]];
+            s3 += a.c_cur[a.row[e + 3 * kThreads]];
+        }
+        for (; e < end; e += kThreads) s0 += a.c_cur[a.row[e]];
+        float s = warp_sum_f((s0 + s1) + (s2 + s3));
         if (lane == 0) s_red[wid] = s;
         __syncthreads();
         if (wid == 0) {
@@ -64,58 +72,33 @@ __global__ void __launch_bounds__(kThreads) pr_step(PrArgs a) {
     for (int64_t i = a.in_off[1] + gwarp; i < a.in_off[2]; i += nwarps) {
         const int32_t v = a.in_list[i];
         const int32_t beg = a.col_ptr[v], end = a.col_ptr[v + 1];
-        float s = 0.0f;
-        for (int32_t e = beg + lane; e < end; e += 32) s += a.c_cur[a.row[e]];
-        s = warp_sum_f(s);
+        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+        int32_t e = beg + lane;
+        for (; e + 96 < end; e += 128) {
+            s0 += a.c_cur[a.row[e]];
+            s1 += a.c_cur[a.row[e + 32]];
+            s2 += a.c_cur[a.row[e + 64]];
+            s3 += a.c_cur[a.row[e + 96]];
+        }
+        for (; e < end; e += 32) s0 += a.c_cur[a.row[e]];
+        const float s = warp_sum_f((s0 + s1) + (s2 + s3));
         if (lane == 0) pr_apply(a, v, s);
     }
-    // small: 32 vertices per warp; segmented sums over the concatenated in-edges
-    float* acc = s_acc[wid];
-    for (int64_t g0 = a.in_off[0] + (int64_t)gwarp * 32; g0 < a.in_off[1]; g0 += (int64_t)nwarps * 32) {
-        const int64_t i = g0 + lane;
-        int32_t v = 0, beg = 0;
-        uint32_t deg = 0;
-        if (i < a.in_off[1]) {
-            v = a.in_list[i];
-            beg = a.col_ptr[v];
-            deg = (uint32_t)(a.col_ptr[v + 1] - beg);
+    // small: one lane per vertex, four in-edges in flight
+    for (int64_t i = a.in_off[0] + (int64_t)gwarp * 32 + lane; i - lane < a.in_off[1]; i += (int64_t)nwarps * 32) {
+        if (i >= a.in_off[1]) continue;
+        const int32_t v = a.in_list[i];
+        const int32_t beg = a.col_ptr[v], end = a.col_ptr[v + 1];
+        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+        int32_t e = beg;
+        for (; e + 3 < end; e += 4) {
+            s0 += a.c_cur[a.row[e]];
+            s1 += a.c_cur[a.row[e + 1]];
+            s2 += a.c_cur[a.row[e + 2]];
+            s3 += a.c_cur[a.row[e + 3]];
         }
-        acc[lane] = 0.0f;
-        __syncwarp();
-        uint32_t incl = deg;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const uint32_t excl = incl - deg;
-        const uint32_t total = __shfl_sync(kFull, incl, 31);
-        for (uint32_t base = 0; base < total; base += 32) {
-            const uint32_t j = base + lane;
-            int k = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const uint32_t ex = __shfl_sync(kFull, excl, k + step);
-                if (ex <= j) k += step;
-            }
-            const int32_t bo = __shfl_sync(kFull, beg, k);
-            const uint32_t eo = __shfl_sync(kFull, excl, k);
-            const bool valid = j < total;
-            float val = valid ? a.c_cur[a.row[bo + (int32_t)(j - eo)]] : 0.0f;
-            const int owner = valid ? k : 32 + lane;  // invalid lanes form their own segments
-            // inclusive segmented scan by owner (owners are non-decreasing across lanes)
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const float y = __shfl_up_sync(kFull, val, o);
-                const int ko = __shfl_up_sync(kFull, owner, o);
-                if (lane >= o && ko == owner) val += y;
-            }
-            const int next_owner = __shfl_down_sync(kFull, owner, 1);
-            if (valid && (lane == 31 || next_owner != owner)) acc[k] += val;
-            __syncwarp();
-        }
-        if (i < a.in_off[1]) pr_apply(a, v, acc[lane]);
-        __syncwarp();
+        for (; e < end; ++e) s0 += a.c_cur[a.row[e]];
+        pr_apply(a, v, (s0 + s1) + (s2 + s3));
     }
     // vertices without in-edges receive no message
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < a.zero_count;
