@@ -11,10 +11,12 @@
 // Apply takes the gradient step.
 //
 // Kernels: a user pass over the CSR (one warp per chunk of <= 512 ratings of a
-// user, the K factor components across the lanes, dot products by warp shuffle)
-// computes and stores e_uv and accumulates sum_v e_uv p_v; an item pass over the
-// CSC gathers the stored e_uv and accumulates sum_u e_uv p_u; an update kernel
-// applies Eqs. 4-5 to every vertex.  Chunks of one long row are combined with
+// user; for K = 8, 16, 32, 64 each rating is handled by K/8 lanes with 8 factor
+// components each, so a warp has 32/(K/8) ratings in flight, other K spread the
+// components over the 32 lanes, one rating at a time) computes and stores e_uv and
+// accumulates sum_v e_uv p_v; an item pass over the CSC gathers the stored e_uv
+// and accumulates sum_u e_uv p_u; an update kernel applies Eqs. 4-5 to every
+// vertex.  Chunks of one long row are combined with
 // float atomics.  Arithmetic in FP32 on CUDA cores: every product is one
 // K-wide dot product per rating, not a dense tile.
 #include <algorithm>
@@ -141,6 +143,112 @@ __global__ void __launch_bounds__(kThreads) cf_item_pass(const int4* __restrict_
     }
 }
 
+// Grouped forms for K = 8 L (L = 1, 2, 4, 8): L lanes share a rating, 8 factor
+// components per lane (two 16-byte loads), so a warp keeps 32 / L ratings in
+// flight instead of one, and a dot product needs log2(L) shuffles instead of 5.
+template <int L>
+__device__ __forceinline__ void load8f(const float* __restrict__ p, int64_t off, float (&x)[8]) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p + off));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(p + off + 4));
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+}
+
+// Sum of x over the 32 / L groups of a warp (lanes with the same component slice).
+template <int L>
+__device__ __forceinline__ void group_reduce8(float (&x)[8]) {
+#pragma unroll
+    for (int o = L; o < 32; o <<= 1)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] += __shfl_xor_sync(kFull, x[j], o);
+}
+
+template <int L>
+__global__ void __launch_bounds__(kThreads) cf_user_pass_g(const int4* __restrict__ chunks, int64_t nchunks,
+                                                           const int32_t* __restrict__ col,
+                                                           const uint32_t* __restrict__ rating,
+                                                           const float* __restrict__ p,
+                                                           float* __restrict__ ebuf, float* __restrict__ acc,
+                                                           double* __restrict__ sq_err) {
+    constexpr int K = 8 * L, R = 32 / L;
+    const int lane = threadIdx.x & 31, grp = lane / L, sub = lane % L;
+    const int64_t gwarp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+    double sq = 0.0;
+    for (int64_t c = gwarp; c < nchunks; c += nwarps) {
+        const int4 ch = chunks[c];
+        const int32_t u = ch.x;
+        float pu[8], ac[8];
+        load8f<L>(p, (int64_t)u * K + 8 * sub, pu);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ac[j] = 0.0f;
+        for (int32_t e0 = ch.y; e0 < ch.z; e0 += R) {
+            const int32_t e = e0 + grp;
+            const bool ok = e < ch.z;
+            const int32_t v = ok ? __ldg(col + e) : u;  // a valid row to read; its terms are dropped
+            const float g = ok ? (float)__ldg(rating + e) : 0.0f;
+            float pv[8];
+            load8f<L>(p, (int64_t)v * K + 8 * sub, pv);
+            float part = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) part += pu[j] * pv[j];
+#pragma unroll
+            for (int o = L / 2; o >= 1; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+            const float err = ok ? g - part : 0.0f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) ac[j] += err * pv[j];
+            if (ok && sub == 0) {
+                if (ebuf) ebuf[e] = err;
+                sq += (double)err * (double)err;
+            }
+        }
+        if (acc) {
+            group_reduce8<L>(ac);
+            if (grp == 0)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) atomicAdd(&acc[(int64_t)u * K + 8 * sub + j], ac[j]);
+        }
+    }
+    if (sq_err) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(kFull, sq, o);
+        if (lane == 0 && sq != 0.0) atomicAdd(sq_err, sq);
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(kThreads) cf_item_pass_g(const int4* __restrict__ chunks, int64_t nchunks,
+                                                           const int32_t* __restrict__ row,
+                                                           const uint32_t* __restrict__ csc_pos,
+                                                           const float* __restrict__ ebuf,
+                                                           const float* __restrict__ p, float* __restrict__ acc) {
+    constexpr int K = 8 * L, R = 32 / L;
+    const int lane = threadIdx.x & 31, grp = lane / L, sub = lane % L;
+    const int64_t gwarp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+    for (int64_t c = gwarp; c < nchunks; c += nwarps) {
+        const int4 ch = chunks[c];
+        const int32_t v = ch.x;
+        float ac[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ac[j] = 0.0f;
+        for (int32_t q0 = ch.y; q0 < ch.z; q0 += R) {
+            const int32_t q = q0 + grp;
+            const bool ok = q < ch.z;
+            const int32_t u = ok ? __ldg(row + q) : 0;
+            const float err = ok ? __ldg(ebuf + __ldg(csc_pos + q)) : 0.0f;
+            float pu[8];
+            load8f<L>(p, (int64_t)u * K + 8 * sub, pu);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) ac[j] += err * pu[j];
+        }
+        group_reduce8<L>(ac);
+        if (grp == 0)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) atomicAdd(&acc[(int64_t)v * K + 8 * sub + j], ac[j]);
+    }
+}
+
 // p <- p + gamma (acc - lambda p); acc <- 0
 __global__ void cf_update(float* __restrict__ p, float* __restrict__ acc, int64_t count, float gamma, float lambda) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
@@ -179,6 +287,19 @@ template <typename F>
 gm_status by_kp(int K, F f) {
     if (K <= 32) return f(std::integral_constant<int, 1>());
     return f(std::integral_constant<int, 2>());
+}
+
+// K = 8, 16, 32, 64 take the grouped kernels (L = K / 8 lanes per rating).
+bool grouped(int K) { return K == 8 || K == 16 || K == 32 || K == 64; }
+
+template <typename F>
+gm_status by_group(int K, F f) {
+    switch (K) {
+        case 8: return f(std::integral_constant<int, 1>());
+        case 16: return f(std::integral_constant<int, 2>());
+        case 32: return f(std::integral_constant<int, 4>());
+        default: return f(std::integral_constant<int, 8>());
+    }
 }
 
 }  // namespace
@@ -239,7 +360,25 @@ gm_status cf_run(gm_graph* g, int32_t iters, int32_t* iters_done) {
     const int64_t nk = g->n * K;
     float* p = as<float>(g->state);
     for (int32_t it = 0; it < iters; ++it) {
-        GM_TRY(by_kp(K, [&](auto kp) -> gm_status {
+        if (grouped(K)) {
+            GM_TRY(by_group(K, [&](auto lc) -> gm_status {
+                constexpr int L = decltype(lc)::value;
+                if (c->n_user_chunks > 0) {
+                    cf_user_pass_g<L><<<grid_cf(), kThreads, 0, s>>>(as<int4>(c->user_chunks), c->n_user_chunks,
+                                                                      as<int32_t>(g->col), as<uint32_t>(g->w), p,
+                                                                      as<float>(c->ebuf), as<float>(c->acc), nullptr);
+                    g_launches++;
+                }
+                if (c->n_item_chunks > 0) {
+                    cf_item_pass_g<L><<<grid_cf(), kThreads, 0, s>>>(as<int4>(c->item_chunks), c->n_item_chunks,
+                                                                      as<int32_t>(g->row), as<uint32_t>(g->csc_pos),
+                                                                      as<float>(c->ebuf), p, as<float>(c->acc));
+                    g_launches++;
+                }
+                GM_CUDA_TRY(cudaGetLastError());
+                return GM_OK;
+            }));
+        } else GM_TRY(by_kp(K, [&](auto kp) -> gm_status {
             constexpr int KP = decltype(kp)::value;
             if (c->n_user_chunks > 0) {
                 cf_user_pass<KP><<<grid_cf(), kThreads, 0, s>>>(as<int4>(c->user_chunks), c->n_user_chunks,
@@ -277,7 +416,18 @@ gm_status cf_loss(gm_graph* g, double* out) {
     const int K = g->params.K;
     double* d = as<double>(c->scalar);
     GM_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(double) * 2, s));
-    GM_TRY(by_kp(K, [&](auto kp) -> gm_status {
+    if (grouped(K)) {
+        GM_TRY(by_group(K, [&](auto lc) -> gm_status {
+            constexpr int L = decltype(lc)::value;
+            if (c->n_user_chunks > 0) {
+                cf_user_pass_g<L><<<grid_cf(), kThreads, 0, s>>>(as<int4>(c->user_chunks), c->n_user_chunks,
+                                                                  as<int32_t>(g->col), as<uint32_t>(g->w),
+                                                                  as<float>(g->state), nullptr, nullptr, d);
+                g_launches++;
+            }
+            return GM_OK;
+        }));
+    } else GM_TRY(by_kp(K, [&](auto kp) -> gm_status {
         constexpr int KP = decltype(kp)::value;
         if (c->n_user_chunks > 0) {
             cf_user_pass<KP><<<grid_cf(), kThreads, 0, s>>>(as<int4>(c->user_chunks), c->n_user_chunks,
