@@ -473,9 +473,9 @@ def main():
         g.close()
         return 0
     tuning = None
-    if not args.no_autotune:  # on the first two sources of each kind, before any timing
-        tb = g.autotune(gm.GM_BFS, bfs_src[:2])
-        ts_ = g.autotune(gm.GM_SSSP, sssp_src[:2])
+    if not args.no_autotune:  # on the first four sources of each kind, before any timing
+        tb = g.autotune(gm.GM_BFS, bfs_src[:4])
+        ts_ = g.autotune(gm.GM_SSSP, sssp_src[:4])
         tuning = {"alpha": ts_["alpha"], "beta": ts_["beta"], "sssp_pull_frac": ts_["sssp_pull_frac"],
                   "bin_small": ts_["bin_small"], "bin_large": ts_["bin_large"], "pull_stage": ts_["pull_stage"]}
 
