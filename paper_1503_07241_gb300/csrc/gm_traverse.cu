@@ -145,10 +145,14 @@ __device__ __forceinline__ void warp_flush(const TravArgs& a, WarpQ* wq, uint32_
 }
 
 // Append the vertices v[k] with want[k] to the next frontier of slot `nxt`,
-// grouped by out-degree bin (large vertices as one item per chunk).  Warp-collective.
+// grouped by out-degree bin (large vertices as one item per chunk); vb, vd and vin
+// hold each wanted vertex's out-degree bin, out-degree and (BFS) in-degree, loaded
+// by the caller ahead of time.  Warp-collective.
 template <bool BFS>
-__device__ __forceinline__ void enqueue_batch(const TravArgs& a, const bool (&want)[kEPT], const int32_t (&v)[kEPT],
-                                              int nxt, Acc& acc) {
+__device__ __forceinline__ void enqueue_batch_pre(const TravArgs& a, const bool (&want)[kEPT],
+                                                  const int32_t (&v)[kEPT], const uint32_t (&vb)[kEPT],
+                                                  const uint32_t (&vd)[kEPT], const uint32_t (&vin)[kEPT], int nxt,
+                                                  Acc& acc) {
     bool mine = false;
 #pragma unroll
     for (int k = 0; k < kEPT; ++k) mine |= want[k];
@@ -161,10 +165,10 @@ __device__ __forceinline__ void enqueue_batch(const TravArgs& a, const bool (&wa
         bin[k] = 0u;
         nch[k] = 0u;
         if (want[k]) {
-            const uint32_t b = a.out_bin[v[k]];
-            const uint32_t d = (uint32_t)a.out_deg[v[k]];
+            const uint32_t b = vb[k];
+            const uint32_t d = vd[k];
             acc.medges += d;
-            if (BFS) acc.unvis += (uint32_t)a.in_deg[v[k]];
+            if (BFS) acc.unvis += vin[k];
             bin[k] = b;
             nch[k] = b == 3u ? (d + kChunk - 1u) / kChunk : 1u;
             cnt[b] += nch[k];
@@ -211,6 +215,24 @@ __device__ __forceinline__ void enqueue_batch(const TravArgs& a, const bool (&wa
             }
         }
     }
+}
+
+// enqueue_batch_pre with the degree data loaded here.  Warp-collective.
+template <bool BFS>
+__device__ __forceinline__ void enqueue_batch(const TravArgs& a, const bool (&want)[kEPT], const int32_t (&v)[kEPT],
+                                              int nxt, Acc& acc) {
+    bool mine = false;
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) mine |= want[k];
+    if (!__any_sync(kFull, mine)) return;
+    uint32_t vb[kEPT], vd[kEPT], vin[kEPT];
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) {
+        vb[k] = want[k] ? (uint32_t)a.out_bin[v[k]] : 0u;
+        vd[k] = want[k] ? (uint32_t)a.out_deg[v[k]] : 0u;
+        vin[k] = (BFS && want[k]) ? (uint32_t)a.in_deg[v[k]] : 0u;
+    }
+    enqueue_batch_pre<BFS>(a, want, v, vb, vd, vin, nxt, acc);
 }
 
 // Push relaxation of up to 8 edges (u -> v[k]) with messages du[k]; `ok` masks
@@ -681,7 +703,8 @@ __device__ __forceinline__ void warp_set_bits(uint32_t* bv, int32_t v, bool want
 }
 
 constexpr int kBuShort = 8;      // in-edges a lane checks alone before its warp helps
-constexpr int kColsPerLane = 4;  // columns a lane handles per step in the pull-side column kernels
+constexpr int kColsPerLane = 4;  // columns a lane handles per step in the SSSP apply kernel
+constexpr int kBuCols = 2;       // the same in the bottom-up BFS pull (more state per column)
 
 // BFS pull superstep in one kernel: the bottom-up search and Apply.  A column is
 // owned by one lane, so the depth is written and the vertex queued directly.
@@ -702,43 +725,49 @@ __global__ void __launch_bounds__(kThreads, 4) trav_pull_bu(TravArgs a) {
     const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
     const uint32_t* __restrict__ bvc = a.bv[cur];
     const int32_t* __restrict__ row = a.row;
-    constexpr int kSpan = 32 * kColsPerLane;
-    // kColsPerLane columns per lane (32 apart, so each group is coalesced and
+    constexpr int kSpan = 32 * kBuCols;
+    // kBuCols columns per lane (32 apart, so each group is coalesced and
     // ascending across the warp), their loads issued together
     for (int64_t base = gwarp * kSpan; base < a.dc_ncols; base += nwarps * kSpan) {
-        int32_t v[kColsPerLane], p[kColsPerLane], end[kColsPerLane];
-        uint32_t dv[kColsPerLane];
+        int32_t v[kBuCols], p[kBuCols], end[kBuCols];
+        uint32_t dv[kBuCols];
 #pragma unroll
-        for (int k = 0; k < kColsPerLane; ++k) {
+        for (int k = 0; k < kBuCols; ++k) {
             const int64_t c = base + 32 * k + lane;
             v[k] = c < a.dc_ncols ? __ldg(a.dc_jc + c) : 0x7fffffff;  // past the last column: a word of its own
         }
 #pragma unroll
-        for (int k = 0; k < kColsPerLane; ++k) dv[k] = v[k] != 0x7fffffff ? a.dist[v[k]] : 0u;
+        for (int k = 0; k < kBuCols; ++k) dv[k] = v[k] != 0x7fffffff ? a.dist[v[k]] : 0u;
+        // for unvisited columns: the in-edge range, and the degree data the enqueue needs
+        uint32_t vb[kEPT] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u}, vd[kEPT] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        uint32_t vin[kEPT] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll
-        for (int k = 0; k < kColsPerLane; ++k) {
+        for (int k = 0; k < kBuCols; ++k) {
             p[k] = end[k] = 0;
             if (dv[k] == kInf) {
                 const int64_t c = base + 32 * k + lane;
                 p[k] = __ldg(a.dc_cp + c);
                 end[k] = __ldg(a.dc_cp + c + 1);
+                vb[k] = __ldg(a.out_bin + v[k]);
+                vd[k] = (uint32_t)__ldg(a.out_deg + v[k]);
+                vin[k] = (uint32_t)(end[k] - p[k]);  // the in-degree: the column's in-edges
                 acc.verts++;
             }
         }
         // each lane alone: up to kBuShort in-edges per column, in rounds of four
         // edges of every column (independent loads)
-        bool found[kColsPerLane];
+        bool found[kBuCols];
 #pragma unroll
-        for (int k = 0; k < kColsPerLane; ++k) found[k] = false;
+        for (int k = 0; k < kBuCols; ++k) found[k] = false;
 #pragma unroll
         for (int rnd = 0; rnd < kBuShort / 4; ++rnd) {
-            int32_t u[kColsPerLane][4];
+            int32_t u[kBuCols][4];
 #pragma unroll
-            for (int k = 0; k < kColsPerLane; ++k)
+            for (int k = 0; k < kBuCols; ++k)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) u[k][j] = (!found[k] && p[k] + j < end[k]) ? __ldg(row + p[k] + j) : -1;
 #pragma unroll
-            for (int k = 0; k < kColsPerLane; ++k) {
+            for (int k = 0; k < kBuCols; ++k) {
                 const int32_t nn = found[k] ? 0 : min(4, end[k] - p[k]);  // edges loaded this round
                 if (nn > 0) {
                     acc.scanned += (unsigned)nn;
@@ -750,7 +779,7 @@ __global__ void __launch_bounds__(kThreads, 4) trav_pull_bu(TravArgs a) {
         }
         // the rest of long unvisited columns, one column at a time by the whole warp
 #pragma unroll
-        for (int k = 0; k < kColsPerLane; ++k) {
+        for (int k = 0; k < kBuCols; ++k) {
             uint32_t rest = __ballot_sync(kFull, !found[k] && p[k] < end[k]);
             while (rest) {
                 const int L = __ffs(rest) - 1;
@@ -775,13 +804,13 @@ __global__ void __launch_bounds__(kThreads, 4) trav_pull_bu(TravArgs a) {
         bool wa[kEPT] = {false, false, false, false, false, false, false, false};
         int32_t va[kEPT] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
-        for (int k = 0; k < kColsPerLane; ++k) {
+        for (int k = 0; k < kBuCols; ++k) {
             if (found[k]) a.dist[v[k]] = t + 1u;
             warp_set_bits(a.bv[nxt], v[k], found[k]);
             wa[k] = found[k];
             va[k] = found[k] ? v[k] : 0;
         }
-        enqueue_batch<true>(a, wa, va, nxt, acc);
+        enqueue_batch_pre<true>(a, wa, va, vb, vd, vin, nxt, acc);
     }
     flush_acc(a, acc, nxt, true, s_stat);
 }
@@ -815,8 +844,15 @@ __global__ void __launch_bounds__(kThreads) trav_pull_b(TravArgs a) {
             b[k] = c < a.dc_ncols ? y[c] : kInf;
             v[k] = c < a.dc_ncols ? __ldg(a.dc_jc + c) : 0x7fffffff;
         }
+        // the degree data the enqueue needs is loaded together with the property
+        uint32_t vb[kEPT] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u}, vd[kEPT] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        const uint32_t vin[kEPT] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll
-        for (int k = 0; k < kColsPerLane; ++k) dv[k] = b[k] != kInf ? a.dist[v[k]] : 0u;
+        for (int k = 0; k < kColsPerLane; ++k) {
+            dv[k] = b[k] != kInf ? a.dist[v[k]] : 0u;
+            vb[k] = b[k] != kInf ? (uint32_t)__ldg(a.out_bin + v[k]) : 0u;
+            vd[k] = b[k] != kInf ? (uint32_t)__ldg(a.out_deg + v[k]) : 0u;
+        }
         bool wa[kEPT] = {false, false, false, false, false, false, false, false};
         int32_t va[kEPT] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
@@ -833,7 +869,7 @@ __global__ void __launch_bounds__(kThreads) trav_pull_b(TravArgs a) {
             }
             warp_set_bits(a.bv[nxt], v[k], wa[k]);
         }
-        enqueue_batch<false>(a, wa, va, nxt, acc);
+        enqueue_batch_pre<false>(a, wa, va, vb, vd, vin, nxt, acc);
     }
     flush_acc(a, acc, nxt, false, s_stat);
 }
