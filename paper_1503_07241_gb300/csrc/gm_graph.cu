@@ -112,21 +112,25 @@ __global__ void gather_u32(const uint32_t* __restrict__ in, const uint32_t* __re
     if (i < len) out[i] = in[idx[i]];
 }
 
-__global__ void csc_keys(const int32_t* __restrict__ esrc, const int32_t* __restrict__ edst, int64_t len, int b,
+// CSC keys from the CSR-ordered edges: the destination in the low 32 bits (the
+// sort looks at its low b bits only; the bits above stay zero), the source in the
+// high 32.  The edges arrive sorted by (src, dst), so a stable sort on the
+// destination alone yields (dst, src) order.
+__global__ void csc_keys(const int32_t* __restrict__ esrc, const int32_t* __restrict__ edst, int64_t len,
                          uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= len) return;
-    keys[p] = ((uint64_t)(uint32_t)edst[p] << b) | (uint32_t)esrc[p];
+    keys[p] = ((uint64_t)(uint32_t)esrc[p] << 32) | (uint32_t)edst[p];
     vals[p] = (uint32_t)p;
 }
 
-__global__ void csc_split(const uint64_t* __restrict__ keys, int64_t len, int b, int32_t* __restrict__ dst_ids,
+__global__ void csc_split(const uint64_t* __restrict__ keys, int64_t len, int32_t* __restrict__ dst_ids,
                           int32_t* __restrict__ row) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= len) return;
     uint64_t k = keys[q];
-    dst_ids[q] = (int32_t)(k >> b);
-    row[q] = (int32_t)(k & ((1ull << b) - 1ull));
+    dst_ids[q] = (int32_t)(uint32_t)k;
+    row[q] = (int32_t)(k >> 32);
 }
 
 __global__ void degrees_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ cp, int64_t n,
@@ -473,12 +477,12 @@ static gm_status ingest(gm_graph* g, const gm_edge_list* el, uint32_t flags) {
     GM_TRY(dev_alloc(g->row, sizeof(int32_t) * (mm + kEdgePad), s));
     GM_TRY(dev_alloc(g->csc_pos, sizeof(uint32_t) * (mm > 0 ? mm : 1), s));
     if (mm > 0) {
-        csc_keys<<<blocks_for(mm), 256, 0, s>>>(as<int32_t>(esrc), as<int32_t>(edst), mm, b, as<uint64_t>(keys),
+        csc_keys<<<blocks_for(mm), 256, 0, s>>>(as<int32_t>(esrc), as<int32_t>(edst), mm, as<uint64_t>(keys),
                                                 as<uint32_t>(vals));
         LAUNCH_CHECK();
         GM_TRY(radix_sort_pairs(as<uint64_t>(keys), as<uint32_t>(vals), as<uint64_t>(keys2), as<uint32_t>(vals2),
-                                mm, 2 * b, s));
-        csc_split<<<blocks_for(mm), 256, 0, s>>>(as<uint64_t>(keys), mm, b, as<int32_t>(esrc), as<int32_t>(g->row));
+                                mm, b, s));
+        csc_split<<<blocks_for(mm), 256, 0, s>>>(as<uint64_t>(keys), mm, as<int32_t>(esrc), as<int32_t>(g->row));
         LAUNCH_CHECK();
         GM_CUDA_TRY(cudaMemcpyAsync(g->csc_pos.p, vals.p, sizeof(uint32_t) * mm, cudaMemcpyDeviceToDevice, s));
     }

@@ -163,14 +163,21 @@ gm_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaS
 // ------------------------------------------------------------------------------
 // Stable LSD radix sort, 8-bit digits.  One pass = per-tile digit histogram,
 // exclusive scan of the digit-major histogram, stable scatter.  The scatter
-// ranks keys inside a tile with __match_any_sync: warp w owns a contiguous
-// sub-range of the tile and walks it 32 keys at a time in input order.
+// ranks keys inside a tile with __match_any_sync (warp w owns a contiguous
+// sub-range of the tile and walks it 32 keys at a time in input order), places
+// them digit by digit in shared memory, and writes them out from there in order:
+// consecutive threads then write consecutive positions of each digit's run, so
+// the global writes are contiguous instead of one scattered store per key.
 // ------------------------------------------------------------------------------
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortRounds = 8;                            // 32-key rounds per warp
-constexpr int kSortTile = kSortThreads * kSortRounds;     // 2048 keys per CTA
+constexpr int kSortRounds = 16;                           // 32-key rounds per warp
+constexpr int kSortTile = kSortThreads * kSortRounds;     // 4096 keys per CTA
 constexpr int kRadix = 256;
+// dynamic shared memory of the scatter: the tile's keys and values, per-warp digit
+// counts, the tile's digit offsets
+constexpr size_t kScatterSmem = (size_t)kSortTile * (sizeof(uint64_t) + sizeof(uint32_t)) +
+                                sizeof(uint32_t) * (kSortWarps * kRadix + 2 * kRadix);
 
 __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint64_t* __restrict__ keys, int64_t n,
                                                            int shift, int64_t tiles,
@@ -179,7 +186,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint64_t* __res
     h[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll
+#pragma unroll 4
     for (int k = 0; k < kSortRounds; ++k) {
         int64_t i = base + (int64_t)k * kSortThreads + threadIdx.x;
         if (i < n) atomicAdd(&h[(keys[i] >> shift) & 0xFF], 1u);
@@ -194,65 +201,93 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint64_t* __
                                                               const uint32_t* __restrict__ hist_scan,
                                                               uint64_t* __restrict__ keys_out,
                                                               uint32_t* __restrict__ vals_out) {
-    __shared__ uint32_t wcnt[kSortWarps][kRadix];
-    __shared__ uint32_t goff[kRadix];
+    extern __shared__ __align__(16) unsigned char sort_smem[];
+    uint64_t* skey = reinterpret_cast<uint64_t*>(sort_smem);
+    uint32_t* sval = reinterpret_cast<uint32_t*>(skey + kSortTile);
+    uint32_t (*wcnt)[kRadix] = reinterpret_cast<uint32_t (*)[kRadix]>(sval + kSortTile);
+    uint32_t* toff = &wcnt[kSortWarps][0];  // digit offsets inside the tile
+    uint32_t* goff = toff + kRadix;         // digit offsets in the output
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&wcnt[0][0])[i] = 0;
     goff[threadIdx.x] = hist_scan[(int64_t)threadIdx.x * tiles + blockIdx.x];
     __syncthreads();
 
-    const int64_t wbase = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * (32 * kSortRounds);
-    uint64_t k[kSortRounds];
-    uint32_t v[kSortRounds];
+    const int64_t tbase = (int64_t)blockIdx.x * kSortTile;
+    const int64_t tlen = min((int64_t)kSortTile, n - tbase);  // keys in this tile
+    const int wofs = warp * (32 * kSortRounds);                // the warp's sub-range in the tile
     uint32_t rank[kSortRounds];
     const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
-        int64_t i = wbase + r * 32 + lane;
-        bool valid = i < n;
-        k[r] = valid ? keys_in[i] : 0ull;
-        v[r] = valid ? vals_in[i] : 0u;
+        const int j = wofs + r * 32 + lane;
+        const bool valid = j < tlen;
+        const uint64_t k = valid ? keys_in[tbase + j] : 0ull;
         // invalid lanes get a digit value no valid key has (256)
-        uint32_t d = valid ? (uint32_t)((k[r] >> shift) & 0xFF) : 256u;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t base = valid ? wcnt[warp][d] : 0u;
+        const uint32_t d = valid ? (uint32_t)((k >> shift) & 0xFF) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t base = valid ? wcnt[warp][d] : 0u;
         __syncwarp();
+        rank[r] = 0u;
         if (valid) {
             rank[r] = base + __popc(peers & lt_mask);
-            int leader = __ffs(peers) - 1;
-            if (lane == leader) wcnt[warp][d] = base + __popc(peers);
-        } else {
-            rank[r] = 0;
+            if (lane == __ffs(peers) - 1) wcnt[warp][d] = base + __popc(peers);
         }
         __syncwarp();
     }
     __syncthreads();
-    // exclusive prefix over warps, one digit per thread
-    {
-        uint32_t run = 0;
+    // per digit: exclusive prefix over warps, and the digit's total
+    uint32_t tot = 0;
 #pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) {
-            uint32_t c = wcnt[w][threadIdx.x];
-            wcnt[w][threadIdx.x] = run;
-            run += c;
+    for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t c = wcnt[w][threadIdx.x];
+        wcnt[w][threadIdx.x] = tot;
+        tot += c;
+    }
+    // exclusive scan of the digit totals over the CTA (kRadix == kSortThreads)
+    {
+        uint32_t x = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        toff[threadIdx.x] = x;  // inclusive within the warp
+        __syncthreads();
+        uint32_t add = 0;
+        for (int w = 0; w < warp; ++w) add += toff[w * 32 + 31];
+        __syncthreads();
+        toff[threadIdx.x] = add + x - tot;  // exclusive over the CTA
+    }
+    __syncthreads();
+    // place each key at its position inside the tile (digit-major, stable)
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        const int j = wofs + r * 32 + lane;
+        if (j < tlen) {
+            const uint64_t k = keys_in[tbase + j];
+            const uint32_t d = (uint32_t)((k >> shift) & 0xFF);
+            const uint32_t lp = toff[d] + wcnt[warp][d] + rank[r];
+            skey[lp] = k;
+            sval[lp] = vals_in[tbase + j];
         }
     }
     __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kSortRounds; ++r) {
-        int64_t i = wbase + r * 32 + lane;
-        if (i < n) {
-            uint32_t d = (uint32_t)((k[r] >> shift) & 0xFF);
-            uint32_t pos = goff[d] + wcnt[warp][d] + rank[r];
-            keys_out[pos] = k[r];
-            vals_out[pos] = v[r];
-        }
+    // write out in tile order: position = the digit's output offset + the rank in its run
+    for (int lp = threadIdx.x; lp < tlen; lp += kSortThreads) {
+        const uint64_t k = skey[lp];
+        const uint32_t d = (uint32_t)((k >> shift) & 0xFF);
+        const uint32_t pos = goff[d] + ((uint32_t)lp - toff[d]);
+        keys_out[pos] = k;
+        vals_out[pos] = sval[lp];
     }
 }
 
 gm_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                            int64_t n, int bits, cudaStream_t s) {
     if (n <= 1 || bits <= 0) return GM_OK;
+    static const cudaError_t attr_ok =
+        cudaFuncSetAttribute(radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+    if (attr_ok != cudaSuccess) { set_error("radix sort: %s", cudaGetErrorString(attr_ok)); return GM_ERR_CUDA; }
     const int64_t tiles = (n + kSortTile - 1) / kSortTile;
     const int passes = (bits + 7) / 8;
     DevBuf hist, hscan;
@@ -267,8 +302,8 @@ gm_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, u
         g_launches++;
         st = scan_exclusive_u32(as<uint32_t>(hist), as<uint32_t>(hscan), kRadix * tiles, s);
         if (st != GM_OK) break;
-        radix_scatter<<<(unsigned)tiles, kSortThreads, 0, s>>>(kin, vin, n, shift, tiles,
-                                                               as<uint32_t>(hscan), kout, vout);
+        radix_scatter<<<(unsigned)tiles, kSortThreads, kScatterSmem, s>>>(kin, vin, n, shift, tiles,
+                                                                          as<uint32_t>(hscan), kout, vout);
         g_launches++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) { set_error("radix sort: %s", cudaGetErrorString(e)); st = GM_ERR_CUDA; }
