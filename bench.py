@@ -123,6 +123,63 @@ def run_queries(gm, g, bfs_src, sssp_src, src_dev, out_host=None):
     return edges
 
 
+def per_query(gm, g, bfs_src, sssp_src, src_dev):
+    """Each query timed alone with CUDA events on the handle's stream: the
+    harmonic mean of the per-query GTEPS (Graph500 convention) per program, and
+    the median time."""
+    import torch
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name, kind, srcs, dev in (("bfs", gm.GM_BFS, bfs_src, src_dev[0]), ("sssp", gm.GM_SSSP, sssp_src, src_dev[1])):
+        teps, times = [], []
+        for i in range(len(srcs)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            g.program_set(kind)
+            g.set_active(dev[i:i + 1])
+            g.run(-1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            edges = g.scalar(gm.GM_SCALAR_REACHED_EDGES)
+            teps.append(edges / (ms / 1e3) / 1e9)
+            times.append(ms)
+        out[name] = {"hmean_gteps": len(teps) / sum(1.0 / x for x in teps),
+                     "median_ms": statistics.median(times), "queries": len(teps)}
+    return out
+
+
+# Configurations of the ablation (Fig. 7 of the paper, on the GPU): each changes
+# one engine option from the tuned setting; results are identical in every case.
+ABLATIONS = (("tuned", {}),
+             ("push only", {"GM_OPT_DIRECTION": 1}),
+             ("pull only", {"GM_OPT_DIRECTION": 2}),
+             ("no degree bins (a warp per vertex)", {"GM_OPT_BIN_LARGE": 1 << 30, "GM_OPT_BIN_SMALL": 1}),
+             ("no shared-memory stage in the SSSP pull", {"GM_OPT_PULL_STAGE": 0}),
+             ("host-driven superstep loop (no CUDA graph)", {"GM_OPT_LOOP_MODE": 1}))
+
+
+def ablation(gm, g, bfs_src, sssp_src, src_dev, tuning):
+    """Per configuration: the per-query GTEPS of BFS and SSSP (harmonic means)."""
+    rows = []
+    for name, opts in ABLATIONS:
+        for opt, val in opts.items():
+            g.set_option(getattr(gm, opt), val)
+        pq = per_query(gm, g, bfs_src, sssp_src, src_dev)  # warm: builds the loop graph for this setting
+        pq = per_query(gm, g, bfs_src, sssp_src, src_dev)
+        rows.append({"config": name, "bfs_hmean_gteps": pq["bfs"]["hmean_gteps"],
+                     "sssp_hmean_gteps": pq["sssp"]["hmean_gteps"],
+                     "bfs_median_ms": pq["bfs"]["median_ms"], "sssp_median_ms": pq["sssp"]["median_ms"]})
+        # back to the tuned setting
+        g.set_option(gm.GM_OPT_DIRECTION, 0)
+        g.set_option(gm.GM_OPT_LOOP_MODE, 0)
+        g.set_option(gm.GM_OPT_BIN_LARGE, int(tuning["bin_large"]) if tuning else 2048)
+        g.set_option(gm.GM_OPT_BIN_SMALL, int(tuning["bin_small"]) if tuning else 32)
+        g.set_option(gm.GM_OPT_PULL_STAGE, int(tuning["pull_stage"]) if tuning else 40960)
+    return rows
+
+
 def cpu_baseline(n, s, d, w, bfs_src, sssp_src, n_pairs=1):
     """The FP64 oracle as it stands (single thread) on a bounded sample."""
     import oracle
@@ -413,6 +470,9 @@ def main():
     ap.add_argument("--host-loop", action="store_true",
                     help="issue every superstep's kernels from the host instead of one CUDA graph "
                          "(same kernels; profilers do not see kernels inside conditional graph nodes)")
+    ap.add_argument("--ablation", action="store_true",
+                    help="after the timed steps, time every query alone under each engine configuration "
+                         "of the ablation (one option changed at a time) and print that table instead")
     ap.add_argument("--probe", choices=["bfs", "sssp", "ingest", "pagerank", "wpagerank", "triangles", "cf"],
                     help="a short command for kernel profilers: bfs/sssp build the workload graph and run "
                          "one query from the first source with --host-loop semantics; the others build "
@@ -526,6 +586,12 @@ def main():
 
     peak, peak_kind = _peaks()
     roofline = pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind)
+    queries = per_query(gm, g, bfs_src, sssp_src, src_dev)
+    if args.ablation:
+        rows = ablation(gm, g, bfs_src, sssp_src, src_dev, tuning)
+        if rank == 0:
+            print(json.dumps({"ablation": rows, "workload": WORKLOAD, "tuning": tuning}), flush=True)
+        return 0
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -578,7 +644,8 @@ def main():
                 "config": {"workload": WORKLOAD, "n": n, "m": m, "queries_per_step": 2 * N_QUERIES,
                            "ingest_ms": 1e3 * ingest_s, "l2": "inputs larger than L2 (CSR+CSC+weights ~1.05 GB)",
                            "parallelism": f"replicas{world}", "tuning": tuning},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline": roofline, "per_query": queries, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches),
                 "clocks": clk.summary(), "extras": ext}
         print(json.dumps(line), flush=True)
     if dist:
