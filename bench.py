@@ -145,8 +145,9 @@ def per_query(gm, g, bfs_src, sssp_src, src_dev):
             edges = g.scalar(gm.GM_SCALAR_REACHED_EDGES)
             teps.append(edges / (ms / 1e3) / 1e9)
             times.append(ms)
-        out[name] = {"hmean_gteps": len(teps) / sum(1.0 / x for x in teps),
-                     "median_ms": statistics.median(times), "queries": len(teps)}
+        if teps:
+            out[name] = {"hmean_gteps": len(teps) / sum(1.0 / x for x in teps),
+                         "median_ms": statistics.median(times), "queries": len(teps)}
     return out
 
 
@@ -364,6 +365,48 @@ def probe_other(gm, name):
     return 0
 
 
+def paper_shapes(gm):
+    """The paper's larger RMAT graphs (Section 5.1, Table 2): PageRank, BFS and SSSP
+    on RMAT-23 (a/b/c = .57/.19/.19) and SSSP on RMAT-24 (a/b/c = .50/.10/.10), each
+    query timed alone after autotuning on its first two sources."""
+    import torch
+    import synth
+    out = {}
+    ev0, ev1 = _events()
+    for name, scale, params, programs in (("rmat23", 23, "graph500", ("pagerank", "bfs", "sssp")),
+                                          ("rmat24_sssp", 24, "sssp24", ("sssp",))):
+        n, s, d = synth.rmat(scale, 16, synth.RMAT_PARAMS[params], synth.BASE_SEED + scale)
+        w = synth.edge_weights_u32(s, d, synth.BASE_SEED + scale + 1)
+        srcs = synth.pick_sources(n, s, d, 8, seed=synth.BASE_SEED + 200 + scale)
+        g = gm.Graph(n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda(),
+                     torch.from_numpy(w.view(np.int32)).cuda())
+        del s, d, w
+        res = {"n": n, "m": g.m}
+        if "pagerank" in programs:
+            g.program_set(gm.GM_PAGERANK)
+            g.run(20)
+            torch.cuda.synchronize()
+            ev0.record()
+            g.program_set(gm.GM_PAGERANK)
+            g.run(20)
+            ev1.record()
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            res["pagerank_20_iters"] = {"ms": ms, "gteps": 20 * g.m / (ms / 1e3) / 1e9}
+        dev = torch.from_numpy(srcs).cuda()
+        if "bfs" in programs:
+            g.autotune(gm.GM_BFS, srcs[:2])
+        g.autotune(gm.GM_SSSP, srcs[4:6])
+        pq = per_query(gm, g, srcs[:4] if "bfs" in programs else srcs[:0], srcs[4:8], (dev[:4], dev[4:8]))
+        if "bfs" in programs:
+            res["bfs"] = pq["bfs"]
+        res["sssp"] = pq["sssp"]
+        out[name] = res
+        g.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def extras(gm):
     """The other workloads, each timed outside the main timed region."""
     import torch
@@ -470,6 +513,9 @@ def main():
     ap.add_argument("--host-loop", action="store_true",
                     help="issue every superstep's kernels from the host instead of one CUDA graph "
                          "(same kernels; profilers do not see kernels inside conditional graph nodes)")
+    ap.add_argument("--paper-shapes", action="store_true",
+                    help="only measure the paper's larger RMAT graphs (RMAT-23 PageRank/BFS/SSSP, "
+                         "RMAT-24 SSSP) and print that line")
     ap.add_argument("--ablation", action="store_true",
                     help="after the timed steps, time every query alone under each engine configuration "
                          "of the ablation (one option changed at a time) and print that table instead")
@@ -481,6 +527,13 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.paper_shapes:
+        import torch
+        import __graft_entry__ as ge
+        ge.build_cuda_library()
+        import paper_1503_07241_gb300 as gm
+        print(json.dumps({"paper_shapes": paper_shapes(gm)}), flush=True)
+        return 0
     if args.probe in ("pagerank", "wpagerank", "triangles", "cf"):
         import __graft_entry__ as ge
         ge.build_cuda_library()

@@ -214,6 +214,25 @@ def test_scale22_workload(gm):
         check_sssp_certificate(n, cs, cd, cv.astype(np.uint32), got, np.array([src]))
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("scale,params", [(23, "graph500"), (24, "sssp24")])
+def test_paper_rmat_shapes(gm, scale, params):
+    """The paper's larger RMAT graphs (Section 5.1): RMAT-23 with a/b/c = .57/.19/.19
+    (BFS and SSSP) and RMAT-24 with .50/.10/.10 (SSSP), one source each, bit-exact
+    against the oracle with the same superstep counts."""
+    n, s, d, w = rmat_case(scale, weighted=True, params=synth.RMAT_PARAMS[params], seed=synth.BASE_SEED + scale)
+    g = gm.Graph(n, s, d, w)
+    og = oracle.Graph(n, s, d, w)
+    src = synth.pick_sources(n, s, d, 2, seed=synth.BASE_SEED + 200 + scale)
+    if scale == 23:
+        got, it = _run(gm, g, gm.GM_BFS, [src[0]])
+        ref, rit = og.bfs([src[0]])
+        assert np.array_equal(got, ref) and it == rit
+    got, it = _run(gm, g, gm.GM_SSSP, [src[1]])
+    ref, rit = og.sssp([src[1]])
+    assert np.array_equal(got, ref) and it == rit
+
+
 def test_autotune_keeps_results(gm):
     n, s, d, w = rmat_case(14, weighted=True)
     g = gm.Graph(n, s, d, w)
