@@ -342,6 +342,14 @@ def case_cf(gm, synth):
     return g, lambda: g.run(10)
 
 
+def case_components(gm, synth):
+    """Connected components (label propagation, the user-program API), symmetrised
+    RMAT scale 20."""
+    n, s, d = synth.rmat(20, 16, synth.RMAT_PARAMS["graph500"], synth.BASE_SEED + 30)
+    g = gm.Graph(n, s, d, flags=gm.GM_DROP_SELF_LOOPS | gm.GM_DEDUP | gm.GM_SYMMETRIZE)
+    return g, lambda: (g.program_set(gm.GM_CONNECTED_COMPONENTS), g.run(-1))
+
+
 def probe_other(gm, name):
     """One warm-up run, then one run inside the NVTX range "probe" (for profilers)."""
     import torch
@@ -352,6 +360,8 @@ def probe_other(gm, name):
         g, _, run = case_wpagerank(gm, synth, torch)
     elif name == "triangles":
         g, run = case_triangles(gm, synth)
+    elif name == "components":
+        g, run = case_components(gm, synth)
     else:
         g, run = case_cf(gm, synth)
     run()
@@ -487,6 +497,16 @@ def extras(gm):
         g.close()
     except Exception as e:  # pragma: no cover
         out["triangles_s20"] = {"error": str(e)}
+    try:  # connected components, symmetrised RMAT scale 20
+        g, run = case_components(gm, synth)
+        run()
+        ms, (_, it) = timed(run, reps=3)
+        out["components_s20_sym"] = {"ms": ms, "supersteps": it, "m": g.m,
+                                     "gteps": it * g.m / (ms / 1e3) / 1e9,
+                                     "components": int(len(np.unique(g.state())))}
+        g.close()
+    except Exception as e:  # pragma: no cover
+        out["components_s20_sym"] = {"error": str(e)}
     try:  # collaborative filtering, 480k x 17.8k, ~1e8 ratings, K = 32, 10 iterations
         g, run = case_cf(gm, synth)
         g.run(1)
@@ -519,7 +539,8 @@ def main():
     ap.add_argument("--ablation", action="store_true",
                     help="after the timed steps, time every query alone under each engine configuration "
                          "of the ablation (one option changed at a time) and print that table instead")
-    ap.add_argument("--probe", choices=["bfs", "sssp", "ingest", "pagerank", "wpagerank", "triangles", "cf"],
+    ap.add_argument("--probe", choices=["bfs", "sssp", "ingest", "pagerank", "wpagerank", "triangles", "cf",
+                                        "components"],
                     help="a short command for kernel profilers: bfs/sssp build the workload graph and run "
                          "one query from the first source with --host-loop semantics; the others build "
                          "that extra workload and run it twice, the second time inside the NVTX range "
@@ -534,7 +555,7 @@ def main():
         import paper_1503_07241_gb300 as gm
         print(json.dumps({"paper_shapes": paper_shapes(gm)}), flush=True)
         return 0
-    if args.probe in ("pagerank", "wpagerank", "triangles", "cf"):
+    if args.probe in ("pagerank", "wpagerank", "triangles", "cf", "components"):
         import __graft_entry__ as ge
         ge.build_cuda_library()
         import paper_1503_07241_gb300 as gm

@@ -113,7 +113,12 @@ typedef enum gm_program_kind {
     GM_BFS = 1,             /* Section 3.II */
     GM_SSSP = 2,            /* Section 3.V and the appendix program */
     GM_TRIANGLE_COUNT = 3,  /* Section 3.IV, two vertex programs (Section 4.2) */
-    GM_CF = 4               /* Section 3.III, Eqs. 2-5, gradient descent */
+    GM_CF = 4,              /* Section 3.III, Eqs. 2-5, gradient descent */
+    GM_CONNECTED_COMPONENTS = 5  /* not one of the paper's programs: label propagation written with the
+                                    user-program API of graphmat_program.cuh (Section 4's four functions);
+                                    label(v) = min(label(v), labels received), labels start at the vertex
+                                    id, every vertex active at the start; uint32 labels.  On a symmetrised
+                                    graph the result is the smallest id of each connected component. */
 } gm_program_kind;
 
 typedef struct gm_program_params {
@@ -138,6 +143,33 @@ typedef struct gm_program_params {
  * n_left > 0 and GM_W_U32 ratings.
  */
 GM_API gm_status gm_program_set(gm_graph* g, int32_t kind, const gm_program_params* params);
+
+/*
+ * Read-only device view of a graph handle for user-defined vertex programs
+ * (graphmat_program.cuh).  Every pointer is device memory owned by the handle,
+ * valid until gm_graph_destroy or an option that rebuilds the degree bins
+ * (GM_OPT_BIN_SMALL / GM_OPT_BIN_LARGE).  CSC: the in-edges of v are
+ * [col_ptr[v], col_ptr[v+1]) with sources row[] and uint32 weights cw[] (cw is
+ * NULL unless the graph has GM_W_U32 weights); CSR likewise with row_ptr, col, w.
+ * in_list holds the vertices with in-degree >= 1, bin b (1: < bin_small, ordered
+ * by in-degree; 2: < bin_large; 3: the rest) at [in_off[b-1], in_off[b]);
+ * zero_in lists the vertices without in-edges.  Errors: GM_ERR_INVALID_ARG for
+ * a NULL argument.
+ */
+typedef struct gm_device_view {
+    int64_t n, m;
+    const int32_t* col_ptr;
+    const int32_t* row;
+    const uint32_t* cw;
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const uint32_t* w;
+    const int32_t* in_list;
+    int64_t in_off[4];
+    const int32_t* zero_in;
+    int64_t zero_in_count;
+} gm_device_view;
+GM_API gm_status gm_graph_device_view(const gm_graph* g, gm_device_view* out);
 
 /*
  * gm_set_active -- mark vertices active for the next gm_run (appendix run_sssp:

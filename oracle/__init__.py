@@ -61,6 +61,7 @@ def _load():
         "or_graph_degrees": ([P, P, P], None),
         "or_pagerank": ([P, f64, i64, i32, P], i64),
         "or_bfs": ([P, P, i64, i64, P], i64),
+        "or_connected_components": ([P, i64, P], i64),
         "or_sssp": ([P, P, i64, i64, P], i64),
         "or_reached_edges": ([P, P], i64),
         "or_triangle_count": ([P, P, P], i64),
@@ -138,6 +139,12 @@ class Graph:
         d = np.empty(self.n, np.uint32)
         it = _load().or_bfs(self._h, _p(s), s.shape[0], max_iters, _p(d))
         return d, int(it)
+
+    def connected_components(self, max_iters=-1):
+        """Label propagation: (uint32 labels, supersteps)."""
+        lab = np.empty(self.n, np.uint32)
+        it = _load().or_connected_components(self._h, max_iters, _p(lab))
+        return lab, int(it)
 
     def sssp(self, sources, max_iters=-1):
         s = np.ascontiguousarray(np.atleast_1d(sources), dtype=np.int32)

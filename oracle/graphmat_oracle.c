@@ -310,6 +310,29 @@ OR_EXPORT int64_t or_sssp(const or_graph* G, const int32_t* sources, int64_t n_s
     return or_traverse(G, 0, sources, n_sources, max_iters, dist_out);
 }
 
+/* ---- Connected components by label propagation (a vertex program outside the
+ * paper's five, in the same four functions): every vertex sends its label, the
+ * receiver keeps the minimum.  Labels start at the vertex id and every vertex
+ * is active.  On a symmetrised graph the labels converge to the smallest id of
+ * each connected component; on a directed graph to the smallest id of any
+ * vertex with a path to v (v included). ---- */
+static double label_process(const or_program* P, double msg, double ev, double dp) {
+    (void)P; (void)ev; (void)dp;
+    return msg;
+}
+
+OR_EXPORT int64_t or_connected_components(const or_graph* G, int64_t max_iters, uint32_t* label_out) {
+    double* prop = (double*)malloc(sizeof(double) * (size_t)(G->n > 0 ? G->n : 1));
+    uint8_t* active = (uint8_t*)malloc((size_t)(G->n > 0 ? G->n : 1));
+    if (!prop || !active) { free(prop); free(active); return -1; }
+    for (int64_t v = 0; v < G->n; ++v) { prop[v] = (double)v; active[v] = 1; }
+    or_program P = {dist_send, label_process, min_reduce, min_apply, 0, 0, OR_INF_U32, 0.0, 0};
+    int64_t it = or_run_graph_program(G, &P, prop, active, max_iters);
+    for (int64_t v = 0; v < G->n; ++v) label_out[v] = (uint32_t)prop[v];
+    free(prop); free(active);
+    return it;
+}
+
 /* Edges reached by a traversal: sum of out-degrees of vertices with a finite
  * distance (the Graph500 convention for traversed edges). */
 OR_EXPORT int64_t or_reached_edges(const or_graph* G, const uint32_t* dist) {

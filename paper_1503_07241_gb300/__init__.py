@@ -19,7 +19,7 @@ GM_OK, GM_ERR_INVALID_ARG, GM_ERR_OUT_OF_MEMORY, GM_ERR_CUDA, GM_ERR_STATE, GM_E
     GM_ERR_UNSUPPORTED = range(7)
 GM_W_NONE, GM_W_U32, GM_W_F32 = 0, 1, 2
 GM_DROP_SELF_LOOPS, GM_DEDUP, GM_SYMMETRIZE, GM_ORIENT_BY_DEGREE = 1, 2, 4, 8
-GM_PAGERANK, GM_BFS, GM_SSSP, GM_TRIANGLE_COUNT, GM_CF = range(5)
+GM_PAGERANK, GM_BFS, GM_SSSP, GM_TRIANGLE_COUNT, GM_CF, GM_CONNECTED_COMPONENTS = range(6)
 (GM_SCALAR_TC_TOTAL, GM_SCALAR_CF_LOSS, GM_SCALAR_REACHED_EDGES, GM_SCALAR_SUPERSTEPS,
  GM_SCALAR_PUSH_STEPS, GM_SCALAR_PULL_STEPS, GM_SCALAR_SCANNED_EDGES, GM_SCALAR_RELAX_MS,
  GM_SCALAR_RELAX_LAUNCHES, GM_SCALAR_PROCESSED_VERTICES, GM_SCALAR_PULL_WEIGHT_BYTES) = range(1, 12)
@@ -65,6 +65,7 @@ SIGNATURES = {
     "gm_graph_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
     "gm_graph_get_edges": ([_P, _P, _P, _P, ctypes.c_int], ctypes.c_int),
     "gm_graph_get_degrees": ([_P, _P, _P, ctypes.c_int], ctypes.c_int),
+    "gm_graph_device_view": ([_P, _P], ctypes.c_int),
     "gm_program_set": ([_P, _I32, ctypes.POINTER(gm_program_params)], ctypes.c_int),
     "gm_set_active": ([_P, _P, _I64, ctypes.c_int], ctypes.c_int),
     "gm_run": ([_P, _I32, ctypes.POINTER(_I32)], ctypes.c_int),
@@ -258,7 +259,7 @@ class Graph:
         return it.value
 
     def _state_spec(self):
-        if self.kind in (GM_BFS, GM_SSSP):
+        if self.kind in (GM_BFS, GM_SSSP, GM_CONNECTED_COMPONENTS):
             return np.uint32, (self.n,)
         if self.kind == GM_PAGERANK:
             return np.float32, (self.n,)

@@ -34,7 +34,8 @@ def _flags(extra=()):
 
 
 def _headers_mtime():
-    hs = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    hs = (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+          + glob.glob(os.path.join(INCLUDE, "*.cuh")))
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 

@@ -23,6 +23,7 @@ int64_t state_bytes(const gm_graph* g) {
         case GM_PAGERANK: return 4 * g->n;
         case GM_TRIANGLE_COUNT: return 8 * g->n;
         case GM_CF: return 4 * g->n * (int64_t)g->params.K;
+        case GM_CONNECTED_COMPONENTS: return 4 * g->n;
         default: return -1;
     }
 }
@@ -74,6 +75,7 @@ gm_status gm_program_set(gm_graph* g, int32_t kind, const gm_program_params* par
         case GM_SSSP:
             break;
         case GM_TRIANGLE_COUNT:
+        case GM_CONNECTED_COMPONENTS:
             break;
         case GM_CF:
             if (g->n_left <= 0 || g->n_left >= g->n) {
@@ -116,6 +118,8 @@ gm_status gm_program_set(gm_graph* g, int32_t kind, const gm_program_params* par
         }
     } else if (kind == GM_CF) {
         st = cf_prepare(g);
+    } else if (kind == GM_CONNECTED_COMPONENTS) {
+        st = cc_prepare(g);
     }
     if (st != GM_OK) { g->kind = -1; return st; }
     GM_CUDA_TRY(cudaStreamSynchronize(g->stream));
@@ -158,10 +162,30 @@ gm_status gm_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
         case GM_PAGERANK: return pr_run(g, max_iters, iters_done);
         case GM_TRIANGLE_COUNT: return tc_run(g, iters_done);
         case GM_CF: return cf_run(g, max_iters, iters_done);
+        case GM_CONNECTED_COMPONENTS: return cc_run(g, max_iters, iters_done);
         default: break;
     }
     set_error("gm_run: program not available");
     return GM_ERR_UNSUPPORTED;
+}
+
+gm_status gm_graph_device_view(const gm_graph* g, gm_device_view* out) {
+    if (!g || !out) { set_error("gm_graph_device_view: NULL argument"); return GM_ERR_INVALID_ARG; }
+    gm_device_view v{};
+    v.n = g->n;
+    v.m = g->m;
+    v.col_ptr = as<int32_t>(g->col_ptr);
+    v.row = as<int32_t>(g->row);
+    v.cw = g->wtype == GM_W_U32 ? as<uint32_t>(g->cw) : nullptr;
+    v.row_ptr = as<int32_t>(g->row_ptr);
+    v.col = as<int32_t>(g->col);
+    v.w = g->wtype == GM_W_U32 ? as<uint32_t>(g->w) : nullptr;
+    v.in_list = as<int32_t>(g->in_list);
+    for (int b = 0; b < 4; ++b) v.in_off[b] = g->in_list_count[b];
+    v.zero_in = as<int32_t>(g->zero_in_list);
+    v.zero_in_count = g->zero_in_count;
+    *out = v;
+    return GM_OK;
 }
 
 gm_status gm_get_vertex_state(gm_graph* g, void* dst, int64_t bytes, int dst_is_device) {

@@ -185,6 +185,8 @@ gm_status cf_loss(gm_graph* g, double* out);
 gm_status reached_edges(gm_graph* g, int64_t* out);
 void wpr_release(gm_graph* g);
 void cf_release(gm_graph* g);
+gm_status cc_prepare(gm_graph* g);  // gm_cc.cu
+gm_status cc_run(gm_graph* g, int32_t max_iters, int32_t* iters_done);
 // Per-edge source ids of a CSR (out[e] = v for e in [ptr[v], ptr[v+1])).
 gm_status expand_rows(const int32_t* ptr, int64_t n, int32_t* out, cudaStream_t s);
 }  // namespace gm

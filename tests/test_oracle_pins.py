@@ -407,3 +407,64 @@ def test_wpr_uniform_weights_is_pagerank():
     x_pr, _ = g.pagerank(0.15, 30)
     x_w, _ = g.wpr_forward(np.full(g.m, 0.7), np.zeros(n), 0.15, 30)
     np.testing.assert_allclose(x_w, x_pr, rtol=1e-13)
+
+
+# ---- connected components by label propagation (a program outside the paper's five) ----
+
+@pytest.mark.parametrize("seed", range(4))
+def test_components_match_scipy_on_symmetrised_graphs(seed):
+    """On a symmetrised graph the label of v is the smallest id in its connected
+    component (scipy's weak components)."""
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(5, 400))
+    s, d = _random_graph(rng, n, int(rng.integers(0, 2 * n)))
+    g = oracle.Graph(n, s, d, flags=CLEAN | oracle.SYMMETRIZE)
+    lab, _ = g.connected_components()
+    cs, cd, _ = g.edges()
+    A = sp.csr_matrix((np.ones(len(cs)), (cs, cd)), shape=(n, n))
+    ncomp, comp = csg.connected_components(A, directed=False)
+    smallest = np.full(ncomp, n, np.int64)
+    np.minimum.at(smallest, comp, np.arange(n))
+    assert np.array_equal(lab.astype(np.int64), smallest[comp])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_components_directed_brute_force(seed):
+    """On a directed graph the label of v is the smallest id of any vertex with a
+    path to v (v included): brute force by a BFS from every vertex."""
+    rng = np.random.default_rng(400 + seed)
+    n = int(rng.integers(3, 40))
+    s, d = _random_graph(rng, n, int(rng.integers(0, 3 * n)))
+    g = oracle.Graph(n, s, d, flags=CLEAN)
+    lab, _ = g.connected_components()
+    adj = [[] for _ in range(n)]
+    for a, b in zip(s.tolist(), d.tolist()):
+        adj[a].append(b)
+    want = np.arange(n)
+    for u in range(n):
+        seen, stack = {u}, [u]
+        while stack:
+            x = stack.pop()
+            for y in adj[x]:
+                if y not in seen:
+                    seen.add(y)
+                    stack.append(y)
+        for v in seen:
+            want[v] = min(want[v], u)
+    assert np.array_equal(lab.astype(np.int64), want)
+
+
+@pytest.mark.parametrize("n", [2, 7, 30])
+def test_components_path_superstep_count(n):
+    """A symmetric path 0 - 1 - ... - n-1: the label 0 needs n-1 supersteps to
+    reach the far end, and one more superstep finds no change: n in all."""
+    s = np.arange(n - 1, dtype=np.int32)
+    g = oracle.Graph(n, s, s + 1, flags=CLEAN | oracle.SYMMETRIZE)
+    lab, it = g.connected_components()
+    assert lab.tolist() == [0] * n and it == n
+
+
+def test_components_without_edges():
+    g = oracle.Graph(5, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    lab, it = g.connected_components()
+    assert lab.tolist() == list(range(5)) and it == 1
