@@ -54,8 +54,8 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        d = os.path.join(ROOT, "gpurun_out")
-        self.path = os.path.join(d if os.path.isdir(d) else "/tmp", f".clocks_{os.getpid()}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"graphmat_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
