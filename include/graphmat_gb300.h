@@ -319,8 +319,12 @@ enum {
     GM_OPT_ALPHA_X1000 = 6,   /* BFS push->pull switch: frontier edges > unvisited in-edges / alpha */
     GM_OPT_BETA_X1000 = 7,    /* BFS pull->push switch: frontier vertices < n / beta */
     GM_OPT_SSSP_PULL_PPM = 8, /* SSSP: pull when frontier edges > ppm * 1e-6 * m */
-    GM_OPT_PULL_STAGE = 9     /* SSSP pull: messages of the highest-out-degree sources each CTA stages in
+    GM_OPT_PULL_STAGE = 9,    /* SSSP pull: messages of the highest-out-degree sources each CTA stages in
                                  shared memory, 0..49152 (rounded down to a multiple of 4; default 40960) */
+    GM_OPT_TEST_STALL_STAGE = 10  /* test hook, 0 or 1: the SSSP pull's staging barrier expects 16 bytes more
+                                     than its copies bring, so every CTA's bounded wait (about a second)
+                                     runs out; those CTAs gather every message from global memory, the
+                                     results stay exact, and gm_run returns GM_ERR_TIMEOUT */
 };
 GM_API gm_status gm_set_option(gm_graph* g, int32_t option, int64_t value);
 
@@ -341,6 +345,15 @@ typedef struct gm_tuning {
     int32_t pull_stage;  /* GM_OPT_PULL_STAGE chosen (SSSP) */
 } gm_tuning;
 GM_API gm_status gm_autotune(gm_graph* g, int32_t kind, const int32_t* sources, int32_t n_sources, gm_tuning* out);
+
+/*
+ * Test hook for failure paths: after `n` more successful device allocations by
+ * this library, every further allocation fails with GM_ERR_OUT_OF_MEMORY (the
+ * calling entry point returns that status and frees what it allocated); n < 0
+ * turns the hook off.  No GPU call fails: the check happens before the
+ * allocation is requested.  Process-wide, all threads.
+ */
+GM_API void gm_debug_fail_allocations_after(int64_t n);
 
 /* Number of kernel launches this library has issued since load (all handles). */
 GM_API uint64_t gm_kernel_launch_count(void);

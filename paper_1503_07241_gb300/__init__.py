@@ -24,7 +24,8 @@ GM_PAGERANK, GM_BFS, GM_SSSP, GM_TRIANGLE_COUNT, GM_CF, GM_CONNECTED_COMPONENTS 
  GM_SCALAR_PUSH_STEPS, GM_SCALAR_PULL_STEPS, GM_SCALAR_SCANNED_EDGES, GM_SCALAR_RELAX_MS,
  GM_SCALAR_RELAX_LAUNCHES, GM_SCALAR_PROCESSED_VERTICES, GM_SCALAR_PULL_WEIGHT_BYTES) = range(1, 12)
 (GM_OPT_DIRECTION, GM_OPT_LOOP_MODE, GM_OPT_PROFILE, GM_OPT_BIN_SMALL, GM_OPT_BIN_LARGE,
- GM_OPT_ALPHA_X1000, GM_OPT_BETA_X1000, GM_OPT_SSSP_PULL_PPM, GM_OPT_PULL_STAGE) = range(1, 10)
+ GM_OPT_ALPHA_X1000, GM_OPT_BETA_X1000, GM_OPT_SSSP_PULL_PPM, GM_OPT_PULL_STAGE,
+ GM_OPT_TEST_STALL_STAGE) = range(1, 11)
 INF_U32 = 0xFFFFFFFF
 
 _SCALAR_TYPES = {
@@ -81,6 +82,7 @@ SIGNATURES = {
     "gm_autotune": ([_P, _I32, _P, _I32, _P], ctypes.c_int),
     "gm_bfs_csr_noalloc_max_vertices": ([], _I64),
     "gm_kernel_launch_count": ([], _U64),
+    "gm_debug_fail_allocations_after": ([_I64], None),
     "gm_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "gm_last_error": ([], ctypes.c_char_p),
 }

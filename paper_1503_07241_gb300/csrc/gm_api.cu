@@ -169,6 +169,8 @@ gm_status gm_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
     return GM_ERR_UNSUPPORTED;
 }
 
+void gm_debug_fail_allocations_after(int64_t n) { g_alloc_budget.store(n < 0 ? -1 : n); }
+
 gm_status gm_graph_device_view(const gm_graph* g, gm_device_view* out) {
     if (!g || !out) { set_error("gm_graph_device_view: NULL argument"); return GM_ERR_INVALID_ARG; }
     gm_device_view v{};
@@ -297,6 +299,11 @@ gm_status gm_set_option(gm_graph* g, int32_t option, int64_t value) {
             if (value < 0 || value > 49152) break;
             t.pull_stage = (int32_t)(value & ~(int64_t)3);
             trav_release(g);  // the loop graph bakes the shared-memory size in
+            return GM_OK;
+        case GM_OPT_TEST_STALL_STAGE:
+            if (value < 0 || value > 1) break;
+            t.test_stall_stage = (int32_t)value;
+            trav_release(g);
             return GM_OK;
         default:
             set_error("gm_set_option: unknown option %d", option);

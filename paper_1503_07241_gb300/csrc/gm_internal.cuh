@@ -49,6 +49,7 @@ struct DevBuf {
 };
 
 gm_status dev_alloc(DevBuf& b, size_t bytes, cudaStream_t s);
+extern std::atomic<int64_t> g_alloc_budget;  // test hook of gm_debug_fail_allocations_after
 void dev_free(DevBuf& b, cudaStream_t s);
 template <typename T>
 inline T* as(const DevBuf& b) { return static_cast<T*>(b.p); }
@@ -92,6 +93,7 @@ struct Tuning {
     double beta = 24.0;         // pull -> push when frontier vertices < n / beta
     double sssp_pull_frac = 0.05;  // SSSP: pull when frontier edges > sssp_pull_frac * m
     int32_t pull_stage = 40960;    // SSSP pull: hottest messages staged in shared memory per CTA
+    int32_t test_stall_stage = 0;  // test hook: the staging barrier waits for bytes that never come
     int32_t direction = 0;      // 0 auto, 1 push only, 2 pull only
     int32_t loop_mode = 0;      // 0 device loop (CUDA graph with a conditional WHILE node), 1 host loop
     int32_t profile = 0;        // 1: host loop with CUDA events around every relax launch

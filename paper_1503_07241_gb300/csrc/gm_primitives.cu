@@ -21,9 +21,20 @@ void set_error(const char* fmt, ...) {
 
 const char* last_error() { return t_err; }
 
+// Test hook: >= 0 allocations left before every further one fails (see
+// gm_debug_fail_allocations_after); < 0 disables.
+std::atomic<int64_t> g_alloc_budget{-1};
+
 gm_status dev_alloc(DevBuf& b, size_t bytes, cudaStream_t s) {
     dev_free(b, s);
     if (bytes == 0) bytes = 16;
+    for (int64_t left = g_alloc_budget.load(); left >= 0;) {
+        if (left == 0) {
+            set_error("device allocation of %zu bytes failed: injected by gm_debug_fail_allocations_after", bytes);
+            return GM_ERR_OUT_OF_MEMORY;
+        }
+        if (g_alloc_budget.compare_exchange_weak(left, left - 1)) break;
+    }
     cudaError_t e = cudaMallocAsync(&b.p, bytes, s);
     if (e != cudaSuccess) {
         b.p = nullptr;

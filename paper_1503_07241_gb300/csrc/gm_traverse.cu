@@ -67,6 +67,7 @@ struct TravArgs {
     const int32_t* row_r;    // SSSP: CSC sources as ranks
     const int32_t* dc_rank;  // SSSP: rank of each non-empty column's vertex
     int32_t hot;             // SSSP pull: messages of ranks [0, hot) are staged in shared memory
+    uint32_t stage_extra;    // test hook: bytes the staging barrier expects beyond its copies (0 or 16)
     uint32_t* ycol;          // pull: reduced value per non-empty column, infinity between supersteps
     const uint32_t* dc_head; // pull: first-edge-of-column bits
     uint32_t* bv[3];         // frontier bitvectors, rotating by superstep
@@ -480,11 +481,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0u;
 }
 
-// Waits for the barrier's phase `parity` to complete, giving up after a bounded
-// number of tries (each try may suspend the thread for a short time).
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the barrier's phase `parity` to complete, giving up after about one
+// second (the global timer, read every 64 tries) or 2^22 tries, whichever comes
+// first; each try may suspend the thread for a short, system-dependent time.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < (1u << 20); ++i)
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0; i < (1u << 22); ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63u) == 63u && global_ns() - t0 > 1000000000ull) return false;
+    }
     return false;
 }
 
@@ -579,7 +590,7 @@ __global__ void __launch_bounds__(kPullThreads, 1) trav_pull_a(TravArgs a) {
         mbar_init(&s_bar, 1u);
         fence_mbar_init();
         const uint32_t bytes = (uint32_t)hot * 4u;
-        mbar_arrive_expect_tx(&s_bar, bytes);
+        mbar_arrive_expect_tx(&s_bar, bytes + a.stage_extra);
         for (uint32_t off = 0; off < bytes; off += kBulkChunk)
             bulk_copy_g2s(reinterpret_cast<char*>(s_hot) + off, reinterpret_cast<const char*>(msgc) + off,
                           min(kBulkChunk, bytes - off), &s_bar);
@@ -1117,6 +1128,7 @@ TravArgs make_args(gm_graph* g) {
     a.hot = g->src_rank.p ? (int32_t)std::min<int64_t>(std::min<int64_t>(kHotMax, g->tune.pull_stage),
                                                          g->n & ~(int64_t)3)
                           : 0;
+    a.stage_extra = g->tune.test_stall_stage ? 16u : 0u;
     a.ctl = as<TravCtlDev>(g->ctl_buf);
     a.use_cond = 0;
     return a;
