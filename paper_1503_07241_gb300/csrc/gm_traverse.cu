@@ -561,10 +561,16 @@ __device__ __forceinline__ void pull_load_tile(const TravArgs& a, uint32_t k, in
 __device__ __forceinline__ uint32_t lane_valid(uint32_t e0, uint32_t m) { return e0 < m ? min(8u, m - e0) : 0u; }
 
 // Messages of a tile's sources: staged ranks from shared memory, the rest from
-// global memory.  Edges at or past m read rank 0's message (present whenever
-// there is an edge) and are masked later.
+// global memory.  Only the last tile can hold edges at or past m: there
+// (`last`) they read rank 0's message (present whenever there is an edge) and
+// are masked later; every other tile skips the masking.
 __device__ __forceinline__ void pull_gather(const uint32_t* __restrict__ msgc, const uint32_t* s_hot, int32_t hlim,
-                                            uint32_t nv, const int32_t (&r)[kEPT], uint32_t (&mv)[kEPT]) {
+                                            bool last, uint32_t nv, const int32_t (&r)[kEPT], uint32_t (&mv)[kEPT]) {
+    if (!last) {
+#pragma unroll
+        for (int q = 0; q < kEPT; ++q) mv[q] = r[q] < hlim ? s_hot[r[q]] : __ldg(msgc + r[q]);
+        return;
+    }
 #pragma unroll
     for (int q = 0; q < kEPT; ++q) {
         const int32_t rq = (uint32_t)q < nv ? r[q] : 0;
@@ -613,19 +619,26 @@ __global__ void __launch_bounds__(kPullThreads, 1) trav_pull_a(TravArgs a) {
     if (!staged && hot > 0 && threadIdx.x == 0) atomicAdd(&cd->c.stage_timeouts, 1u);
     const int32_t hlim = staged ? hot : 0;  // without the staged block every message is gathered
     uint32_t mv[kEPT];
-    if (gwarp < ntiles) pull_gather(msgc, s_hot, hlim, lane_valid(gwarp * kWTile + lane * kEPT, m), cur.r, mv);
+    if (gwarp < ntiles)
+        pull_gather(msgc, s_hot, hlim, gwarp + 1 == ntiles, lane_valid(gwarp * kWTile + lane * kEPT, m), cur.r, mv);
 
     for (uint32_t k = gwarp; k < ntiles; k += nwarps) {
         const uint32_t nv = lane_valid(k * kWTile + lane * kEPT, m);
         const uint32_t vmask = (1u << nv) - 1u;
         uint32_t cand[kEPT];
+        if (k + 1 < ntiles) {  // a full tile (warp-uniform)
 #pragma unroll
-        for (int q = 0; q < kEPT; ++q) cand[q] = (uint32_t)q < nv ? sat_add(mv[q], cur.weight(q)) : kInf;
+            for (int q = 0; q < kEPT; ++q) cand[q] = sat_add(mv[q], cur.weight(q));
+        } else {
+#pragma unroll
+            for (int q = 0; q < kEPT; ++q) cand[q] = (uint32_t)q < nv ? sat_add(mv[q], cur.weight(q)) : kInf;
+        }
         const uint32_t heads = (cur.hw >> ((lane & 3) * 8)) & vmask;
         const int32_t c0 = cur.c0;
         // pipeline: gather tile k+1's messages, stream tile k+2's sources
         const uint32_t k1 = k + nwarps, k2 = k1 + nwarps;
-        if (k1 < ntiles) pull_gather(msgc, s_hot, hlim, lane_valid(k1 * kWTile + lane * kEPT, m), nxt.r, mv);
+        if (k1 < ntiles)
+            pull_gather(msgc, s_hot, hlim, k1 + 1 == ntiles, lane_valid(k1 * kWTile + lane * kEPT, m), nxt.r, mv);
         cur = nxt;
         if (k2 < ntiles) pull_load_tile<WB>(a, k2, lane, nxt);
         scanned += nv;
