@@ -96,6 +96,17 @@ gm_status gm_program_set(gm_graph* g, int32_t kind, const gm_program_params* par
             return GM_ERR_INVALID_ARG;
     }
     GM_TRY(ensure_pinned(g));
+    const bool traversal = kind == GM_BFS || kind == GM_SSSP;
+    if (traversal && (g->kind == GM_BFS || g->kind == GM_SSSP) && g->state.p && g->work.p && g->ctl_buf.p) {
+        // BFS <-> SSSP: keep the workspace and the cached loop graphs (same sizes)
+        g->kind = kind;
+        g->params = p;
+        g->stats = RunStats{};
+        gm_status st = kind == GM_SSSP ? ensure_unit_weights(g) : GM_OK;
+        if (st == GM_OK) st = trav_reuse(g);
+        if (st != GM_OK) g->kind = -1;
+        return st;
+    }
     trav_release(g);
     cf_release(g);
     dev_free(g->state, g->stream);

@@ -728,7 +728,8 @@ void release_graph(gm_graph* g) {
     DevBuf* bufs[] = {&g->row_ptr, &g->col, &g->w, &g->col_ptr, &g->row, &g->cw, &g->cw8, &g->csc_pos,
                       &g->out_deg, &g->in_deg, &g->out_bin, &g->in_bin, &g->in_list, &g->zero_in_list,
                       &g->out_list, &g->zero_out_list, &g->dc_jc, &g->dc_cp, &g->dc_tile, &g->dc_head,
-                      &g->src_rank, &g->row_r, &g->dc_rank, &g->state, &g->work, &g->ctl_buf};
+                      &g->src_rank, &g->row_r, &g->dc_rank, &g->state, &g->work, &g->ctl_buf,
+                      &g->reached_buf};
     for (DevBuf* b : bufs) dev_free(*b, s);
     if (g->host_pinned) cudaFreeHost(g->host_pinned);
     cudaStreamSynchronize(s);

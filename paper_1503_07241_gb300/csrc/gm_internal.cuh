@@ -161,10 +161,11 @@ struct gm_graph {
     gm::DevBuf ctl_buf;              // TravCtl
     void* host_pinned = nullptr;     // small pinned staging buffer
     // device-loop graph for traversal
-    cudaGraph_t loop_graph = nullptr;
-    cudaGraphExec_t loop_exec = nullptr;
-    int32_t loop_graph_max_iters = -2;
-    uint64_t loop_graph_kernels = 0;
+    // device-loop graphs for traversal, one per program (0 BFS, 1 SSSP), kept until
+    // an option that changes their launch shapes or the workspace is freed
+    cudaGraph_t loop_graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t loop_exec[2] = {nullptr, nullptr};
+    gm::DevBuf reached_buf;          // counter of gm_get_scalar(GM_SCALAR_REACHED_EDGES)
     // results
     uint64_t tc_total = 0;
     void* wpr = nullptr;             // weighted-PageRank buffers (gm_wpr.cu)
@@ -174,6 +175,7 @@ struct gm_graph {
 namespace gm {
 // per-program entry points (implemented in gm_traverse.cu, gm_pagerank.cu, ...)
 gm_status trav_prepare(gm_graph* g);
+gm_status trav_reuse(gm_graph* g);  // program_set between BFS and SSSP with the workspace kept
 gm_status build_source_ranks(gm_graph* g);  // gm_graph.cu
 gm_status trav_set_active(gm_graph* g, const int32_t* vertices_dev, int64_t count);
 gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done);

@@ -993,6 +993,19 @@ __global__ void __launch_bounds__(kThreads) trav_finalize(TravArgs a) {
     if (a.use_cond) cudaGraphSetConditional(a.cond, done ? 0u : 1u);
 }
 
+// Run parameters of the control block; `fresh` also sets the start-of-run
+// fields (the direction of superstep 0 and the unvisited in-edge count).
+__global__ void ctl_params(TravCtlDev* cd, int32_t max_iters, int32_t dir_mode, float alpha, float beta,
+                           float sssp_frac, unsigned long long m, int fresh) {
+    cd->max_iters = max_iters;
+    cd->dir_mode = dir_mode;
+    cd->alpha = alpha;
+    cd->beta = beta;
+    cd->sssp_frac = sssp_frac;
+    if (fresh) cd->c.unvisited_in_edges = m;
+    if (cd->c.iter == 0u) cd->c.dir = dir_mode == 2 ? 1u : 0u;
+}
+
 // ---------------------------------------------------------------- frontier set-up
 __global__ void seed_frontier(TravArgs a, const int32_t* __restrict__ verts, int64_t count, int bfs) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1203,29 +1216,23 @@ gm_status reset_frontier(gm_graph* g) {
     for (int k = 0; k < 3; ++k) GM_CUDA_TRY(cudaMemsetAsync(w.bv[k], 0, sizeof(uint32_t) * nwords, s));
     if (g->kind == GM_SSSP)
         for (int k = 0; k < 2; ++k) GM_CUDA_TRY(cudaMemsetAsync(w.msg[k], 0xFF, sizeof(uint32_t) * n, s));
-    TravCtlDev h{};
-    h.c.dir = g->tune.direction == 2 ? 1u : 0u;
-    h.c.unvisited_in_edges = (unsigned long long)g->m;
-    h.max_iters = -1;
-    h.dir_mode = g->tune.direction;
-    h.alpha = (float)g->tune.alpha;
-    h.beta = (float)g->tune.beta;
-    h.sssp_frac = (float)g->tune.sssp_pull_frac;
-    TravCtlDev* hp = static_cast<TravCtlDev*>(g->host_pinned);
-    *hp = h;
-    GM_CUDA_TRY(cudaMemcpyAsync(g->ctl_buf.p, hp, sizeof(TravCtlDev), cudaMemcpyHostToDevice, s));
-    GM_CUDA_TRY(cudaStreamSynchronize(s));  // the pinned staging buffer is reused
+    GM_CUDA_TRY(cudaMemsetAsync(g->ctl_buf.p, 0, sizeof(TravCtlDev), s));
+    ctl_params<<<1, 1, 0, s>>>(as<TravCtlDev>(g->ctl_buf), -1, g->tune.direction, (float)g->tune.alpha,
+                               (float)g->tune.beta, (float)g->tune.sssp_pull_frac, (unsigned long long)g->m, 1);
+    g_launches++;
+    LAUNCH_OK();
     return GM_OK;
 }
 
 gm_status build_loop_graph(gm_graph* g, bool sssp) {
-    if (g->loop_exec) {
-        cudaGraphExecDestroy(g->loop_exec);
-        g->loop_exec = nullptr;
+    const int slot = sssp ? 1 : 0;
+    if (g->loop_exec[slot]) {
+        cudaGraphExecDestroy(g->loop_exec[slot]);
+        g->loop_exec[slot] = nullptr;
     }
-    if (g->loop_graph) {
-        cudaGraphDestroy(g->loop_graph);
-        g->loop_graph = nullptr;
+    if (g->loop_graph[slot]) {
+        cudaGraphDestroy(g->loop_graph[slot]);
+        g->loop_graph[slot] = nullptr;
     }
     cudaGraph_t graph;
     GM_CUDA_TRY(cudaGraphCreate(&graph, 0));
@@ -1289,9 +1296,8 @@ gm_status build_loop_graph(gm_graph* g, bool sssp) {
         set_error("superstep loop graph: %s", cudaGetErrorString(e));
         return GM_ERR_CUDA;
     }
-    g->loop_graph = graph;
-    g->loop_exec = exec;
-    g->loop_graph_max_iters = sssp ? 1 : 0;  // records which program the graph was built for
+    g->loop_graph[slot] = graph;
+    g->loop_exec[slot] = exec;
     return GM_OK;
 }
 
@@ -1313,6 +1319,22 @@ gm_status trav_prepare(gm_graph* g) {
     LAUNCH_OK();
     // per-column pull results start at infinity; pull_b restores that after every use
     GM_CUDA_TRY(cudaMemsetAsync(work_layout(g).ycol, 0xFF, sizeof(uint32_t) * n, s));
+    return reset_frontier(g);
+}
+
+// program_set between BFS and SSSP when the workspace of a traversal is already
+// allocated: the buffers and the cached loop graphs stay, the properties go back
+// to infinity and the frontier is reset if seeds are pending or the program
+// changed (the message arrays are SSSP's alone).
+gm_status trav_reuse(gm_graph* g) {
+    cudaStream_t s = g->stream;
+    if (g->kind == GM_SSSP && !g->src_rank.p) {  // the SSSP loop graph needs the ranks; build them first
+        GM_TRY(build_source_ranks(g));
+        trav_release(g);
+    }
+    fill_u32<<<num_sms() * 4, 256, 0, s>>>(as<uint32_t>(g->state), g->n, kInf);
+    g_launches++;
+    LAUNCH_OK();
     return reset_frontier(g);
 }
 
@@ -1343,18 +1365,16 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
         return reset_frontier(g);
     }
     TravCtlDev* hp = static_cast<TravCtlDev*>(g->host_pinned);
-    {   // parameters that may change between runs
-        int32_t params[2] = {max_iters, g->tune.direction};
-        GM_CUDA_TRY(cudaMemcpyAsync(reinterpret_cast<char*>(g->ctl_buf.p) + offsetof(TravCtlDev, max_iters), params,
-                                    sizeof(params), cudaMemcpyHostToDevice, s));
-        float f[3] = {(float)g->tune.alpha, (float)g->tune.beta, (float)g->tune.sssp_pull_frac};
-        GM_CUDA_TRY(cudaMemcpyAsync(reinterpret_cast<char*>(g->ctl_buf.p) + offsetof(TravCtlDev, alpha), f,
-                                    sizeof(f), cudaMemcpyHostToDevice, s));
-    }
+    // parameters that may have changed since the frontier was reset
+    ctl_params<<<1, 1, 0, s>>>(as<TravCtlDev>(g->ctl_buf), max_iters, g->tune.direction, (float)g->tune.alpha,
+                               (float)g->tune.beta, (float)g->tune.sssp_pull_frac, (unsigned long long)g->m, 0);
+    g_launches++;
+    LAUNCH_OK();
     const bool host_loop = g->tune.loop_mode == 1 || g->tune.profile;
     if (!host_loop) {
-        if (!g->loop_exec || g->loop_graph_max_iters != (sssp ? 1 : 0)) GM_TRY(build_loop_graph(g, sssp));
-        GM_CUDA_TRY(cudaGraphLaunch(g->loop_exec, s));
+        const int slot = sssp ? 1 : 0;
+        if (!g->loop_exec[slot]) GM_TRY(build_loop_graph(g, sssp));
+        GM_CUDA_TRY(cudaGraphLaunch(g->loop_exec[slot], s));
     } else {
         TravArgs a = make_args(g);
         const int pg = push_grid(), lg = sssp ? pull_grid() : pull_bu_grid(), fg = finalize_grid();
@@ -1452,31 +1472,28 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
 
 gm_status reached_edges(gm_graph* g, int64_t* out) {
     cudaStream_t s = g->stream;
-    DevBuf acc;
-    GM_TRY(dev_alloc(acc, sizeof(unsigned long long), s));
-    gm_status st = GM_OK;
-    cudaError_t e = cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long), s);
-    if (e == cudaSuccess && g->n > 0) {
+    if (!g->reached_buf.p) GM_TRY(dev_alloc(g->reached_buf, sizeof(unsigned long long), s));
+    GM_CUDA_TRY(cudaMemsetAsync(g->reached_buf.p, 0, sizeof(unsigned long long), s));
+    if (g->n > 0) {
         reached_kernel<<<num_sms() * 4, 256, 0, s>>>(as<uint32_t>(g->state), as<int32_t>(g->out_deg), g->n,
-                                                     as<unsigned long long>(acc));
+                                                     as<unsigned long long>(g->reached_buf));
         g_launches++;
-        e = cudaGetLastError();
+        LAUNCH_OK();
     }
     unsigned long long h = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) { set_error("reached_edges: %s", cudaGetErrorString(e)); st = GM_ERR_CUDA; }
-    dev_free(acc, s);
+    GM_CUDA_TRY(cudaMemcpyAsync(&h, g->reached_buf.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GM_CUDA_TRY(cudaStreamSynchronize(s));
     *out = (int64_t)h;
-    return st;
+    return GM_OK;
 }
 
 void trav_release(gm_graph* g) {
-    if (g->loop_exec) cudaGraphExecDestroy(g->loop_exec);
-    if (g->loop_graph) cudaGraphDestroy(g->loop_graph);
-    g->loop_exec = nullptr;
-    g->loop_graph = nullptr;
-    g->loop_graph_max_iters = -2;
+    for (int k = 0; k < 2; ++k) {
+        if (g->loop_exec[k]) cudaGraphExecDestroy(g->loop_exec[k]);
+        if (g->loop_graph[k]) cudaGraphDestroy(g->loop_graph[k]);
+        g->loop_exec[k] = nullptr;
+        g->loop_graph[k] = nullptr;
+    }
 }
 
 }  // namespace gm
