@@ -252,11 +252,14 @@ GM_API gm_status gm_wpagerank_backward(gm_graph* g, const float* dLdx, float* dL
 /*
  * gm_run_batch -- many BFS / SSSP queries (an added form: the programs of
  * Sections 3.II and 3.V) over one or more graphs, in one device-driven superstep
- * loop.  All queries advance in lockstep supersteps; a device work queue hands
- * (query, vertex, edge chunk) items of every active query's frontier to the
- * warps; the loop is one CUDA graph whose conditional node stops when no query
- * is active.  Each query's result and superstep count equal gm_run's for the
- * same graph, program and single source.
+ * loop.  Queries of one program on one graph are bundled, up to 8 per bundle,
+ * and run as one multi-source SpMSpV: a frontier byte per vertex (a bit per
+ * query) and, for SSSP, a 32-byte row of 8 messages per vertex, so one pass over
+ * the in-edges per superstep serves the whole bundle.  All bundles advance in
+ * lockstep supersteps; a device work queue hands vertex groups of every bundle
+ * to the warps; the loop is one CUDA graph whose conditional node stops when no
+ * query is active.  Each query's result and superstep count equal gm_run's for
+ * the same graph, program and single source.
  *   graphs     n_graphs handles (their programs and states are not touched).
  *   queries    n_queries entries: graph index, GM_BFS or GM_SSSP, source vertex.
  *   out_state  n_queries device pointers, uint32[n of the query's graph] each:
@@ -264,8 +267,9 @@ GM_API gm_status gm_wpagerank_backward(gm_graph* g, const float* dLdx, float* dL
  *   max_iters  -1: every query until convergence; k > 0: at most k supersteps.
  *   iters_done NULL or int32[n_queries] (host): supersteps of each query.
  *   stream     cudaStream_t (NULL = default); the call synchronises it.
- * Workspace (messages, queued bits, two item queues per query) is allocated for
- * the call and released before it returns.
+ * Workspace (per bundle: two frontier bytes per vertex, and a reached byte per
+ * vertex for BFS or two 32-byte message rows per vertex for SSSP) is allocated
+ * for the call and released before it returns.
  */
 typedef struct gm_query {
     int32_t graph;   /* index into graphs */

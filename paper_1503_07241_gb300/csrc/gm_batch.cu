@@ -2,23 +2,27 @@
 // device-driven superstep loop (an added form; each query follows Algorithm 2
 // with the min semiring exactly as gm_run does).
 //
-// All queries advance in lockstep supersteps.  Superstep t is three kernels,
-// captured once in a CUDA graph whose conditional WHILE node repeats them until
-// every query has converged:
-//   relax     a device work queue of items (query, vertex, edge chunk) over all
-//             active queries' frontiers; a warp takes 32 consecutive items at a
-//             time (one atomic per 32 items), concatenates their edge lists and
-//             relaxes 8 edges per lane (atomicCAS for BFS, atomicMin for SSSP on
-//             the query's own distance array); vertices that change go to the
-//             query's next frontier (warp-aggregated per query with match_any).
-//   plan      one CTA: per query, the next frontier's length; a query whose
-//             frontier is empty has converged (its superstep count is t+1);
-//             prefix sums of the item counts index the next work queue; the WHILE
-//             condition is cleared once no query is active.
-//   snapshot  SSSP messages of superstep t+1 (the distances fixed now) and
-//             clearing of the "queued" bits, over the next work queue.
-// A vertex with more than kBChunk out-edges is queued as one item per chunk of
-// kBChunk edges, so no warp gets an unbounded edge list.
+// Queries of the same program on the same graph are bundled, up to 8 per bundle,
+// and a bundle's queries advance in lockstep supersteps as one multi-source
+// SpMSpV: a vertex's frontier membership for the bundle is one byte (bit q =
+// in query q's frontier), and for SSSP its 8 messages are one 32-byte row
+// (infinity for the queries whose frontier does not hold it).  Each superstep
+// pulls over the in-edges (CSC) of every vertex once for the whole bundle:
+//   BFS   new(v) = OR over in-edges u->v of front(u), minus the queries that
+//         already reached v (the scan stops once every missing query is found);
+//         depth_q(v) = t+1 for each new query q.
+//   SSSP  acc_q(v) = min over in-edges of sat(msg_q(u) + w(u, v)), one 32-byte
+//         gather per in-edge whose source is in any frontier; dist_q(v) =
+//         min(dist_q(v), acc_q(v)); the changed queries form front(v) and
+//         msg_q(v) of the next superstep.
+// The work of a superstep is one queue of warp items over all bundles of all
+// graphs: groups of 32 vertices of in-degree < bin_small (a lane each), single
+// vertices of larger in-degree (a warp each, lanes over the in-edges, warp
+// reductions), and groups of 32 vertices without in-edges (their next front
+// byte is cleared).  A one-CTA plan kernel retires the queries whose next
+// frontier is empty (recording their superstep counts) and stops the loop when
+// no query runs.  Both kernels are captured in one CUDA graph whose conditional
+// WHILE node repeats them.
 #include <algorithm>
 #include <vector>
 
@@ -29,311 +33,267 @@ namespace gm {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr int kEPT = 8;
-constexpr int kBChunk = 256;  // out-edges per work item
+constexpr int kSlots = 8;  // queries per bundle
 constexpr uint32_t kFull = 0xffffffffu;
 
 struct BGraph {
-    const int32_t* row_ptr;
-    const int32_t* col;
-    const uint32_t* w;  // nullptr: every weight is 1
+    const int32_t* col_ptr;
+    const int32_t* row;
+    const uint32_t* cw;   // uint32 in-edge weights, or nullptr
+    const uint8_t* cw8;   // one-byte copy when every weight fits, or nullptr
+    const int32_t* in_list;
+    int64_t in_off[4];    // bins 1..3 of in_list at [in_off[b-1], in_off[b])
+    const int32_t* zero_in;
+    int64_t zero_count;
     int64_t n;
 };
 
-struct BQuery {
-    int32_t graph, sssp, source, pad;
-    uint32_t* dist;   // caller's output, n of its graph
-    uint32_t* msg;    // SSSP messages (n)
-    uint32_t* qbits;  // "queued for the next superstep" bits (n/32 words)
-    int2* q[2];       // frontier items (vertex, chunk) by superstep parity
-    uint32_t cap;     // item capacity of each queue
+struct Bundle {
+    int32_t graph, sssp, nq, pad;
+    uint32_t* out[kSlots];   // the callers' depth / distance arrays (nullptr past nq)
+    int32_t qid[kSlots];     // index of each slot's query in the call
+    int32_t source[kSlots];
+    uint8_t* front[2];       // per vertex, by superstep parity: bit q = in query q's frontier
+    uint8_t* vis;            // BFS: bit q = reached by query q
+    uint32_t* msg[2];        // SSSP: n rows of 8 messages, by superstep parity
+    uint32_t item0;          // first work item of the bundle
+    uint32_t n_small, n_big, n_zero;  // work items of each kind
+    uint32_t active;         // queries still running (bits)
+    uint32_t next_active;    // queries with a vertex in the next frontier (this superstep)
 };
 
 struct BCtl {
     uint32_t t;
-    uint32_t active;       // queries still running
-    uint32_t item_next;    // work-queue head of the current superstep
-    uint32_t total[2];     // items in the queues of each parity
+    uint32_t any_active;
     uint32_t guard_hit;
-    uint32_t max_iters;    // 0: until convergence
-    uint32_t pad;
+    uint32_t max_iters;  // 0: until convergence
 };
 
 struct BArgs {
     const BGraph* graphs;
-    const BQuery* queries;
-    int32_t nq;
-    uint32_t* count;    // [nq][2] items queued per parity
-    uint32_t* prefix;   // [2][nq + 1] exclusive prefix of count per parity
-    uint32_t* done;     // [nq]
-    int32_t* iters;     // [nq]
+    Bundle* bundles;
+    int32_t nb;
+    uint32_t total_items;
+    int32_t* iters;  // per query of the call
     BCtl* ctl;
-    uint64_t guard;     // max n + 2
+    uint64_t guard;  // max n + 2
     cudaGraphConditionalHandle cond;
     int use_cond;
 };
 
 __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) {
     const uint32_t s = a + b;
-    return (s < a || s == kInf) ? kInf : s;
+    return s < b ? kInf : s;
 }
 
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ uint32_t edge_weight(const BGraph& G, int32_t e) {
+    return G.cw8 ? (uint32_t)G.cw8[e] : (G.cw ? G.cw[e] : 1u);
+}
+
+// The 8 messages of source u (two 16-byte loads).
+__device__ __forceinline__ void load_msgs(const uint32_t* __restrict__ msg, int32_t u, uint32_t (&m)[kSlots]) {
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(msg + (int64_t)u * kSlots));
+    const uint4 b = __ldg(reinterpret_cast<const uint4*>(msg + (int64_t)u * kSlots + 4));
+    m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w;
+    m[4] = b.x; m[5] = b.y; m[6] = b.z; m[7] = b.w;
+}
+
+// Apply of SSSP at v: returns the changed queries; writes the next messages row.
+__device__ __forceinline__ uint32_t sssp_apply(const Bundle& B, int32_t v, const uint32_t (&acc)[kSlots],
+                                               uint32_t* __restrict__ msg_next) {
+    uint32_t mask = 0u, nm[kSlots];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, v, o);
-        if (lane >= o) v += y;
+    for (int q = 0; q < kSlots; ++q) {
+        nm[q] = kInf;
+        if (q < B.nq && acc[q] != kInf && acc[q] < B.out[q][v]) {
+            B.out[q][v] = acc[q];
+            nm[q] = acc[q];
+            mask |= 1u << q;
+        }
     }
-    return v;
+    uint4* row = reinterpret_cast<uint4*>(msg_next + (int64_t)v * kSlots);
+    row[0] = make_uint4(nm[0], nm[1], nm[2], nm[3]);
+    row[1] = make_uint4(nm[4], nm[5], nm[6], nm[7]);
+    return mask;
 }
 
-// Largest q with pre[q] <= i (pre ascending, nq + 1 entries).
-__device__ __forceinline__ int32_t query_of(const uint32_t* pre, int32_t nq, uint32_t i) {
-    int32_t lo = 0, hi = nq - 1;
+// Apply of BFS at v: `found` = queries with an in-neighbour in their frontier.
+__device__ __forceinline__ uint32_t bfs_apply(const Bundle& B, int32_t v, uint32_t vis_v, uint32_t found,
+                                              uint32_t t) {
+    const uint32_t nw = found & ~vis_v;
+    if (nw) {
+        B.vis[v] = (uint8_t)(vis_v | nw);
+#pragma unroll
+        for (int q = 0; q < kSlots; ++q)
+            if ((nw >> q) & 1u) B.out[q][v] = t + 1u;
+    }
+    return nw;
+}
+
+__device__ __forceinline__ int32_t bundle_of(const Bundle* bs, int32_t nb, uint32_t item) {
+    int32_t lo = 0, hi = nb - 1;
     while (lo < hi) {
         const int32_t mid = (lo + hi + 1) >> 1;
-        if (pre[mid] <= i) lo = mid;
+        if (bs[mid].item0 <= item) lo = mid;
         else hi = mid - 1;
     }
     return lo;
 }
 
-__device__ __forceinline__ uint32_t chunks_of(const BGraph& g, int32_t v) {
-    const int32_t d = g.row_ptr[v + 1] - g.row_ptr[v];
-    return d <= 0 ? 1u : (uint32_t)((d + kBChunk - 1) / kBChunk);
-}
-
-__global__ void __launch_bounds__(kThreads) batch_relax(BArgs a) {
-    BCtl* c = a.ctl;
-    if (c->active == 0u) return;
+__global__ void __launch_bounds__(kThreads) batch_pull(BArgs a) {
+    const BCtl* c = a.ctl;
+    if (c->any_active == 0u) return;
     const uint32_t t = c->t;
     const int cur = (int)(t & 1u), nxt = cur ^ 1;
-    const uint32_t total = c->total[cur];
-    const uint32_t* pre = a.prefix + (size_t)cur * (a.nq + 1);
     const int lane = threadIdx.x & 31;
-    __shared__ int32_t s_beg[kWarps][32];
-    __shared__ uint32_t s_ex[kWarps][33];
-    __shared__ uint32_t s_du[kWarps][32];
-    __shared__ int32_t s_q[kWarps][32];
-    int32_t* sb = s_beg[threadIdx.x >> 5];
-    uint32_t* se = s_ex[threadIdx.x >> 5];
-    uint32_t* sd = s_du[threadIdx.x >> 5];
-    int32_t* sq = s_q[threadIdx.x >> 5];
-    while (true) {
-        uint32_t base = 0u;
-        if (lane == 0) base = atomicAdd(&c->item_next, 32u);
-        base = __shfl_sync(kFull, base, 0);
-        if (base >= total) break;
-        // this lane's item
-        const uint32_t i = base + lane;
-        int32_t qid = 0, beg = 0;
-        uint32_t deg = 0u, du = 0u;
-        if (i < total) {
-            qid = query_of(pre, a.nq, i);
-            const BQuery& Q = a.queries[qid];
-            const BGraph& G = a.graphs[Q.graph];
-            const int2 it = Q.q[cur][i - pre[qid]];
-            const int32_t rb = G.row_ptr[it.x], re = G.row_ptr[it.x + 1];
-            beg = rb + it.y * kBChunk;
-            const int32_t end = min(re, beg + kBChunk);
-            deg = end > beg ? (uint32_t)(end - beg) : 0u;
-            du = Q.sssp ? Q.msg[it.x] : t;
-        }
-        const uint32_t incl = warp_incl_scan(deg);
-        __syncwarp();
-        sb[lane] = beg;
-        se[lane] = incl - deg;
-        sd[lane] = du;
-        sq[lane] = qid;
-        if (lane == 31) se[32] = incl;
-        __syncwarp();
-        const uint32_t tot = se[32];
-        for (uint32_t b0 = 0; b0 < tot; b0 += 32 * kEPT) {
-            const uint32_t j0 = b0 + (uint32_t)lane * kEPT;
-            int o = 0;
+    const uint32_t gwarp = (blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * kThreads) >> 5;
+    for (uint32_t item = gwarp; item < a.total_items; item += nwarps) {
+        const int32_t bi = bundle_of(a.bundles, a.nb, item);
+        Bundle& B = a.bundles[bi];
+        if (B.active == 0u) continue;  // warp-uniform
+        const BGraph& G = a.graphs[B.graph];
+        const uint8_t* __restrict__ fc = B.front[cur];
+        uint8_t* __restrict__ fn = B.front[nxt];
+        uint32_t k = item - B.item0;
+        uint32_t mask = 0u;
+        if (k < B.n_small) {  // 32 vertices of small in-degree, a lane each
+            const int64_t i = G.in_off[0] + (int64_t)k * 32 + lane;
+            if (i < G.in_off[1]) {
+                const int32_t v = G.in_list[i];
+                const int32_t beg = G.col_ptr[v], end = G.col_ptr[v + 1];
+                if (B.sssp) {
+                    uint32_t acc[kSlots];
 #pragma unroll
-            for (int step = 16; step >= 1; step >>= 1)
-                if (se[o + step] <= j0) o += step;
-            int32_t vq[kEPT], qq[kEPT];
-            uint32_t nd[kEPT];
-            bool want[kEPT];
+                    for (int q = 0; q < kSlots; ++q) acc[q] = kInf;
+                    for (int32_t e = beg; e < end; ++e) {
+                        const int32_t u = G.row[e];
+                        if (!fc[u]) continue;
+                        uint32_t m[kSlots];
+                        load_msgs(B.msg[cur], u, m);
+                        const uint32_t w = edge_weight(G, e);
 #pragma unroll
-            for (int k = 0; k < kEPT; ++k) {
-                const uint32_t j = j0 + k;
-                vq[k] = 0;
-                qq[k] = -1;
-                nd[k] = kInf;
-                want[k] = false;
-                if (j < tot) {
-                    while (j >= se[o + 1]) ++o;
-                    const int32_t e = sb[o] + (int32_t)(j - se[o]);
-                    const BQuery& Q = a.queries[sq[o]];
-                    const BGraph& G = a.graphs[Q.graph];
-                    vq[k] = G.col[e];
-                    qq[k] = sq[o];
-                    nd[k] = Q.sssp ? sat_add(sd[o], G.w ? G.w[e] : 1u) : sd[o] + 1u;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < kEPT; ++k) {
-                if (qq[k] < 0) continue;
-                const BQuery& Q = a.queries[qq[k]];
-                uint32_t* dv = Q.dist + vq[k];
-                if (nd[k] >= *dv) continue;
-                if (Q.sssp) {
-                    if (nd[k] < atomicMin(dv, nd[k])) {
-                        const uint32_t bit = 1u << (vq[k] & 31);
-                        want[k] = (atomicOr(Q.qbits + (vq[k] >> 5), bit) & bit) == 0u;
+                        for (int q = 0; q < kSlots; ++q) acc[q] = min(acc[q], sat_add(m[q], w));
                     }
+                    mask = sssp_apply(B, v, acc, B.msg[nxt]);
                 } else {
-                    want[k] = atomicCAS(dv, kInf, nd[k]) == kInf;
+                    const uint32_t vis_v = B.vis[v];
+                    const uint32_t need = B.active & ~vis_v;  // running queries that have not reached v
+                    uint32_t found = 0u;
+                    for (int32_t e = beg; e < end && (found & need) != need; ++e) found |= fc[G.row[e]];
+                    mask = need ? bfs_apply(B, v, vis_v, found, t) : 0u;
                 }
+                fn[v] = (uint8_t)mask;
             }
-            // append to each query's next frontier, aggregated per query within the warp
+        } else if ((k -= B.n_small) < B.n_big) {  // one vertex of larger in-degree, a warp
+            const int32_t v = G.in_list[G.in_off[1] + k];
+            const int32_t beg = G.col_ptr[v], end = G.col_ptr[v + 1];
+            if (B.sssp) {
+                uint32_t acc[kSlots];
 #pragma unroll
-            for (int k = 0; k < kEPT; ++k) {
-                uint32_t items = 0u;
-                if (want[k]) items = chunks_of(a.graphs[a.queries[qq[k]].graph], vq[k]);
-                const int key = want[k] ? qq[k] : -1 - lane;
-                const uint32_t peers = __match_any_sync(kFull, key);
-                if (!want[k]) continue;
-                const int leader = __ffs(peers) - 1;
-                // exclusive prefix of items among lower peers
-                uint32_t before = 0u, sum = 0u;
-                for (uint32_t m = peers; m; m &= m - 1) {
-                    const int l = __ffs(m) - 1;
-                    const uint32_t x = __shfl_sync(peers, items, l);
-                    if (l < lane) before += x;
-                    sum += x;
+                for (int q = 0; q < kSlots; ++q) acc[q] = kInf;
+                for (int32_t e = beg + lane; e < end; e += 32) {
+                    const int32_t u = G.row[e];
+                    if (!fc[u]) continue;
+                    uint32_t m[kSlots];
+                    load_msgs(B.msg[cur], u, m);
+                    const uint32_t w = edge_weight(G, e);
+#pragma unroll
+                    for (int q = 0; q < kSlots; ++q) acc[q] = min(acc[q], sat_add(m[q], w));
                 }
-                uint32_t pos = 0u;
-                if (lane == leader) pos = atomicAdd(&a.count[qq[k] * 2 + nxt], sum);
-                pos = __shfl_sync(peers, pos, leader) + before;
-                const BQuery& Q = a.queries[qq[k]];
-                if (pos + items <= Q.cap)
-                    for (uint32_t ch = 0; ch < items; ++ch) Q.q[nxt][pos + ch] = make_int2(vq[k], (int32_t)ch);
+#pragma unroll
+                for (int q = 0; q < kSlots; ++q) acc[q] = __reduce_min_sync(kFull, acc[q]);
+                if (lane == 0) {
+                    mask = sssp_apply(B, v, acc, B.msg[nxt]);
+                    fn[v] = (uint8_t)mask;
+                }
+            } else {
+                const uint32_t vis_v = B.vis[v];
+                const uint32_t need = B.active & ~vis_v;
+                uint32_t found = 0u;
+                for (int32_t e0 = beg; e0 < end && need; e0 += 32) {
+                    if (e0 + lane < end) found |= fc[G.row[e0 + lane]];
+                    found = __reduce_or_sync(kFull, found);
+                    if ((found & need) == need) break;  // warp-uniform
+                }
+                if (lane == 0) {
+                    mask = need ? bfs_apply(B, v, vis_v, found, t) : 0u;
+                    fn[v] = (uint8_t)mask;
+                }
             }
+        } else {  // 32 vertices without in-edges: nothing reaches them
+            k -= B.n_big;
+            const int64_t i = (int64_t)k * 32 + lane;
+            if (i < G.zero_count) fn[G.zero_in[i]] = 0u;
         }
+        mask = __reduce_or_sync(kFull, mask);
+        if (lane == 0 && mask) atomicOr(&B.next_active, mask);
     }
 }
 
-// One CTA: convergence, prefix sums of the next work queue, the loop condition.
+// One CTA: retire the queries whose next frontier is empty, stop at max_iters,
+// advance the superstep and set the loop condition.
 __global__ void batch_plan(BArgs a) {
     BCtl* c = a.ctl;
-    __shared__ uint32_t s_part[1024 / 32 + 1];
-    __shared__ uint32_t s_active;
-    if (c->active == 0u) return;
+    __shared__ uint32_t s_any;
+    if (c->any_active == 0u) return;
     const uint32_t t = c->t;
-    const int nxt = (int)((t + 1u) & 1u);
-    if (threadIdx.x == 0) s_active = 0u;
+    if (threadIdx.x == 0) s_any = 0u;
     __syncthreads();
-    uint32_t* pre = a.prefix + (size_t)nxt * (a.nq + 1);
-    uint32_t run = 0u;
-    for (int32_t q0 = 0; q0 < a.nq; q0 += blockDim.x) {
-        const int32_t q = q0 + (int32_t)threadIdx.x;
-        uint32_t items = 0u;
-        if (q < a.nq && !a.done[q]) {
-            items = a.count[q * 2 + nxt];
-            a.iters[q] = (int32_t)(t + 1u);
-            bool stop = items == 0u || (c->max_iters > 0u && t + 1u >= c->max_iters);
-            if (items > a.queries[q].cap) {  // cannot happen: each vertex is queued once per superstep
-                c->guard_hit = 1u;
-                stop = true;
-            }
-            if (stop) {
-                a.done[q] = 1u;
-                items = 0u;
-            } else {
-                atomicAdd(&s_active, 1u);
-            }
-            a.count[q * 2 + (nxt ^ 1)] = 0u;  // the consumed queue is refilled two supersteps on
-        }
-        // block-wide exclusive scan of items
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        const uint32_t incl = warp_incl_scan(items);
-        if (lane == 31) s_part[wid] = incl;
-        __syncthreads();
-        if (wid == 0) {
-            const uint32_t nw = blockDim.x / 32;
-            uint32_t v = lane < (int)nw ? s_part[lane] : 0u;
-            const uint32_t vi = warp_incl_scan(v);
-            if (lane < (int)nw) s_part[lane] = vi - v;
-            if (lane == 31) s_part[32] = vi;
-        }
-        __syncthreads();
-        if (q < a.nq) pre[q] = run + s_part[wid] + incl - items;
-        run += s_part[32];
-        __syncthreads();
+    const bool stop = (c->max_iters != 0u && t + 1u >= c->max_iters) || (uint64_t)t + 1u >= a.guard;
+    for (int32_t b = threadIdx.x; b < a.nb; b += blockDim.x) {
+        Bundle& B = a.bundles[b];
+        if (B.active == 0u) continue;
+        const uint32_t still = stop ? 0u : (B.active & B.next_active);
+        const uint32_t ended = B.active & ~still;
+        for (int q = 0; q < kSlots; ++q)
+            if ((ended >> q) & 1u) a.iters[B.qid[q]] = (int32_t)(t + 1u);
+        if (still == 0u && (B.active & B.next_active) != 0u && (uint64_t)t + 1u >= a.guard) c->guard_hit = 1u;
+        B.active = still;
+        B.next_active = 0u;
+        if (still) atomicOr(&s_any, 1u);
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        pre[a.nq] = run;
-        c->total[nxt] = run;
-        c->item_next = 0u;
         c->t = t + 1u;
-        c->active = s_active;
-        if ((uint64_t)t + 1u >= a.guard && s_active) {
-            c->guard_hit = 1u;
-            c->active = 0u;
-        }
-        if (a.use_cond) cudaGraphSetConditional(a.cond, c->active ? 1u : 0u);
+        c->any_active = s_any;
+        if (a.use_cond) cudaGraphSetConditional(a.cond, s_any ? 1u : 0u);
     }
 }
 
-// Messages of the next superstep (SSSP) and clearing of the queued bits.
-__global__ void batch_snapshot(BArgs a) {
-    BCtl* c = a.ctl;
-    if (c->active == 0u) return;
-    const int cur = (int)(c->t & 1u);  // plan already advanced t
-    const uint32_t total = c->total[cur];
-    const uint32_t* pre = a.prefix + (size_t)cur * (a.nq + 1);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        const int32_t q = query_of(pre, a.nq, i);
-        const BQuery& Q = a.queries[q];
-        if (!Q.sssp) continue;
-        const int2 it = Q.q[cur][i - pre[q]];
-        if (it.y != 0) continue;
-        Q.msg[it.x] = Q.dist[it.x];
-        atomicAnd(Q.qbits + (it.x >> 5), ~(1u << (it.x & 31)));
+// Every bundle's arrays at the start: fronts and reached bits clear, messages
+// and outputs infinity (bundles strided over y, vertices over x).
+__global__ void batch_clear(BArgs a) {
+    for (int32_t b = blockIdx.y; b < a.nb; b += gridDim.y) {
+    const Bundle& B = a.bundles[b];
+    const int64_t n = a.graphs[B.graph].n;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        B.front[0][v] = 0u;
+        B.front[1][v] = 0u;
+        if (!B.sssp) B.vis[v] = 0u;
+        for (int q = 0; q < B.nq; ++q) B.out[q][v] = kInf;
+        if (B.sssp)
+            for (int s = 0; s < 2; ++s) {
+                uint4* row = reinterpret_cast<uint4*>(B.msg[s] + v * kSlots);
+                row[0] = make_uint4(kInf, kInf, kInf, kInf);
+                row[1] = make_uint4(kInf, kInf, kInf, kInf);
+            }
+    }
     }
 }
 
-// Initial state: distances infinity except the source, the source queued.
+// The sources (one thread per bundle, after batch_clear).
 __global__ void batch_seed(BArgs a) {
-    const int32_t q = blockIdx.y;
-    if (q >= a.nq) return;
-    const BQuery& Q = a.queries[q];
-    const BGraph& G = a.graphs[Q.graph];
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < G.n; v += (int64_t)gridDim.x * blockDim.x) {
-        Q.dist[v] = v == Q.source ? 0u : kInf;
-        if (Q.sssp && (v & 31) == 0) Q.qbits[v >> 5] = 0u;
+    for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < a.nb; b += gridDim.x * blockDim.x) {
+        const Bundle& B = a.bundles[b];
+        for (int q = 0; q < B.nq; ++q) {
+            const int32_t s = B.source[q];
+            B.out[q][s] = 0u;
+            B.front[0][s] |= (uint8_t)(1u << q);
+            if (B.sssp) B.msg[0][(int64_t)s * kSlots + q] = 0u;
+            else B.vis[s] |= (uint8_t)(1u << q);
+        }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const uint32_t nch = chunks_of(G, Q.source);
-        for (uint32_t ch = 0; ch < nch; ++ch) Q.q[0][ch] = make_int2(Q.source, (int32_t)ch);
-        if (Q.sssp) Q.msg[Q.source] = 0u;
-        a.count[q * 2 + 0] = nch;
-        a.count[q * 2 + 1] = 0u;
-        a.done[q] = 0u;
-        a.iters[q] = 0;
-    }
-}
-
-__global__ void batch_prefix0(BArgs a) {  // single thread: prefix of the initial queues
-    uint32_t run = 0u;
-    for (int32_t q = 0; q < a.nq; ++q) {
-        a.prefix[q] = run;
-        run += a.count[q * 2];
-    }
-    a.prefix[a.nq] = run;
-    BCtl* c = a.ctl;
-    c->t = 0u;
-    c->active = a.nq > 0 ? (uint32_t)a.nq : 0u;
-    c->item_next = 0u;
-    c->total[0] = run;
-    c->total[1] = 0u;
-    c->guard_hit = 0u;
 }
 
 }  // namespace
@@ -352,26 +312,8 @@ gm_status gm_run_batch(gm_graph* const* graphs, int32_t n_graphs, const gm_query
     }
     if (max_iters < -1) { set_error("gm_run_batch: max_iters must be >= -1"); return GM_ERR_INVALID_ARG; }
     if (n_queries == 0) return GM_OK;
-    if (max_iters == 0) {
-        for (int32_t i = 0; i < n_queries; ++i)
-            if (iters_done) iters_done[i] = 0;
-        return GM_OK;
-    }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    std::vector<BGraph> hg((size_t)n_graphs);
-    int64_t max_n = 0;
-    for (int32_t gi = 0; gi < n_graphs; ++gi) {
-        const gm_graph* g = graphs[gi];
-        if (!g) { set_error("gm_run_batch: graph %d is NULL", gi); return GM_ERR_INVALID_ARG; }
-        hg[gi] = BGraph{as<int32_t>(g->row_ptr), as<int32_t>(g->col),
-                        g->wtype == GM_W_U32 ? as<uint32_t>(g->w) : nullptr, g->n};
-        max_n = std::max(max_n, g->n);
-    }
-    // per-query workspace: messages, queued bits and two item queues
-    std::vector<BQuery> hq((size_t)n_queries);
-    std::vector<size_t> offs((size_t)n_queries);
-    size_t total_bytes = 0;
-    auto round = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    for (int32_t gi = 0; gi < n_graphs; ++gi)
+        if (!graphs[gi]) { set_error("gm_run_batch: graph %d is NULL", gi); return GM_ERR_INVALID_ARG; }
     for (int32_t i = 0; i < n_queries; ++i) {
         const gm_query& Q = queries[i];
         if (Q.graph < 0 || Q.graph >= n_graphs || (Q.kind != GM_BFS && Q.kind != GM_SSSP) || !out_state[i]) {
@@ -387,66 +329,122 @@ gm_status gm_run_batch(gm_graph* const* graphs, int32_t n_graphs, const gm_query
             set_error("gm_run_batch: query %d: SSSP needs uint32 weights", i);
             return GM_ERR_INVALID_ARG;
         }
-        const int64_t n = g->n, cap = n + g->m / kBChunk + 2;
-        offs[i] = total_bytes;
-        total_bytes += round(sizeof(uint32_t) * n) + round(sizeof(uint32_t) * ((n + 31) / 32)) +
-                       2 * round(sizeof(int2) * cap);
-        hq[i] = BQuery{Q.graph, Q.kind == GM_SSSP ? 1 : 0, Q.source, 0, out_state[i], nullptr, nullptr,
-                       {nullptr, nullptr}, (uint32_t)cap};
     }
-    DevBuf work, dgraphs, dqueries, arrays, ctl;
+    if (max_iters == 0) {
+        for (int32_t i = 0; i < n_queries; ++i)
+            if (iters_done) iters_done[i] = 0;
+        return GM_OK;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<BGraph> hg((size_t)n_graphs);
+    int64_t max_n = 0;
+    for (int32_t gi = 0; gi < n_graphs; ++gi) {
+        const gm_graph* g = graphs[gi];
+        BGraph& G = hg[gi];
+        G.col_ptr = as<int32_t>(g->col_ptr);
+        G.row = as<int32_t>(g->row);
+        G.cw = g->wtype == GM_W_U32 ? as<uint32_t>(g->cw) : nullptr;
+        G.cw8 = g->wtype == GM_W_U32 ? as<uint8_t>(g->cw8) : nullptr;
+        G.in_list = as<int32_t>(g->in_list);
+        for (int b = 0; b < 4; ++b) G.in_off[b] = g->in_list_count[b];
+        G.zero_in = as<int32_t>(g->zero_in_list);
+        G.zero_count = g->zero_in_count;
+        G.n = g->n;
+        max_n = std::max(max_n, g->n);
+    }
+    // bundles: queries of one program on one graph, up to kSlots each, in call order
+    std::vector<Bundle> hb;
+    {
+        std::vector<int32_t> open((size_t)n_graphs * 2, -1);
+        for (int32_t i = 0; i < n_queries; ++i) {
+            const gm_query& Q = queries[i];
+            const int key = Q.graph * 2 + (Q.kind == GM_SSSP ? 1 : 0);
+            if (open[key] < 0 || hb[open[key]].nq == kSlots) {
+                Bundle b{};
+                b.graph = Q.graph;
+                b.sssp = Q.kind == GM_SSSP ? 1 : 0;
+                open[key] = (int32_t)hb.size();
+                hb.push_back(b);
+            }
+            Bundle& b = hb[open[key]];
+            b.out[b.nq] = out_state[i];
+            b.qid[b.nq] = i;
+            b.source[b.nq] = Q.source;
+            b.nq++;
+        }
+    }
+    // work items and workspace of every bundle
+    auto round = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t ws = 0;
+    uint64_t items = 0;
+    std::vector<size_t> offs(hb.size());
+    for (size_t b = 0; b < hb.size(); ++b) {
+        Bundle& B = hb[b];
+        const BGraph& G = hg[B.graph];
+        const int64_t n = G.n > 0 ? G.n : 1;
+        B.item0 = (uint32_t)items;
+        B.n_small = (uint32_t)((G.in_off[1] - G.in_off[0] + 31) / 32);
+        B.n_big = (uint32_t)(G.in_off[3] - G.in_off[1]);
+        B.n_zero = (uint32_t)((G.zero_count + 31) / 32);
+        items += (uint64_t)B.n_small + B.n_big + B.n_zero;
+        B.active = (1u << B.nq) - 1u;
+        offs[b] = ws;
+        ws += 2 * round((size_t)n) + (B.sssp ? 2 * round(sizeof(uint32_t) * kSlots * (size_t)n) : round((size_t)n));
+    }
+    if (items >= (1ull << 32)) { set_error("gm_run_batch: too many work items"); return GM_ERR_INVALID_ARG; }
+    DevBuf work, dgraphs, dbundles, diters, ctl;
     struct Scope {
         cudaStream_t s;
         DevBuf* b[5];
         ~Scope() { for (DevBuf* x : b) dev_free(*x, s); }
-    } scope{s, {&work, &dgraphs, &dqueries, &arrays, &ctl}};
-    GM_TRY(dev_alloc(work, total_bytes, s));
-    char* base = static_cast<char*>(work.p);
-    for (int32_t i = 0; i < n_queries; ++i) {
-        const gm_graph* g = graphs[hq[i].graph];
-        const int64_t n = g->n;
-        char* p = base + offs[i];
-        hq[i].msg = reinterpret_cast<uint32_t*>(p);
-        p += round(sizeof(uint32_t) * n);
-        hq[i].qbits = reinterpret_cast<uint32_t*>(p);
-        p += round(sizeof(uint32_t) * ((n + 31) / 32));
-        hq[i].q[0] = reinterpret_cast<int2*>(p);
-        p += round(sizeof(int2) * hq[i].cap);
-        hq[i].q[1] = reinterpret_cast<int2*>(p);
+    } scope{s, {&work, &dgraphs, &dbundles, &diters, &ctl}};
+    GM_TRY(dev_alloc(work, ws, s));
+    for (size_t b = 0; b < hb.size(); ++b) {
+        Bundle& B = hb[b];
+        const int64_t n = hg[B.graph].n > 0 ? hg[B.graph].n : 1;
+        char* p = static_cast<char*>(work.p) + offs[b];
+        B.front[0] = reinterpret_cast<uint8_t*>(p);
+        p += round((size_t)n);
+        B.front[1] = reinterpret_cast<uint8_t*>(p);
+        p += round((size_t)n);
+        if (B.sssp) {
+            B.msg[0] = reinterpret_cast<uint32_t*>(p);
+            p += round(sizeof(uint32_t) * kSlots * (size_t)n);
+            B.msg[1] = reinterpret_cast<uint32_t*>(p);
+        } else {
+            B.vis = reinterpret_cast<uint8_t*>(p);
+        }
     }
-    GM_TRY(dev_alloc(dgraphs, sizeof(BGraph) * (hg.size() + 1), s));
-    GM_TRY(dev_alloc(dqueries, sizeof(BQuery) * hq.size(), s));
-    const size_t nq = (size_t)n_queries;
-    const size_t arr_bytes = sizeof(uint32_t) * (2 * nq + 2 * (nq + 1) + nq) + sizeof(int32_t) * nq;
-    GM_TRY(dev_alloc(arrays, arr_bytes, s));
+    GM_TRY(dev_alloc(dgraphs, sizeof(BGraph) * hg.size(), s));
+    GM_TRY(dev_alloc(dbundles, sizeof(Bundle) * hb.size(), s));
+    GM_TRY(dev_alloc(diters, sizeof(int32_t) * (size_t)n_queries, s));
     GM_TRY(dev_alloc(ctl, sizeof(BCtl), s));
     GM_CUDA_TRY(cudaMemcpyAsync(dgraphs.p, hg.data(), sizeof(BGraph) * hg.size(), cudaMemcpyHostToDevice, s));
-    GM_CUDA_TRY(cudaMemcpyAsync(dqueries.p, hq.data(), sizeof(BQuery) * hq.size(), cudaMemcpyHostToDevice, s));
+    GM_CUDA_TRY(cudaMemcpyAsync(dbundles.p, hb.data(), sizeof(Bundle) * hb.size(), cudaMemcpyHostToDevice, s));
+    GM_CUDA_TRY(cudaMemsetAsync(diters.p, 0, sizeof(int32_t) * (size_t)n_queries, s));
     BCtl hc{};
+    hc.any_active = 1u;
     hc.max_iters = max_iters > 0 ? (uint32_t)max_iters : 0u;
     GM_CUDA_TRY(cudaMemcpyAsync(ctl.p, &hc, sizeof(BCtl), cudaMemcpyHostToDevice, s));
     BArgs a{};
     a.graphs = as<BGraph>(dgraphs);
-    a.queries = as<BQuery>(dqueries);
-    a.nq = n_queries;
-    uint32_t* ab = as<uint32_t>(arrays);
-    a.count = ab;
-    a.prefix = ab + 2 * nq;
-    a.done = a.prefix + 2 * (nq + 1);
-    a.iters = reinterpret_cast<int32_t*>(a.done + nq);
+    a.bundles = as<Bundle>(dbundles);
+    a.nb = (int32_t)hb.size();
+    a.total_items = (uint32_t)items;
+    a.iters = as<int32_t>(diters);
     a.ctl = as<BCtl>(ctl);
     a.guard = (uint64_t)max_n + 2u;
-    // seed every query, then build the initial work queue
     {
-        dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((max_n + 255) / 256, 64)), (unsigned)n_queries);
-        batch_seed<<<grid, 256, 0, s>>>(a);
-        batch_prefix0<<<1, 1, 0, s>>>(a);
+        const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((max_n + 255) / 256, 256)),
+                        (unsigned)std::min<size_t>(hb.size(), 65535));
+        batch_clear<<<grid, 256, 0, s>>>(a);
+        batch_seed<<<1, 128, 0, s>>>(a);
         g_launches += 2;
         GM_CUDA_TRY(cudaGetLastError());
     }
-    // the superstep loop: WHILE { relax; plan; snapshot }
+    // the superstep loop: WHILE { pull over every bundle; plan }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_relax, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_pull, kThreads, 0);
     if (per_sm <= 0) per_sm = 1;
     cudaGraph_t graph;
     GM_CUDA_TRY(cudaGraphCreate(&graph, 0));
@@ -470,8 +468,8 @@ gm_status gm_run_batch(gm_graph* const* graphs, int32_t n_graphs, const gm_query
         cudaKernelNodeParams kp = {};
         kp.blockDim = dim3(kThreads);
         kp.kernelParams = kargs;
-        cudaGraphNode_t n1, n2, n3;
-        kp.func = (void*)batch_relax;
+        cudaGraphNode_t n1, n2;
+        kp.func = (void*)batch_pull;
         kp.gridDim = dim3((unsigned)(per_sm * num_sms()));
         e = cudaGraphAddKernelNode(&n1, body, nullptr, 0, &kp);
         if (e == cudaSuccess) {
@@ -479,12 +477,6 @@ gm_status gm_run_batch(gm_graph* const* graphs, int32_t n_graphs, const gm_query
             kp.gridDim = dim3(1);
             kp.blockDim = dim3(1024);
             e = cudaGraphAddKernelNode(&n2, body, &n1, 1, &kp);
-        }
-        if (e == cudaSuccess) {
-            kp.func = (void*)batch_snapshot;
-            kp.gridDim = dim3((unsigned)(num_sms() * 2));
-            kp.blockDim = dim3(kThreads);
-            e = cudaGraphAddKernelNode(&n3, body, &n2, 1, &kp);
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
         if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
@@ -495,13 +487,13 @@ gm_status gm_run_batch(gm_graph* const* graphs, int32_t n_graphs, const gm_query
         set_error("gm_run_batch: superstep loop graph: %s", cudaGetErrorString(e));
         return GM_ERR_CUDA;
     }
-    std::vector<int32_t> its(nq);
-    GM_CUDA_TRY(cudaMemcpyAsync(its.data(), a.iters, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> its((size_t)n_queries);
+    GM_CUDA_TRY(cudaMemcpyAsync(its.data(), diters.p, sizeof(int32_t) * (size_t)n_queries, cudaMemcpyDeviceToHost, s));
     GM_CUDA_TRY(cudaMemcpyAsync(&hc, ctl.p, sizeof(BCtl), cudaMemcpyDeviceToHost, s));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
-    g_launches += 3ull * hc.t;
+    g_launches += 2ull * hc.t;
     if (iters_done)
-        for (size_t i = 0; i < nq; ++i) iters_done[i] = its[i];
+        for (int32_t i = 0; i < n_queries; ++i) iters_done[i] = its[(size_t)i];
     if (hc.guard_hit) {
         set_error("gm_run_batch: superstep loop exceeded its bound (internal error)");
         return GM_ERR_TIMEOUT;

@@ -102,3 +102,29 @@ def test_batch_config_64_graphs_1024_queries(gm):
         n, s, d, w, g = graphs[gi]
         oref, oit = (oracle.Graph(n, s, d, w).bfs if kind == 1 else oracle.Graph(n, s, d, w).sssp)([src])
         assert np.array_equal(res[i], oref) and its[i] == oit
+
+
+def test_batch_full_bundles_duplicates_and_unweighted(gm):
+    """More than eight queries of one program on one graph (several bundles, one
+    partly filled), repeated sources inside a bundle, interleaved programs, an
+    unweighted graph next to a weighted one, and a graph of one vertex."""
+    n, s, d = synth.rmat(10, 16, synth.RMAT_PARAMS["graph500"], synth.BASE_SEED + 90)
+    w = synth.edge_weights_u32(s, d, synth.BASE_SEED + 91)
+    gw = gm.Graph(n, s, d, w)
+    gu = gm.Graph(n, s, d)
+    g1 = gm.Graph(1, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.uint32))
+    src = synth.pick_sources(n, s, d, 12, seed=92)
+    queries = []
+    for i in range(21):
+        queries.append((0, 2 if i % 3 else 1, int(src[i % 12])))
+        queries.append((1, 1 if i % 2 else 2, int(src[(5 * i) % 12])))
+    queries += [(2, 1, 0), (2, 2, 0)]
+    graphs = [(n, s, d, w, gw), (n, s, d, None, gu), (1, None, None, None, g1)]
+    res, its = _run(gm, graphs, queries)
+    og = {0: oracle.Graph(n, s, d, w), 1: oracle.Graph(n, s, d)}
+    for (gi, kind, x), got, it in zip(queries, res, its):
+        if gi == 2:
+            assert got.tolist() == [0] and it == 1
+            continue
+        oref, oit = (og[gi].bfs if kind == 1 else og[gi].sssp)([x])
+        assert np.array_equal(got, oref) and it == oit
