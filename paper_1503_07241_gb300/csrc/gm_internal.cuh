@@ -83,6 +83,7 @@ struct TravCtl {
     uint32_t bad_ids;             // seeding saw vertex ids outside [0, n)
     uint32_t guard_hit;           // the loop passed n + 1 supersteps (impossible for valid runs)
     uint32_t stage_timeouts;      // pull CTAs whose shared-memory staging copy did not complete in time
+    uint32_t loops;               // iterations of the device loop (for the launch count)
 };
 
 // Options and tuning knobs of a graph handle.

@@ -56,6 +56,7 @@ struct TravArgs {
     const int32_t* col_ptr; const int32_t* row; const uint32_t* cw;
     const uint8_t* cw8;      // one byte per in-edge weight when all fit (nullptr otherwise)
     const int32_t* out_deg; const int32_t* in_deg; const uint8_t* out_bin;
+    int32_t bin_small, bin_large;  // degree bins (out_bin[v] == out_bin_of(out_deg[v]))
     const int32_t* in_list; int64_t in_s0, in_s1, in_m1;  // small bin [in_s0, in_s1), medium [in_s1, in_m1)
     const int32_t* dc_jc; const int32_t* dc_cp; const int32_t* dc_tile;  // doubly compressed CSC + tiles
     int64_t dc_ncols, ntiles;
@@ -99,6 +100,11 @@ struct Acc {
 __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) {
     const uint32_t s = a + b;
     return s < b ? kInf : s;
+}
+
+// Out-degree bin of a vertex from its out-degree (the rule that built out_bin).
+__device__ __forceinline__ uint32_t out_bin_of(const TravArgs& a, uint32_t d) {
+    return d == 0u ? 0u : (d < (uint32_t)a.bin_small ? 1u : (d < (uint32_t)a.bin_large ? 2u : 3u));
 }
 
 __device__ __forceinline__ bool test_bit(const uint32_t* bv, int32_t v) {
@@ -842,7 +848,7 @@ __global__ void __launch_bounds__(kThreads, 4) trav_pull_bu(TravArgs a) {
 // SSSP Apply after trav_pull_a: four columns per lane per step (independent loads
 // in flight), coalesced across the warp for each of the four.
 
-__global__ void __launch_bounds__(kThreads) trav_pull_b(TravArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) trav_pull_b(TravArgs a) {
     TravCtlDev* cd = a.ctl;
     if (cd->c.done || cd->c.dir != 1u) return;
     const uint32_t t = cd->c.iter;
@@ -859,39 +865,58 @@ __global__ void __launch_bounds__(kThreads) trav_pull_b(TravArgs a) {
     uint32_t* __restrict__ y = a.ycol;
     uint32_t* __restrict__ msgn = a.msg[(t + 1u) & 1u];
     constexpr int kSpan = 32 * kColsPerLane;
-    for (int64_t base = gwarp * kSpan; base < a.dc_ncols; base += nwarps * kSpan) {
-        uint32_t b[kColsPerLane], dv[kColsPerLane];
-        int32_t v[kColsPerLane];
+    // column data of a step: reduced value, vertex and source rank (independent
+    // loads); the next step's are loaded while this step's vertices are read
+    uint32_t b[kColsPerLane];
+    int32_t v[kColsPerLane], rk[kColsPerLane];
+    auto load_cols = [&](int64_t base) {
 #pragma unroll
         for (int k = 0; k < kColsPerLane; ++k) {
             const int64_t c = base + 32 * k + lane;
-            b[k] = c < a.dc_ncols ? y[c] : kInf;
-            v[k] = c < a.dc_ncols ? __ldg(a.dc_jc + c) : 0x7fffffff;
+            const bool in = c < a.dc_ncols;
+            b[k] = in ? y[c] : kInf;
+            v[k] = in ? __ldg(a.dc_jc + c) : 0x7fffffff;
+            rk[k] = in ? __ldg(a.dc_rank + c) : 0;
         }
-        // the degree data the enqueue needs is loaded together with the property
+    };
+    int64_t base = gwarp * kSpan;
+    if (base < a.dc_ncols) load_cols(base);
+    for (; base < a.dc_ncols; base += nwarps * kSpan) {
+        uint32_t dv[kColsPerLane];
+        // the out-degree the enqueue needs is loaded together with the property
         uint32_t vb[kEPT] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u}, vd[kEPT] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
         const uint32_t vin[kEPT] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll
         for (int k = 0; k < kColsPerLane; ++k) {
             dv[k] = b[k] != kInf ? a.dist[v[k]] : 0u;
-            vb[k] = b[k] != kInf ? (uint32_t)__ldg(a.out_bin + v[k]) : 0u;
             vd[k] = b[k] != kInf ? (uint32_t)__ldg(a.out_deg + v[k]) : 0u;
         }
         bool wa[kEPT] = {false, false, false, false, false, false, false, false};
         int32_t va[kEPT] = {0, 0, 0, 0, 0, 0, 0, 0};
+        uint32_t bc[kColsPerLane];
+        int32_t rc[kColsPerLane], vc[kColsPerLane];
 #pragma unroll
         for (int k = 0; k < kColsPerLane; ++k) {
-            if (b[k] != kInf) {
+            bc[k] = b[k];
+            rc[k] = rk[k];
+            vc[k] = v[k];
+        }
+        const int64_t next = base + nwarps * kSpan;
+        if (next < a.dc_ncols) load_cols(next);
+#pragma unroll
+        for (int k = 0; k < kColsPerLane; ++k) {
+            if (bc[k] != kInf) {
                 y[base + 32 * k + lane] = kInf;
                 acc.verts++;
-                if (b[k] < dv[k]) {
-                    a.dist[v[k]] = b[k];
-                    msgn[a.dc_rank[base + 32 * k + lane]] = b[k];  // superstep t+1's message (finalize skips pulls)
+                if (bc[k] < dv[k]) {
+                    a.dist[vc[k]] = bc[k];
+                    msgn[rc[k]] = bc[k];  // superstep t+1's message (finalize skips pulls)
                     wa[k] = true;
-                    va[k] = v[k];
+                    va[k] = vc[k];
+                    vb[k] = out_bin_of(a, vd[k]);
                 }
             }
-            warp_set_bits(a.bv[nxt], v[k], wa[k]);
+            warp_set_bits(a.bv[nxt], vc[k], wa[k]);
         }
         enqueue_batch_pre<false>(a, wa, va, vb, vd, vin, nxt, acc);
     }
@@ -915,6 +940,51 @@ __global__ void __launch_bounds__(kThreads) trav_push(TravArgs a) {
     Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, &s_q[threadIdx.x >> 5]};
     push_phase<SSSP>(a, t, cur, nxt, acc, s_w[threadIdx.x >> 5]);
     flush_acc(a, acc, nxt, !SSSP, s_stat);
+}
+
+// End of superstep t (one thread, once every relax of the superstep is
+// complete): counts the next frontier (cnt[b] = its vertices of out-degree bin
+// b), stops at convergence, max_iters or the guard, picks push or pull for
+// superstep t+1 and clears the counters of the slot superstep t+2 fills.  The
+// control block is accessed through volatile so that values other threads of
+// the same kernel wrote with atomics are read from L2.  Returns done.
+template <bool SSSP>
+__device__ uint32_t finish_superstep(const TravArgs& a, TravCtlDev* cdp, uint32_t t, const uint32_t* cnt) {
+    volatile TravCtlDev* cd = cdp;
+    volatile TravCtl* c = &cd->c;
+    const int nxt = (int)((t + 1u) % 3u);
+    const unsigned long long active = (unsigned long long)cnt[0] + cnt[1] + cnt[2] + cnt[3];
+    const uint32_t iters = t + 1u;
+    if (c->dir == 0) c->pushes = c->pushes + 1u;
+    else c->pulls = c->pulls + 1u;
+    uint32_t done = (active == 0ull) ? 1u : 0u;
+    if (cd->max_iters >= 0 && iters >= (uint32_t)cd->max_iters) done = 1u;
+    // Min-semiring traversals with non-negative weights settle within n supersteps
+    // (shortest paths have at most n-1 edges) plus one that finds no change.
+    if (!done && (unsigned long long)iters >= (unsigned long long)a.n + 2ull) {
+        done = 1u;
+        c->guard_hit = 1u;
+    }
+    if (!done) {
+        uint32_t dir = c->dir;
+        const double mf = (double)c->medges[nxt];
+        if (cd->dir_mode == 1) dir = 0;
+        else if (cd->dir_mode == 2) dir = 1;
+        else if (!SSSP) {
+            if (dir == 0) dir = (mf > (double)c->unvisited_in_edges / cd->alpha) ? 1u : 0u;
+            else dir = ((double)active < (double)a.n / cd->beta) ? 0u : 1u;
+        } else {
+            dir = (mf > cd->sssp_frac * (double)a.m) ? 1u : 0u;
+        }
+        c->dir = dir;
+        const int clr = (int)((t + 2u) % 3u);
+        for (int b = 0; b < 4; ++b) c->count[clr][b] = 0u;
+        c->medges[clr] = 0ull;
+    }
+    c->iter = iters;
+    c->iters_done = iters;
+    c->done = done;
+    return done;
 }
 
 template <bool SSSP>
@@ -959,38 +1029,219 @@ __global__ void __launch_bounds__(kThreads) trav_finalize(TravArgs a) {
     // ---- last CTA: termination and direction for superstep t+1 ----
     __threadfence();
     c->ticket = 0;
-    const unsigned long long active = (unsigned long long)s_cnt[0] + s_cnt[1] + s_cnt[2] + s_cnt[3];
-    const uint32_t iters = t + 1u;
-    if (c->dir == 0) c->pushes++;
-    else c->pulls++;
-    uint32_t done = (active == 0ull) ? 1u : 0u;
-    if (cd->max_iters >= 0 && iters >= (uint32_t)cd->max_iters) done = 1u;
-    // Min-semiring traversals with non-negative weights settle within n supersteps
-    // (shortest paths have at most n-1 edges) plus one that finds no change.
-    if (!done && (unsigned long long)iters >= (unsigned long long)a.n + 2ull) {
-        done = 1u;
-        c->guard_hit = 1u;
-    }
-    if (!done) {
-        uint32_t dir = c->dir;
-        const double mf = (double)c->medges[nxt];
-        if (cd->dir_mode == 1) dir = 0;
-        else if (cd->dir_mode == 2) dir = 1;
-        else if (!SSSP) {
-            if (dir == 0) dir = (mf > (double)c->unvisited_in_edges / cd->alpha) ? 1u : 0u;
-            else dir = ((double)active < (double)a.n / cd->beta) ? 0u : 1u;
-        } else {
-            dir = (mf > cd->sssp_frac * (double)a.m) ? 1u : 0u;
-        }
-        c->dir = dir;
-        const int clr = (int)((t + 2u) % 3u);
-        for (int b = 0; b < 4; ++b) c->count[clr][b] = 0u;
-        c->medges[clr] = 0ull;
-    }
-    c->iter = iters;
-    c->iters_done = iters;
-    c->done = done;
+    const uint32_t done = finish_superstep<SSSP>(a, cd, t, s_cnt);
     if (a.use_cond) cudaGraphSetConditional(a.cond, done ? 0u : 1u);
+}
+
+// ---------------------------------------------------------------- small supersteps
+// Supersteps whose frontier is tiny cost little work but a full superstep's
+// launches (push, pull, finalize, each with hundreds of CTAs, plus the loop's
+// own overhead).  trav_small, the first node of every loop iteration, runs such
+// supersteps itself, one after another, in one CTA: while the next superstep is
+// a push over at most kSmallItems work items and kSmallEdges out-edges, it does
+// exactly what push + finalize would (same relaxation, same queues, counters,
+// bitvectors and messages, same termination and direction rule), then returns
+// and the other nodes run the first superstep it did not take (or nothing, once
+// done).  All reads of data this kernel itself changed go to L2 (ld.global.cg
+// or volatile), since the SM's L1 is not coherent with atomics.
+constexpr int kSmallThreads = 1024;
+constexpr uint32_t kSmallItems = 2 * kSmallThreads;  // frontier vertices / large-vertex chunks
+constexpr uint32_t kSmallEdges = 16384;              // frontier out-edges
+constexpr uint32_t kSmallClear = 65536;              // SSSP: messages of the previous frontier to clear
+constexpr uint32_t kSmallList = 2048;                // vertices whose frontier bit a superstep set, kept to clear
+constexpr int64_t kSmallFullClearWords = 1 << 19;    // largest bitvector the CTA clears whole (2 MB)
+
+template <bool SSSP>
+__global__ void __launch_bounds__(kSmallThreads, 1) trav_small(TravArgs a) {
+    __shared__ uint32_t s_ex[kSmallItems + 1];  // exclusive prefix of the items' edge counts
+    __shared__ int32_t s_beg[kSmallItems];      // first out-edge of each item
+    __shared__ uint32_t s_du[kSmallItems];      // SSSP: message of each item's vertex
+    // vertices whose bit in bv[slot] superstep t set, by t's parity (superstep
+    // t+2 clears exactly those words); a count above kSmallList: not known
+    __shared__ int32_t s_list[2][kSmallList];
+    __shared__ uint32_t s_nlist[2];
+    __shared__ uint32_t s_wsum[kSmallThreads / 32];
+    __shared__ unsigned long long s_stat[5];
+    __shared__ uint32_t s_go, s_t, s_total, s_cnt[4];
+    TravCtlDev* cd = a.ctl;
+    TravCtl* c = &cd->c;
+    volatile TravCtl* vc = c;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) {
+        vc->loops = vc->loops + 1u;
+        s_nlist[0] = s_nlist[1] = kSmallList + 1u;  // bits set by the launches before: clear whole
+    }
+    for (;;) {
+        if (tid == 0) {
+            uint32_t go = 0u;
+            const uint32_t t = vc->iter;
+            if (!vc->done && vc->dir == 0u) {
+                const int cur = (int)(t % 3u), clr = (int)((t + 2u) % 3u);
+                const uint32_t items = vc->count[cur][1] + vc->count[cur][2] + vc->count[cur][3];
+                const uint32_t prev = vc->count[clr][1] + vc->count[clr][2] + vc->count[clr][3];
+                const bool listed = s_nlist[t & 1u] <= kSmallList;
+                go = (items <= kSmallItems && vc->medges[cur] <= (unsigned long long)kSmallEdges &&
+                      (!SSSP || prev <= kSmallClear) && (listed || a.nwords <= kSmallFullClearWords))
+                         ? 1u
+                         : 0u;
+            }
+            s_go = go;
+            s_t = t;
+        }
+        if (tid < 5) s_stat[tid] = 0ull;
+        __syncthreads();
+        if (!s_go) return;
+        const uint32_t t = s_t;
+        const int cur = (int)(t % 3u), nxt = (int)((t + 1u) % 3u), clr = (int)((t + 2u) % 3u);
+        const uint32_t par = t & 1u;
+
+        // ---- the relax prologue: clear the frontier bits superstep t-2 set and
+        // (SSSP) the messages of superstep t-1
+        uint32_t* bz = a.bv[clr];
+        const uint32_t nl = s_nlist[par];
+        if (nl <= kSmallList) {
+            for (uint32_t i = tid; i < nl; i += kSmallThreads) bz[s_list[par][i] >> 5] = 0u;
+        } else {
+            const int64_t n4 = a.nwords >> 2;
+            for (int64_t i = tid; i < n4; i += kSmallThreads) reinterpret_cast<uint4*>(bz)[i] = make_uint4(0, 0, 0, 0);
+            for (int64_t i = (n4 << 2) + tid; i < a.nwords; i += kSmallThreads) bz[i] = 0u;
+        }
+        if (SSSP) {
+            const uint32_t p1 = __ldcg(&c->count[clr][1]), p2 = __ldcg(&c->count[clr][2]),
+                           p3 = __ldcg(&c->count[clr][3]);
+            uint32_t* mz = a.msg[(t + 1u) & 1u];
+            for (uint32_t i = tid; i < p1 + p2 + p3; i += kSmallThreads) {
+                int32_t v;
+                if (i < p1) v = __ldcg(a.q[clr][1] + i);
+                else if (i < p1 + p2) v = __ldcg(a.q[clr][2] + (i - p1));
+                else v = __ldcg(&a.qc[clr][i - p1 - p2].x);
+                mz[a.rank[v]] = kInf;
+            }
+        }
+
+        // ---- the frontier's work items, their edge ranges and messages
+        const uint32_t n1 = __ldcg(&c->count[cur][1]), n2 = __ldcg(&c->count[cur][2]),
+                       n3 = __ldcg(&c->count[cur][3]);
+        const uint32_t ni = n1 + n2 + n3;
+        const uint32_t* __restrict__ msgc = a.msg[t & 1u];
+        Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, nullptr};
+        uint32_t d2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t i = 2u * (uint32_t)tid + (uint32_t)h;
+            d2[h] = 0u;
+            if (i < ni) {
+                int32_t u, beg, end;
+                if (i < n1 + n2) {
+                    u = i < n1 ? __ldcg(a.q[cur][1] + i) : __ldcg(a.q[cur][2] + (i - n1));
+                    beg = a.row_ptr[u];
+                    end = a.row_ptr[u + 1];
+                    acc.verts++;
+                } else {
+                    const int2 it = __ldcg(&a.qc[cur][i - n1 - n2]);
+                    u = it.x;
+                    beg = a.row_ptr[u] + it.y * kChunk;
+                    end = min(a.row_ptr[u + 1], beg + kChunk);
+                    if (it.y == 0) acc.verts++;
+                }
+                s_beg[i] = beg;
+                s_du[i] = SSSP ? __ldcg(msgc + a.rank[u]) : 0u;
+                d2[h] = (uint32_t)(end - beg);
+            }
+        }
+        // exclusive scan of the edge counts over the items (two per thread)
+        const uint32_t x = d2[0] + d2[1];
+        const uint32_t incl = warp_incl_scan(x);
+        if (lane == 31) s_wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const uint32_t w = s_wsum[lane];
+            s_wsum[lane] = warp_incl_scan(w) - w;
+        }
+        __syncthreads();
+        const uint32_t ex = s_wsum[wid] + incl - x;
+        if (2u * tid < ni) s_ex[2 * tid] = ex;
+        if (2u * tid + 1u < ni) s_ex[2 * tid + 1] = ex + d2[0];
+        if (tid == kSmallThreads - 1) {
+            s_total = ex + x;
+            s_ex[ni] = ex + x;
+        }
+        if (tid == 0) s_nlist[par] = 0u;
+        __syncthreads();
+
+        // ---- relax: 8 consecutive edges per thread, as push_phase does
+        const uint32_t total = s_total;
+        for (uint32_t base = 0; base < total; base += kSmallThreads * kEPT) {
+            const uint32_t j0 = base + (uint32_t)tid * kEPT;
+            int32_t v[kEPT];
+            uint32_t wt[kEPT], du[kEPT];
+            uint32_t ok = 0u;
+#pragma unroll
+            for (int k = 0; k < kEPT; ++k) {
+                v[k] = 0;
+                wt[k] = 0u;
+                du[k] = 0u;
+            }
+            if (j0 < total) {
+                int32_t lo = 0, hi = (int32_t)ni - 1;  // the item holding edge j0: last with s_ex <= j0
+                while (lo < hi) {
+                    const int32_t mid = (lo + hi + 1) >> 1;
+                    if (s_ex[mid] <= j0) lo = mid;
+                    else hi = mid - 1;
+                }
+                int32_t o = lo;
+#pragma unroll
+                for (int k = 0; k < kEPT; ++k) {
+                    const uint32_t j = j0 + (uint32_t)k;
+                    if (j < total) {
+                        while (j >= s_ex[o + 1]) ++o;
+                        const int32_t e = s_beg[o] + (int32_t)(j - s_ex[o]);
+                        v[k] = a.col[e];
+                        if (SSSP) wt[k] = a.w[e];
+                        du[k] = s_du[o];
+                        ok |= 1u << k;
+                    }
+                }
+            }
+            bool want[kEPT];
+            push_relax8<SSSP>(a, v, wt, du, ok, t, nxt, want);
+            acc.scanned += (unsigned)__popc(ok);
+#pragma unroll
+            for (int k = 0; k < kEPT; ++k)
+                if (want[k]) {
+                    const uint32_t pos = atomicAdd(&s_nlist[par], 1u);
+                    if (pos < kSmallList) s_list[par][pos] = v[k];
+                }
+            enqueue_batch<!SSSP>(a, want, v, nxt, acc);
+        }
+        flush_acc(a, acc, nxt, !SSSP, s_stat);
+        __syncthreads();
+
+        // ---- finalize: messages of superstep t+1, then termination and direction
+        if (tid < 4) s_cnt[tid] = __ldcg(&c->count[nxt][tid]);
+        __syncthreads();
+        if (SSSP) {
+            const uint32_t m1 = s_cnt[1], m2 = s_cnt[2], m3 = s_cnt[3];
+            uint32_t* ms = a.msg[(t + 1u) & 1u];
+            for (uint32_t i = tid; i < m1 + m2 + m3; i += kSmallThreads) {
+                int32_t v;
+                if (i < m1) v = __ldcg(a.q[nxt][1] + i);
+                else if (i < m1 + m2) v = __ldcg(a.q[nxt][2] + (i - m1));
+                else {
+                    const int2 it = __ldcg(&a.qc[nxt][i - m1 - m2]);
+                    if (it.y != 0) continue;
+                    v = it.x;
+                }
+                ms[a.rank[v]] = __ldcg(a.dist + v);
+            }
+        }
+        if (tid == 0) {
+            __threadfence();  // this thread's statistics atomics land before the counters are read
+            const uint32_t done = finish_superstep<SSSP>(a, cd, t, s_cnt);
+            if (done && a.use_cond) cudaGraphSetConditional(a.cond, 0u);
+        }
+        __syncthreads();
+    }
 }
 
 // Run parameters of the control block; `fresh` also sets the start-of-run
@@ -1127,6 +1378,8 @@ TravArgs make_args(gm_graph* g) {
     a.out_deg = as<int32_t>(g->out_deg);
     a.in_deg = as<int32_t>(g->in_deg);
     a.out_bin = as<uint8_t>(g->out_bin);
+    a.bin_small = g->tune.bin_small;
+    a.bin_large = g->tune.bin_large;
     a.in_list = as<int32_t>(g->in_list);
     a.in_s0 = g->in_list_count[0];
     a.in_s1 = g->in_list_count[1];
@@ -1261,12 +1514,16 @@ gm_status build_loop_graph(gm_graph* g, bool sssp) {
     a.use_cond = 1;
     void* kargs[] = {&a};
     cudaKernelNodeParams kp = {};
+    kp.func = sssp ? (void*)trav_small<true> : (void*)trav_small<false>;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(kSmallThreads);
+    kp.kernelParams = kargs;
+    cudaGraphNode_t ns, n0, n1, n2;
+    e = cudaGraphAddKernelNode(&ns, body, nullptr, 0, &kp);
     kp.func = sssp ? (void*)trav_push<true> : (void*)trav_push<false>;
     kp.gridDim = dim3((unsigned)push_grid());
     kp.blockDim = dim3(kThreads);
-    kp.kernelParams = kargs;
-    cudaGraphNode_t n0, n1, n2;
-    e = cudaGraphAddKernelNode(&n0, body, nullptr, 0, &kp);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n0, body, &ns, 1, &kp);
     cudaGraphNode_t n1b;
     if (e == cudaSuccess) {
         kp.func = !sssp ? (void*)trav_pull_bu : a.cw8 ? (void*)trav_pull_a<1> : (void*)trav_pull_a<4>;
@@ -1443,7 +1700,7 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
     }
     GM_CUDA_TRY(cudaMemcpyAsync(hp, g->ctl_buf.p, sizeof(TravCtlDev), cudaMemcpyDeviceToHost, s));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
-    if (!host_loop) g_launches += (sssp ? 4ull : 3ull) * hp->c.iters_done;
+    if (!host_loop) g_launches += (sssp ? 5ull : 4ull) * hp->c.loops;
     g->stats.supersteps = (int32_t)hp->c.iters_done;
     g->stats.pushes = (int32_t)hp->c.pushes;
     g->stats.pulls = (int32_t)hp->c.pulls;

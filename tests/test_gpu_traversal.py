@@ -244,3 +244,45 @@ def test_autotune_keeps_results(gm):
         got, it = _run(gm, g, kind, [srcs[2]])
         ref, rit = ref_fn([srcs[2]])
         assert np.array_equal(got, ref) and it == rit
+
+
+def _stats(gm, g):
+    return [g.scalar(x) for x in (gm.GM_SCALAR_SUPERSTEPS, gm.GM_SCALAR_PUSH_STEPS, gm.GM_SCALAR_PULL_STEPS,
+                                  gm.GM_SCALAR_SCANNED_EDGES, gm.GM_SCALAR_PROCESSED_VERTICES)]
+
+
+@pytest.mark.parametrize("kind", ["bfs", "sssp"])
+def test_small_supersteps_match_host_loop(gm, kind):
+    """The device loop runs supersteps with tiny frontiers in one CTA (trav_small),
+    the host loop never does: properties, superstep counts, push/pull counts,
+    edges scanned and vertices processed agree, with and without max_iters, on
+    an RMAT graph (small heads and tails around large supersteps), a long path
+    (every superstep small) and a graph whose frontier has large-degree hubs."""
+    k = gm.GM_BFS if kind == "bfs" else gm.GM_SSSP
+    n, s, d, w = rmat_case(14, weighted=True)
+    n2 = 3000
+    ps, pd = np.arange(n2 - 1, dtype=np.int32), np.arange(1, n2, dtype=np.int32)
+    hs = np.concatenate([np.zeros(5000, np.int32), np.arange(1, 5001, dtype=np.int32)])
+    hd = np.concatenate([np.arange(1, 5001, dtype=np.int32), (np.arange(5000, dtype=np.int32) * 7 + 3) % 5001])
+    cases = [(n, s, d, w, list(synth.pick_sources(n, s, d, 4, seed=31))),
+             (n2, ps, pd, (ps % 7 + 1).astype(np.uint32), [0, 1500]),
+             (5001, hs, hd, ((hs + hd) % 11 + 1).astype(np.uint32), [0, 17])]
+    for nn, ss, dd, ww, srcs in cases:
+        g = gm.Graph(nn, ss, dd, ww)
+        og = oracle.Graph(nn, ss, dd, ww)
+        for src in srcs:
+            for max_iters in (-1, 1, 2, 5):
+                res = []
+                for loop_mode in (0, 1):
+                    g.set_option(gm.GM_OPT_LOOP_MODE, loop_mode)
+                    l0 = gm.kernel_launch_count()
+                    got, it = _run(gm, g, k, [int(src)], max_iters)
+                    res.append((got, it, _stats(gm, g)))
+                    if nn == n2 and loop_mode == 0 and max_iters == -1:  # one loop iteration ran them all
+                        assert it > 1000 and gm.kernel_launch_count() - l0 < 100  # vs about 4 per superstep
+                assert np.array_equal(res[0][0], res[1][0]) and res[0][1] == res[1][1]
+                assert res[0][2] == res[1][2], (nn, src, max_iters, res[0][2], res[1][2])
+                if max_iters == -1:
+                    ref, rit = (og.bfs if kind == "bfs" else og.sssp)([int(src)])
+                    assert np.array_equal(res[0][0], ref) and res[0][1] == rit
+        g.close()
