@@ -224,6 +224,7 @@ gm_status gm_set_vertex_state(gm_graph* g, const void* src, int64_t bytes, int s
         set_error("gm_set_vertex_state: expected %lld bytes", (long long)need);
         return GM_ERR_INVALID_ARG;
     }
+    g->reached_valid = false;  // a property set by the caller: count reached vertices from the state
     if (need > 0)
         GM_CUDA_TRY(cudaMemcpyAsync(g->state.p, src, (size_t)need,
                                     src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));

@@ -84,6 +84,7 @@ struct TravCtl {
     uint32_t guard_hit;           // the loop passed n + 1 supersteps (impossible for valid runs)
     uint32_t stage_timeouts;      // pull CTAs whose shared-memory staging copy did not complete in time
     uint32_t loops;               // iterations of the device loop (for the launch count)
+    unsigned long long reached;   // out-degrees of the vertices whose property became finite since the reset
 };
 
 // Options and tuning knobs of a graph handle.
@@ -151,6 +152,13 @@ struct gm_graph {
     int64_t zero_in_count = 0;
     gm::Tuning tune;
     gm::RunStats stats;
+    // GM_SCALAR_REACHED_EDGES kept up to date by the traversal itself: the sum of
+    // out-degrees of vertices with a finite property, valid when no change since
+    // the last fold is unaccounted (seeds pending in the control block, a state
+    // written by the caller)
+    int64_t reached_total = 0;
+    bool reached_valid = false;
+    bool reached_pending = false;
 
     // program state
     int32_t kind = -1;

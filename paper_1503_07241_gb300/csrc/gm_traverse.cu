@@ -92,6 +92,7 @@ struct WarpQ {
 // Per-thread statistics (reduced per CTA once per kernel) and the warp's stage.
 struct Acc {
     unsigned long long scanned, verts, medges, unvis, n0;
+    unsigned long long reached;  // out-degrees of vertices whose property went from infinity to finite
     WarpQ* wq;  // nullptr: enqueue straight to the global queue
 };
 
@@ -175,7 +176,10 @@ __device__ __forceinline__ void enqueue_batch_pre(const TravArgs& a, const bool 
             const uint32_t b = vb[k];
             const uint32_t d = vd[k];
             acc.medges += d;
-            if (BFS) acc.unvis += vin[k];
+            if (BFS) {
+                acc.unvis += vin[k];
+                acc.reached += d;  // a BFS vertex joins a frontier once: when first reached
+            }
             bin[k] = b;
             nch[k] = b == 3u ? (d + kChunk - 1u) / kChunk : 1u;
             cnt[b] += nch[k];
@@ -247,7 +251,7 @@ __device__ __forceinline__ void enqueue_batch(const TravArgs& a, const bool (&wa
 template <bool SSSP>
 __device__ __forceinline__ void push_relax8(const TravArgs& a, const int32_t (&v)[kEPT], const uint32_t (&wt)[kEPT],
                                             const uint32_t (&du)[kEPT], uint32_t ok, uint32_t t, int nxt,
-                                            bool (&want)[kEPT]) {
+                                            bool (&want)[kEPT], Acc& acc) {
     uint32_t curd[kEPT];
 #pragma unroll
     for (int k = 0; k < kEPT; ++k) curd[k] = ((ok >> k) & 1u) ? a.dist[v[k]] : 0u;
@@ -275,6 +279,7 @@ __device__ __forceinline__ void push_relax8(const TravArgs& a, const int32_t (&v
 #pragma unroll
         for (int k = 0; k < kEPT; ++k) {
             tr[k] = tr[k] && nd[k] < old[k];
+            if (tr[k] && old[k] == kInf) acc.reached += (uint32_t)__ldg(a.out_deg + v[k]);
             prev[k] = tr[k] ? atomicOr(&a.bv[nxt][v[k] >> 5], 1u << (v[k] & 31)) : 0u;
         }
 #pragma unroll
@@ -303,7 +308,7 @@ __device__ __forceinline__ void push_contig(const TravArgs& a, int32_t e0, int32
         dv[k] = du;
     }
     bool want[kEPT];
-    push_relax8<SSSP>(a, v, wt, dv, ok, t, nxt, want);
+    push_relax8<SSSP>(a, v, wt, dv, ok, t, nxt, want, acc);
     acc.scanned += (unsigned)__popc(ok);
     enqueue_batch<!SSSP>(a, want, v, nxt, acc);
 }
@@ -393,7 +398,7 @@ __device__ void push_phase(const TravArgs& a, uint32_t t, int cur, int nxt, Acc&
                 }
             }
             bool want[kEPT];
-            push_relax8<SSSP>(a, v, wt, dv, ok, t, nxt, want);
+            push_relax8<SSSP>(a, v, wt, dv, ok, t, nxt, want, acc);
             acc.scanned += (unsigned)__popc(ok);
             enqueue_batch<!SSSP>(a, want, v, nxt, acc);
         }
@@ -432,9 +437,9 @@ __device__ __forceinline__ void flush_acc(const TravArgs& a, Acc& acc, int nxt, 
         warp_flush(a, acc.wq, 1u, nxt);
         warp_flush(a, acc.wq, 2u, nxt);
     }
-    unsigned long long vals[5] = {acc.scanned, acc.verts, acc.medges, acc.unvis, acc.n0};
+    unsigned long long vals[6] = {acc.scanned, acc.verts, acc.medges, acc.unvis, acc.n0, acc.reached};
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < 6; ++i) {
         vals[i] = warp_sum_u64(vals[i]);
         if ((threadIdx.x & 31) == 0 && vals[i]) atomicAdd(&s_stat[i], vals[i]);
     }
@@ -445,6 +450,7 @@ __device__ __forceinline__ void flush_acc(const TravArgs& a, Acc& acc, int nxt, 
         if (s_stat[2]) atomicAdd(&c->medges[nxt], s_stat[2]);
         if (bfs && s_stat[3]) atomicAdd(&c->unvisited_in_edges, 0ull - s_stat[3]);
         if (s_stat[4]) atomicAdd(&c->count[nxt][0], (uint32_t)s_stat[4]);
+        if (s_stat[5]) atomicAdd(&c->reached, s_stat[5]);
     }
 }
 
@@ -745,11 +751,11 @@ __global__ void __launch_bounds__(kThreads, 4) trav_pull_bu(TravArgs a) {
     const int cur = (int)(t % 3u), nxt = (int)((t + 1u) % 3u), clr = (int)((t + 2u) % 3u);
     relax_prologue<false>(a, &cd->c, t, clr);
     __shared__ WarpQ s_q[kWarps];
-    __shared__ unsigned long long s_stat[5];
-    if (threadIdx.x < 5) s_stat[threadIdx.x] = 0ull;
+    __shared__ unsigned long long s_stat[6];
+    if (threadIdx.x < 6) s_stat[threadIdx.x] = 0ull;
     if ((threadIdx.x & 31) < 2) s_q[threadIdx.x >> 5].n[threadIdx.x & 31] = 0u;
     __syncthreads();
-    Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, &s_q[threadIdx.x >> 5]};
+    Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, &s_q[threadIdx.x >> 5]};
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
@@ -854,11 +860,11 @@ __global__ void __launch_bounds__(kThreads, 4) trav_pull_b(TravArgs a) {
     const uint32_t t = cd->c.iter;
     const int nxt = (int)((t + 1u) % 3u);
     __shared__ WarpQ s_q[kWarps];
-    __shared__ unsigned long long s_stat[5];
-    if (threadIdx.x < 5) s_stat[threadIdx.x] = 0ull;
+    __shared__ unsigned long long s_stat[6];
+    if (threadIdx.x < 6) s_stat[threadIdx.x] = 0ull;
     if ((threadIdx.x & 31) < 2) s_q[threadIdx.x >> 5].n[threadIdx.x & 31] = 0u;
     __syncthreads();
-    Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, &s_q[threadIdx.x >> 5]};
+    Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, &s_q[threadIdx.x >> 5]};
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
@@ -909,6 +915,7 @@ __global__ void __launch_bounds__(kThreads, 4) trav_pull_b(TravArgs a) {
                 y[base + 32 * k + lane] = kInf;
                 acc.verts++;
                 if (bc[k] < dv[k]) {
+                    if (dv[k] == kInf) acc.reached += vd[k];
                     a.dist[vc[k]] = bc[k];
                     msgn[rc[k]] = bc[k];  // superstep t+1's message (finalize skips pulls)
                     wa[k] = true;
@@ -933,11 +940,11 @@ __global__ void __launch_bounds__(kThreads) trav_push(TravArgs a) {
     relax_prologue<SSSP>(a, &cd->c, t, clr);
     __shared__ uint32_t s_w[kWarps][100];
     __shared__ WarpQ s_q[kWarps];
-    __shared__ unsigned long long s_stat[5];
-    if (threadIdx.x < 5) s_stat[threadIdx.x] = 0ull;
+    __shared__ unsigned long long s_stat[6];
+    if (threadIdx.x < 6) s_stat[threadIdx.x] = 0ull;
     if ((threadIdx.x & 31) < 2) s_q[threadIdx.x >> 5].n[threadIdx.x & 31] = 0u;
     __syncthreads();
-    Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, &s_q[threadIdx.x >> 5]};
+    Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, &s_q[threadIdx.x >> 5]};
     push_phase<SSSP>(a, t, cur, nxt, acc, s_w[threadIdx.x >> 5]);
     flush_acc(a, acc, nxt, !SSSP, s_stat);
 }
@@ -1061,7 +1068,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) trav_small(TravArgs a) {
     __shared__ int32_t s_list[2][kSmallList];
     __shared__ uint32_t s_nlist[2];
     __shared__ uint32_t s_wsum[kSmallThreads / 32];
-    __shared__ unsigned long long s_stat[5];
+    __shared__ unsigned long long s_stat[6];
     __shared__ uint32_t s_go, s_t, s_total, s_cnt[4];
     TravCtlDev* cd = a.ctl;
     TravCtl* c = &cd->c;
@@ -1088,7 +1095,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) trav_small(TravArgs a) {
             s_go = go;
             s_t = t;
         }
-        if (tid < 5) s_stat[tid] = 0ull;
+        if (tid < 6) s_stat[tid] = 0ull;
         __syncthreads();
         if (!s_go) return;
         const uint32_t t = s_t;
@@ -1124,7 +1131,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) trav_small(TravArgs a) {
                        n3 = __ldcg(&c->count[cur][3]);
         const uint32_t ni = n1 + n2 + n3;
         const uint32_t* __restrict__ msgc = a.msg[t & 1u];
-        Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, nullptr};
+        Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, nullptr};
         uint32_t d2[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -1204,7 +1211,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) trav_small(TravArgs a) {
                 }
             }
             bool want[kEPT];
-            push_relax8<SSSP>(a, v, wt, du, ok, t, nxt, want);
+            push_relax8<SSSP>(a, v, wt, du, ok, t, nxt, want, acc);
             acc.scanned += (unsigned)__popc(ok);
 #pragma unroll
             for (int k = 0; k < kEPT; ++k)
@@ -1262,26 +1269,29 @@ __global__ void seed_frontier(TravArgs a, const int32_t* __restrict__ verts, int
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool want = false;
     int32_t v = 0;
+    uint32_t first = 0u;  // out-degree of a source reached here for the first time
     if (i < count) v = verts[i];
     if (i < count && (v < 0 || v >= a.n)) {
         atomicAdd(&a.ctl->c.bad_ids, 1u);
         v = 0;
     } else if (i < count) {
-        a.dist[v] = 0u;
+        if (atomicExch(&a.dist[v], 0u) == kInf) first = (uint32_t)a.out_deg[v];
         if (!bfs) a.msg[0][a.rank[v]] = 0u;
         const uint32_t bit = 1u << (v & 31);
         want = (atomicOr(&a.bv[0][v >> 5], bit) & bit) == 0u;
     }
-    Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, nullptr};
+    Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, nullptr};
     bool wa[kEPT] = {want, false, false, false, false, false, false, false};
     int32_t va[kEPT] = {v, 0, 0, 0, 0, 0, 0, 0};
     if (bfs) enqueue_batch<true>(a, wa, va, 0, acc);
     else enqueue_batch<false>(a, wa, va, 0, acc);
     acc.medges = warp_sum_u64(acc.medges);
     acc.unvis = warp_sum_u64(acc.unvis);
+    const unsigned long long reached = warp_sum_u64(first);
     if ((threadIdx.x & 31) == 0) {
         if (acc.medges) atomicAdd(&a.ctl->c.medges[0], acc.medges);
         if (bfs && acc.unvis) atomicAdd(&a.ctl->c.unvisited_in_edges, 0ull - acc.unvis);
+        if (reached) atomicAdd(&a.ctl->c.reached, reached);
     }
 }
 
@@ -1289,21 +1299,24 @@ __global__ void seed_all(TravArgs a, int bfs) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool want = i < a.n;
     const int32_t v = want ? (int32_t)i : 0;
+    uint32_t first = 0u;
     if (want) {
-        a.dist[v] = 0u;
+        if (atomicExch(&a.dist[v], 0u) == kInf) first = (uint32_t)a.out_deg[v];
         if (!bfs) a.msg[0][a.rank[v]] = 0u;
         atomicOr(&a.bv[0][v >> 5], 1u << (v & 31));
     }
-    Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, nullptr};
+    Acc acc = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, nullptr};
     bool wa[kEPT] = {want, false, false, false, false, false, false, false};
     int32_t va[kEPT] = {v, 0, 0, 0, 0, 0, 0, 0};
     if (bfs) enqueue_batch<true>(a, wa, va, 0, acc);
     else enqueue_batch<false>(a, wa, va, 0, acc);
     acc.medges = warp_sum_u64(acc.medges);
     acc.unvis = warp_sum_u64(acc.unvis);
+    const unsigned long long reached = warp_sum_u64(first);
     if ((threadIdx.x & 31) == 0) {
         if (acc.medges) atomicAdd(&a.ctl->c.medges[0], acc.medges);
         if (bfs && acc.unvis) atomicAdd(&a.ctl->c.unvisited_in_edges, 0ull - acc.unvis);
+        if (reached) atomicAdd(&a.ctl->c.reached, reached);
     }
 }
 
@@ -1463,6 +1476,10 @@ int pull_b_grid() {
 // Reset the control block and the frontier before seeding.
 gm_status reset_frontier(gm_graph* g) {
     cudaStream_t s = g->stream;
+    if (g->reached_pending) {  // seeds counted in the control block that is about to be cleared
+        g->reached_valid = false;
+        g->reached_pending = false;
+    }
     TravWork w = work_layout(g);
     const int64_t n = g->n > 0 ? g->n : 1;
     const int64_t nwords = (n + 31) / 32;
@@ -1576,7 +1593,10 @@ gm_status trav_prepare(gm_graph* g) {
     LAUNCH_OK();
     // per-column pull results start at infinity; pull_b restores that after every use
     GM_CUDA_TRY(cudaMemsetAsync(work_layout(g).ycol, 0xFF, sizeof(uint32_t) * n, s));
-    return reset_frontier(g);
+    GM_TRY(reset_frontier(g));
+    g->reached_total = 0;  // every property is infinity
+    g->reached_valid = true;
+    return GM_OK;
 }
 
 // program_set between BFS and SSSP when the workspace of a traversal is already
@@ -1592,11 +1612,15 @@ gm_status trav_reuse(gm_graph* g) {
     fill_u32<<<num_sms() * 4, 256, 0, s>>>(as<uint32_t>(g->state), g->n, kInf);
     g_launches++;
     LAUNCH_OK();
-    return reset_frontier(g);
+    GM_TRY(reset_frontier(g));
+    g->reached_total = 0;
+    g->reached_valid = true;
+    return GM_OK;
 }
 
 gm_status trav_set_active(gm_graph* g, const int32_t* vertices_dev, int64_t count) {
     cudaStream_t s = g->stream;
+    g->reached_pending = true;  // the seeding kernel adds newly reached sources to the control block
     TravArgs a = make_args(g);
     const int bfs = g->kind == GM_BFS ? 1 : 0;
     if (count < 0) {
@@ -1707,6 +1731,8 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
     g->stats.scanned_edges = (int64_t)hp->c.scanned_edges;
     g->stats.processed_vertices = (int64_t)hp->c.processed_vertices;
     if (iters_done) *iters_done = (int32_t)hp->c.iters_done;
+    g->reached_total += (int64_t)hp->c.reached;  // seeds since the last reset and this run
+    g->reached_pending = false;
     const uint32_t bad = hp->c.bad_ids;
     const uint32_t guard = hp->c.guard_hit;
     const uint32_t stage_to = hp->c.stage_timeouts;
@@ -1729,6 +1755,10 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
 
 gm_status reached_edges(gm_graph* g, int64_t* out) {
     cudaStream_t s = g->stream;
+    if (g->reached_valid && !g->reached_pending) {  // kept by the traversal kernels
+        *out = g->reached_total;
+        return GM_OK;
+    }
     if (!g->reached_buf.p) GM_TRY(dev_alloc(g->reached_buf, sizeof(unsigned long long), s));
     GM_CUDA_TRY(cudaMemsetAsync(g->reached_buf.p, 0, sizeof(unsigned long long), s));
     if (g->n > 0) {
@@ -1741,6 +1771,10 @@ gm_status reached_edges(gm_graph* g, int64_t* out) {
     GM_CUDA_TRY(cudaMemcpyAsync(&h, g->reached_buf.p, sizeof(h), cudaMemcpyDeviceToHost, s));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
     *out = (int64_t)h;
+    if (!g->reached_pending) {  // counted from the state itself: the traversal keeps it from here
+        g->reached_total = (int64_t)h;
+        g->reached_valid = true;
+    }
     return GM_OK;
 }
 

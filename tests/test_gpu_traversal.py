@@ -286,3 +286,58 @@ def test_small_supersteps_match_host_loop(gm, kind):
                     ref, rit = (og.bfs if kind == "bfs" else og.sssp)([int(src)])
                     assert np.array_equal(res[0][0], ref) and res[0][1] == rit
         g.close()
+
+
+def test_reached_edges_counter(gm):
+    """GM_SCALAR_REACHED_EDGES is kept by the traversal kernels (a vertex's
+    out-degree is added when its property first becomes finite: seeding, push,
+    pull, the small-superstep kernel); it must equal the sum of out-degrees over
+    the finite properties after every call sequence: one or several sources,
+    repeated and already-reached sources, continued runs, max_iters, every
+    direction, all vertices active, program switches and a caller-written state."""
+    n, s, d, w = rmat_case(13, weighted=True)
+    g = gm.Graph(n, s, d, w)
+    od, _ = g.degrees()
+    srcs = [int(x) for x in synth.pick_sources(n, s, d, 6, seed=41)]
+
+    def expect():
+        st = g.state()
+        return int(od[st != gm.INF_U32].astype(np.int64).sum())
+
+    for kind in (gm.GM_BFS, gm.GM_SSSP):
+        for direction in DIRS:
+            g.set_option(gm.GM_OPT_DIRECTION, direction)
+            g.program_set(kind)
+            assert g.scalar(gm.GM_SCALAR_REACHED_EDGES) == 0
+            g.set_active(srcs[:1])
+            g.run(2)
+            assert g.scalar(gm.GM_SCALAR_REACHED_EDGES) == expect()
+            g.set_active(srcs[1:3] + srcs[1:2])  # a repeated source
+            g.run(-1)
+            assert g.scalar(gm.GM_SCALAR_REACHED_EDGES) == expect()
+            g.set_active(srcs[:4])  # sources already reached
+            g.run(3)
+            assert g.scalar(gm.GM_SCALAR_REACHED_EDGES) == expect()
+            g.set_active(srcs[4:5])
+            assert g.scalar(gm.GM_SCALAR_REACHED_EDGES) == expect()  # seeds pending: counted from the state
+            g.run(-1)
+            assert g.scalar(gm.GM_SCALAR_REACHED_EDGES) == expect()
+        g.set_option(gm.GM_OPT_DIRECTION, 0)
+        g.program_set(kind)
+        g.set_active(np.arange(0, n, 97, dtype=np.int32))
+        g.run(0)
+        assert g.scalar(gm.GM_SCALAR_REACHED_EDGES) == expect()
+        g.run(-1)
+        assert g.scalar(gm.GM_SCALAR_REACHED_EDGES) == expect()
+        g.program_set(kind)
+        g.set_active()  # every vertex
+        g.run(2)
+        assert g.scalar(gm.GM_SCALAR_REACHED_EDGES) == expect() == int(od.astype(np.int64).sum())
+        st = g.state()
+        st[:n // 2] = gm.INF_U32
+        g.set_state(st)
+        assert g.scalar(gm.GM_SCALAR_REACHED_EDGES) == expect()
+        g.set_active(srcs[5:6])
+        g.run(-1)
+        assert g.scalar(gm.GM_SCALAR_REACHED_EDGES) == expect()
+    g.close()
