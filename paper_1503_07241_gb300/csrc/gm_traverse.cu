@@ -21,8 +21,8 @@
 // Work decomposition for HBM bandwidth: every lane handles 8 edges per step with
 // two 16-byte streaming loads per edge array, so each warp keeps 1-2 KB of edge
 // data in flight.  Push: frontier vertices of small degree go 32 to a warp with
-// their edge lists concatenated, medium ones a warp each, large ones as 2048-edge
-// chunks, one CTA per chunk.  Pull: fixed 256-edge warp tiles over the doubly
+// their edge lists concatenated; the edges of medium vertices and of the
+// 2048-edge chunks of large ones are cut into 256-edge pieces dealt to all warps.  Pull: fixed 256-edge warp tiles over the doubly
 // compressed CSC, columns crossing tiles combined with atomics.
 //
 // BSP semantics are exact: messages come from values fixed at the start of the
@@ -40,9 +40,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kEPT = 8;                    // edges per lane per step
 constexpr int kWarpSpan = 32 * kEPT;       // 256 edges per warp step
-constexpr int kCtaSpan = kThreads * kEPT;  // 2048 edges per CTA step (== kChunk)
 constexpr uint32_t kFull = 0xffffffffu;
-static_assert(kCtaSpan == kChunk, "a large-vertex chunk is one CTA step");
 
 struct TravCtlDev {
     TravCtl c;
@@ -332,26 +330,65 @@ __device__ void push_phase(const TravArgs& a, uint32_t t, int cur, int nxt, Acc&
     const uint32_t gwarp = (blockIdx.x * kThreads + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * kThreads) >> 5;
 
-    // large: one CTA per 2048-edge chunk
-    for (uint32_t i = blockIdx.x; i < nC; i += gridDim.x) {
-        const int2 it = a.qc[cur][i];
-        const int32_t u = it.x;
-        if (threadIdx.x == 0 && it.y == 0) acc.verts++;
-        const int32_t re = a.row_ptr[u + 1];
-        const int32_t beg = a.row_ptr[u] + it.y * kChunk;
-        const int32_t end = min(re, beg + kChunk);
+    // Large chunks and medium vertices as warp pieces, dealt to every warp of the
+    // grid so that no CTA or warp is left with a long serial tail: piece p of an
+    // edge range [beg, end) is the 16-byte-aligned window
+    // [(beg & ~3) + 256 p, + 256) clipped to the range (one warp step); a range
+    // has at most kPiecesL (chunk of 2048) or pm (medium: degree < bin_large)
+    // such windows, and windows past its end are empty.
+    constexpr uint32_t kPiecesL = kChunk / kWarpSpan + 1;
+    const uint32_t pm = (uint32_t)(((int64_t)a.bin_large + 2 + kWarpSpan - 1) / kWarpSpan);
+    const uint64_t nL64 = (uint64_t)nC * kPiecesL, nMP64 = (uint64_t)nM * pm;
+    // 32-bit piece numbers (always, short of graphs with ~2^28 frontier vertices);
+    // else large chunks a CTA each and medium vertices a warp each
+    const bool pieces = pm <= 16u && nL64 + nMP64 < (1ull << 32);
+    const uint32_t nL = pieces ? (uint32_t)nL64 : 0u, nP = pieces ? (uint32_t)(nL64 + nMP64) : 0u;
+    for (uint32_t i = gwarp; i < nP; i += nwarps) {
+        int32_t u, beg, end;
+        uint32_t p;
+        bool first;
+        if (i < nL) {
+            const uint32_t c = i / kPiecesL;
+            const int2 it = a.qc[cur][c];
+            p = i - c * kPiecesL;
+            u = it.x;
+            beg = a.row_ptr[u] + it.y * kChunk;
+            end = min(a.row_ptr[u + 1], beg + kChunk);
+            first = it.y == 0 && p == 0u;
+        } else {
+            const uint32_t j = i - nL, vi = j / pm;
+            p = j - vi * pm;
+            u = a.q[cur][2][vi];
+            beg = a.row_ptr[u];
+            end = a.row_ptr[u + 1];
+            first = p == 0u;
+        }
+        const int32_t base = (beg & ~3) + (int32_t)p * kWarpSpan;
+        if (base >= end) continue;  // warp-uniform
+        if (lane == 0 && first) acc.verts++;
         const uint32_t du = SSSP ? msgc[a.rank[u]] : 0u;
-        for (int32_t base = beg & ~3; base < end; base += kCtaSpan)
-            push_contig<SSSP>(a, base + (int32_t)threadIdx.x * kEPT, beg, end, du, t, nxt, acc);
+        push_contig<SSSP>(a, base + lane * kEPT, beg, end, du, t, nxt, acc);
     }
-    // medium: one warp per vertex
-    for (uint32_t i = gwarp; i < nM; i += nwarps) {
-        const int32_t u = a.q[cur][2][i];
-        if (lane == 0) acc.verts++;
-        const int32_t beg = a.row_ptr[u], end = a.row_ptr[u + 1];
-        const uint32_t du = SSSP ? msgc[a.rank[u]] : 0u;
-        for (int32_t base = beg & ~3; base < end; base += kWarpSpan)
-            push_contig<SSSP>(a, base + lane * kEPT, beg, end, du, t, nxt, acc);
+    if (!pieces) {
+        for (uint32_t i = blockIdx.x; i < nC; i += gridDim.x) {  // large: one CTA per 2048-edge chunk
+            const int2 it = a.qc[cur][i];
+            const int32_t u = it.x;
+            if (threadIdx.x == 0 && it.y == 0) acc.verts++;
+            const int32_t beg = a.row_ptr[u] + it.y * kChunk;
+            const int32_t end = min(a.row_ptr[u + 1], beg + kChunk);
+            const uint32_t du = SSSP ? msgc[a.rank[u]] : 0u;
+            for (int32_t base = beg & ~3; base < end; base += kThreads * kEPT)
+                push_contig<SSSP>(a, base + (int32_t)threadIdx.x * kEPT, beg, end, du, t, nxt, acc);
+        }
+        // medium: one warp per vertex
+        for (uint32_t i = gwarp; i < nM; i += nwarps) {
+            const int32_t u = a.q[cur][2][i];
+            if (lane == 0) acc.verts++;
+            const int32_t beg = a.row_ptr[u], end = a.row_ptr[u + 1];
+            const uint32_t du = SSSP ? msgc[a.rank[u]] : 0u;
+            for (int32_t base = beg & ~3; base < end; base += kWarpSpan)
+                push_contig<SSSP>(a, base + lane * kEPT, beg, end, du, t, nxt, acc);
+        }
     }
     // small: 32 vertices per warp, edge lists concatenated
     int32_t* s_beg = reinterpret_cast<int32_t*>(sw);
