@@ -159,6 +159,10 @@ struct gm_graph {
     int64_t reached_total = 0;
     bool reached_valid = false;
     bool reached_pending = false;
+    // traversal workspace already in its reset state (bitvectors clear, control
+    // block fresh; msg_clean: the SSSP message arrays all infinity)
+    bool frontier_clean = false;
+    bool msg_clean = false;
 
     // program state
     int32_t kind = -1;

@@ -1528,6 +1528,8 @@ gm_status reset_frontier(gm_graph* g) {
                                (float)g->tune.beta, (float)g->tune.sssp_pull_frac, (unsigned long long)g->m, 1);
     g_launches++;
     LAUNCH_OK();
+    g->frontier_clean = true;
+    if (g->kind == GM_SSSP) g->msg_clean = true;
     return GM_OK;
 }
 
@@ -1624,6 +1626,7 @@ gm_status trav_prepare(gm_graph* g) {
     work_layout(g, &wb);
     GM_TRY(dev_alloc(g->work, wb, s));
     g->work_bytes = (int64_t)wb;
+    g->frontier_clean = g->msg_clean = false;
     GM_TRY(dev_alloc(g->ctl_buf, sizeof(TravCtlDev), s));
     fill_u32<<<num_sms() * 4, 256, 0, s>>>(as<uint32_t>(g->state), g->n, kInf);
     g_launches++;
@@ -1649,7 +1652,9 @@ gm_status trav_reuse(gm_graph* g) {
     fill_u32<<<num_sms() * 4, 256, 0, s>>>(as<uint32_t>(g->state), g->n, kInf);
     g_launches++;
     LAUNCH_OK();
-    GM_TRY(reset_frontier(g));
+    // gm_run leaves the frontier reset: no second reset unless seeds were set
+    // since or the SSSP messages were last used (or never cleared)
+    if (!g->frontier_clean || (g->kind == GM_SSSP && !g->msg_clean)) GM_TRY(reset_frontier(g));
     g->reached_total = 0;
     g->reached_valid = true;
     return GM_OK;
@@ -1657,6 +1662,8 @@ gm_status trav_reuse(gm_graph* g) {
 
 gm_status trav_set_active(gm_graph* g, const int32_t* vertices_dev, int64_t count) {
     cudaStream_t s = g->stream;
+    g->frontier_clean = false;
+    if (g->kind == GM_SSSP) g->msg_clean = false;
     g->reached_pending = true;  // the seeding kernel adds newly reached sources to the control block
     TravArgs a = make_args(g);
     const int bfs = g->kind == GM_BFS ? 1 : 0;
@@ -1678,6 +1685,8 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
     cudaStream_t s = g->stream;
     const bool sssp = g->kind == GM_SSSP;
     g->stats = RunStats{};
+    g->frontier_clean = false;
+    if (sssp) g->msg_clean = false;
     if (max_iters == 0) {
         if (iters_done) *iters_done = 0;
         return reset_frontier(g);
