@@ -1494,7 +1494,9 @@ int pull_bu_grid() {
     return blocks;
 }
 
-int finalize_grid() { return 2 * num_sms(); }
+// SSSP's finalize writes the next messages after a push (a grid-stride loop);
+// BFS's only elects the last CTA, so one CTA is enough.
+int finalize_grid(bool sssp) { return sssp ? 2 * num_sms() : 1; }
 
 int pull_b_grid() {
     static int blocks = grid_for(trav_pull_b);
@@ -1574,13 +1576,13 @@ gm_status build_loop_graph(gm_graph* g, bool sssp) {
     kp.gridDim = dim3(1);
     kp.blockDim = dim3(kSmallThreads);
     kp.kernelParams = kargs;
-    cudaGraphNode_t ns, n0, n1, n2;
+    cudaGraphNode_t ns = nullptr, n0 = nullptr, n1 = nullptr, n2 = nullptr;
     e = cudaGraphAddKernelNode(&ns, body, nullptr, 0, &kp);
     kp.func = sssp ? (void*)trav_push<true> : (void*)trav_push<false>;
     kp.gridDim = dim3((unsigned)push_grid());
     kp.blockDim = dim3(kThreads);
     if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n0, body, &ns, 1, &kp);
-    cudaGraphNode_t n1b;
+    cudaGraphNode_t n1b = nullptr;
     if (e == cudaSuccess) {
         kp.func = !sssp ? (void*)trav_pull_bu : a.cw8 ? (void*)trav_pull_a<1> : (void*)trav_pull_a<4>;
         kp.gridDim = dim3((unsigned)(sssp ? pull_grid() : pull_bu_grid()));
@@ -1594,12 +1596,12 @@ gm_status build_loop_graph(gm_graph* g, bool sssp) {
         kp.func = (void*)trav_pull_b;
         kp.gridDim = dim3((unsigned)pull_b_grid());
         e = cudaGraphAddKernelNode(&n1b, body, &n1, 1, &kp);
-    } else {
+    } else if (e == cudaSuccess) {
         n1b = n1;  // the BFS pull applies in trav_pull_bu
     }
     if (e == cudaSuccess) {
         kp.func = sssp ? (void*)trav_finalize<true> : (void*)trav_finalize<false>;
-        kp.gridDim = dim3((unsigned)finalize_grid());
+        kp.gridDim = dim3((unsigned)finalize_grid(sssp));
         e = cudaGraphAddKernelNode(&n2, body, &n1b, 1, &kp);
     }
     cudaGraphExec_t exec = nullptr;
@@ -1704,7 +1706,7 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
         GM_CUDA_TRY(cudaGraphLaunch(g->loop_exec[slot], s));
     } else {
         TravArgs a = make_args(g);
-        const int pg = push_grid(), lg = sssp ? pull_grid() : pull_bu_grid(), fg = finalize_grid();
+        const int pg = push_grid(), lg = sssp ? pull_grid() : pull_bu_grid(), fg = finalize_grid(sssp);
         cudaEvent_t ev0 = nullptr, ev1 = nullptr, evA = nullptr, evB = nullptr;
         if (g->tune.profile) {
             GM_CUDA_TRY(cudaEventCreate(&ev0));
