@@ -3,7 +3,10 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The CUDA library never calls it, and the
 two share no code: the oracle is plain serial C (``graphmat_oracle.c``) compiled
-with the host gcc, wrapped here with ctypes and numpy.
+with the host gcc, wrapped here with ctypes and numpy.  For timing on all host
+cores, PageRank, BFS and SSSP can also run on OpenMP threads (``threads=``
+argument; PageRank as a pull in the serial Reduce order, BFS and SSSP as a push
+with an atomic minimum), which gives identical results.
 
 Every function follows a passage of the paper (Sundaram et al., VLDB 2015):
 Algorithm 1 (generalized SPMV) inside Algorithm 2 (Run_Graph_Program) for
@@ -38,8 +41,11 @@ def build(force: bool = False) -> str:
                 and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
             return _LIB_PATH
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", "-O2", "-shared", "-fPIC", "-std=c11", "-o", tmp, _SRC, "-lm"],
-                       check=True)
+        cmd = ["gcc", "-O2", "-shared", "-fPIC", "-std=c11", "-o", tmp, _SRC, "-lm"]
+        try:  # OpenMP for the multi-threaded pull engine; without it that engine runs one thread
+            subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], check=True, capture_output=True)
+        except subprocess.CalledProcessError:
+            subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
         return _LIB_PATH
 
@@ -60,7 +66,11 @@ def _load():
         "or_graph_edges": ([P, P, P, P], None),
         "or_graph_degrees": ([P, P, P], None),
         "or_pagerank": ([P, f64, i64, i32, P], i64),
+        "or_pagerank_threads": ([P, f64, i64, i32, P, i32], i64),
         "or_bfs": ([P, P, i64, i64, P], i64),
+        "or_bfs_threads": ([P, P, i64, i64, P, i32], i64),
+        "or_sssp_threads": ([P, P, i64, i64, P, i32], i64),
+        "or_openmp": ([], i32),
         "or_connected_components": ([P, i64, P], i64),
         "or_sssp": ([P, P, i64, i64, P], i64),
         "or_reached_edges": ([P, P], i64),
@@ -129,15 +139,22 @@ class Graph:
         return o, i
 
     # -- vertex programs -------------------------------------------------
-    def pagerank(self, r=0.15, iters=20, apply_all_vertices=True):
+    # threads=0: the serial engine (Algorithm 1 as a push in source order);
+    # threads>=1: a threaded engine on that many OpenMP threads (same results).
+    def pagerank(self, r=0.15, iters=20, apply_all_vertices=True, threads=0):
         x = np.empty(self.n, np.float64)
-        it = _load().or_pagerank(self._h, r, iters, 1 if apply_all_vertices else 0, _p(x))
+        a = 1 if apply_all_vertices else 0
+        lib = _load()
+        it = (lib.or_pagerank_threads(self._h, r, iters, a, _p(x), threads) if threads > 0
+              else lib.or_pagerank(self._h, r, iters, a, _p(x)))
         return x, int(it)
 
-    def bfs(self, sources, max_iters=-1):
+    def bfs(self, sources, max_iters=-1, threads=0):
         s = np.ascontiguousarray(np.atleast_1d(sources), dtype=np.int32)
         d = np.empty(self.n, np.uint32)
-        it = _load().or_bfs(self._h, _p(s), s.shape[0], max_iters, _p(d))
+        lib = _load()
+        it = (lib.or_bfs_threads(self._h, _p(s), s.shape[0], max_iters, _p(d), threads) if threads > 0
+              else lib.or_bfs(self._h, _p(s), s.shape[0], max_iters, _p(d)))
         return d, int(it)
 
     def connected_components(self, max_iters=-1):
@@ -146,10 +163,12 @@ class Graph:
         it = _load().or_connected_components(self._h, max_iters, _p(lab))
         return lab, int(it)
 
-    def sssp(self, sources, max_iters=-1):
+    def sssp(self, sources, max_iters=-1, threads=0):
         s = np.ascontiguousarray(np.atleast_1d(sources), dtype=np.int32)
         d = np.empty(self.n, np.uint32)
-        it = _load().or_sssp(self._h, _p(s), s.shape[0], max_iters, _p(d))
+        lib = _load()
+        it = (lib.or_sssp_threads(self._h, _p(s), s.shape[0], max_iters, _p(d), threads) if threads > 0
+              else lib.or_sssp(self._h, _p(s), s.shape[0], max_iters, _p(d)))
         return d, int(it)
 
     def reached_edges(self, dist):
@@ -199,3 +218,8 @@ def cf_init(n, K, seed, sigma=0.1):
     out = np.empty(n * K, np.float64)
     _load().or_cf_init(seed, n * K, sigma, _p(out))
     return out.reshape(n, K)
+
+
+def openmp() -> bool:
+    """Whether the oracle's threaded engines were built with OpenMP."""
+    return bool(_load().or_openmp())

@@ -20,11 +20,21 @@
  *
  * Precision: every floating-point quantity is double; BFS/SSSP distances and
  * triangle counts are exact integers (held in double below 2^53, or uint64).
+ *
+ * For timing on many host cores only, PageRank, BFS and SSSP also run on
+ * OpenMP threads: PageRank on a pull engine (or_run_graph_program_pull) that
+ * evaluates Algorithm 1 per destination with the serial engine's Reduce order,
+ * BFS and SSSP on a push engine (or_run_min_program_threads) whose Reduce, an
+ * exact minimum, is applied with atomic compare-and-swap; both give results
+ * identical to the serial engine's (tested).
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_EXPORT __attribute__((visibility("default")))
 
@@ -224,6 +234,161 @@ static int64_t or_run_graph_program(const or_graph* G, or_program* P, double* pr
     return it;
 }
 
+/* Algorithm 2 with Algorithm 1 evaluated destination by destination (pull
+ * form), for the multi-core timing of the oracle.  Each superstep first marks
+ * the out-neighbours of the vertices that sent a message (the destinations that
+ * receive one); each marked destination k then reduces the processed messages
+ * of its in-edges j -> k in ascending order of j (ties in input order): the
+ * order in which or_spmv's push over the sorted edges reaches k, so every
+ * destination sees the same sequence of Reduce calls and the result equals
+ * or_run_graph_program's exactly.  Destinations are independent (one owner
+ * thread each); `threads` OpenMP threads (one without OpenMP).  The in-edge
+ * lists are built here from the sorted edges. */
+static int64_t or_run_graph_program_pull(const or_graph* G, or_program* P, double* prop, uint8_t* active,
+                                         int64_t max_iters, int threads) {
+    const int64_t n = G->n, m = G->m;
+    const size_t nz = (size_t)(n > 0 ? n : 1), mz = (size_t)(m > 0 ? m : 1);
+    int64_t* in_begin = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * nz);
+    int32_t* in_src = (int32_t*)malloc(sizeof(int32_t) * mz);
+    double* in_val = (double*)malloc(sizeof(double) * mz);
+    uint8_t* xp = (uint8_t*)malloc(nz);
+    uint8_t* yp = (uint8_t*)malloc(nz);
+    uint8_t* mk = (uint8_t*)calloc(nz, 1); /* destinations that receive a message */
+    double* x = (double*)malloc(sizeof(double) * nz);
+    double* y = (double*)malloc(sizeof(double) * nz);
+    int64_t it = -1;
+    if (!in_begin || !pos || !in_src || !in_val || !xp || !yp || !mk || !x || !y) goto done;
+    for (int64_t e = 0; e < m; ++e) in_begin[G->dst[e] + 1]++;
+    for (int64_t v = 0; v < n; ++v) in_begin[v + 1] += in_begin[v];
+    for (int64_t v = 0; v < n; ++v) pos[v] = in_begin[v];
+    for (int64_t e = 0; e < m; ++e) { /* edges are sorted by source: each list comes out ascending */
+        const int64_t k = pos[G->dst[e]]++;
+        in_src[k] = G->src[e];
+        in_val[k] = G->val[e];
+    }
+    if (threads < 1) threads = 1;
+    (void)threads;
+    for (it = 0; max_iters < 0 || it < max_iters; ++it) {
+        P->iter = it;
+#pragma omp parallel for num_threads(threads) schedule(static)
+        for (int64_t v = 0; v < n; ++v) { /* send_message from active vertices */
+            xp[v] = 0;
+            if (active[v] && P->send_message(P, G, v, prop[v], &x[v])) xp[v] = 1;
+        }
+#pragma omp parallel for num_threads(threads) schedule(dynamic, 1024)
+        for (int64_t j = 0; j < n; ++j) { /* mark the receivers */
+            if (!xp[j]) continue;
+            for (int64_t e = G->out_begin[j]; e < G->out_begin[j + 1]; ++e) {
+#pragma omp atomic write
+                mk[G->dst[e]] = 1;
+            }
+        }
+#pragma omp parallel for num_threads(threads) schedule(dynamic, 4096)
+        for (int64_t k = 0; k < n; ++k) { /* generalized SPMV, destination k */
+            int has = 0;
+            double acc = 0.0;
+            if (!mk[k]) { yp[k] = 0; continue; }
+            mk[k] = 0;
+            for (int64_t i = in_begin[k]; i < in_begin[k + 1]; ++i) {
+                const int64_t j = in_src[i];
+                if (!xp[j]) continue;
+                const double result = P->process_message(P, x[j], in_val[i], prop[k]);
+                if (!has) { acc = result; has = 1; }
+                else acc = P->reduce(acc, result);
+            }
+            yp[k] = (uint8_t)has;
+            y[k] = acc;
+        }
+        int64_t n_active = 0;
+#pragma omp parallel for num_threads(threads) schedule(static) reduction(+ : n_active)
+        for (int64_t v = 0; v < n; ++v) { /* apply; changed vertices become active */
+            active[v] = 0;
+            double yv = y[v];
+            if (!yp[v]) {
+                if (!P->apply_to_all) continue;
+                yv = P->identity;
+            }
+            const double old = prop[v];
+            prop[v] = P->apply(P, yv, prop[v]);
+            if (prop[v] != old) { active[v] = 1; ++n_active; }
+        }
+        if (P->all_active) { memset(active, 1, (size_t)n); n_active = n; }
+        if (n_active == 0) { ++it; break; } /* converged */
+    }
+done:
+    free(in_begin); free(pos); free(in_src); free(in_val); free(xp); free(yp); free(mk); free(x); free(y);
+    return it;
+}
+
+/* y = min(y, v) on the bit pattern of a non-negative double (such patterns
+ * order like the values), atomically. */
+static void or_atomic_min_bits(uint64_t* p, double v) {
+    uint64_t nv;
+    memcpy(&nv, &v, sizeof nv);
+    uint64_t cur = __atomic_load_n(p, __ATOMIC_RELAXED);
+    while (nv < cur && !__atomic_compare_exchange_n(p, &cur, nv, 1, __ATOMIC_RELAXED, __ATOMIC_RELAXED)) {
+    }
+}
+
+/* Algorithm 2 for programs whose Reduce is the minimum of non-negative values
+ * (BFS, SSSP), for the multi-core timing of the oracle: Algorithm 1 as a push
+ * over the out-edges of the vertices that sent a message, sources split over
+ * `threads` OpenMP threads, each processed message combined into y[k] with an
+ * atomic minimum.  The minimum of exact values does not depend on the order of
+ * the combines, so the result equals or_run_graph_program's exactly. */
+static int64_t or_run_min_program_threads(const or_graph* G, or_program* P, double* prop, uint8_t* active,
+                                          int64_t max_iters, int threads) {
+    const int64_t n = G->n;
+    const size_t nz = (size_t)(n > 0 ? n : 1);
+    uint8_t* xp = (uint8_t*)malloc(nz);
+    uint8_t* yp = (uint8_t*)calloc(nz, 1);
+    double* x = (double*)malloc(sizeof(double) * nz);
+    uint64_t* yb = (uint64_t*)malloc(sizeof(uint64_t) * nz);
+    int64_t it = -1;
+    if (!xp || !yp || !x || !yb) goto done;
+    const double top = INFINITY;
+    uint64_t top_bits;
+    memcpy(&top_bits, &top, sizeof top_bits);
+    if (threads < 1) threads = 1;
+    (void)threads;
+    for (int64_t v = 0; v < n; ++v) yb[v] = top_bits;
+    for (it = 0; max_iters < 0 || it < max_iters; ++it) {
+        P->iter = it;
+#pragma omp parallel for num_threads(threads) schedule(static)
+        for (int64_t v = 0; v < n; ++v) { /* send_message from active vertices */
+            xp[v] = 0;
+            if (active[v] && P->send_message(P, G, v, prop[v], &x[v])) xp[v] = 1;
+        }
+#pragma omp parallel for num_threads(threads) schedule(dynamic, 256)
+        for (int64_t j = 0; j < n; ++j) { /* generalized SPMV, push from source j */
+            if (!xp[j]) continue;
+            for (int64_t e = G->out_begin[j]; e < G->out_begin[j + 1]; ++e) {
+                const int64_t k = G->dst[e];
+                or_atomic_min_bits(&yb[k], P->process_message(P, x[j], G->val[e], prop[k]));
+                __atomic_store_n(&yp[k], (uint8_t)1, __ATOMIC_RELAXED);
+            }
+        }
+        int64_t n_active = 0;
+#pragma omp parallel for num_threads(threads) schedule(static) reduction(+ : n_active)
+        for (int64_t v = 0; v < n; ++v) { /* apply; changed vertices become active */
+            active[v] = 0;
+            if (!yp[v]) continue;
+            double yv;
+            memcpy(&yv, &yb[v], sizeof yv);
+            yp[v] = 0;
+            yb[v] = top_bits;
+            const double old = prop[v];
+            prop[v] = P->apply(P, yv, prop[v]);
+            if (prop[v] != old) { active[v] = 1; ++n_active; }
+        }
+        if (n_active == 0) { ++it; break; } /* converged */
+    }
+done:
+    free(xp); free(yp); free(x); free(yb);
+    return it;
+}
+
 /* ---- PageRank, Eq. 1: PR_{t+1}(v) = r + (1-r) * sum_{u->v} PR_t(u)/deg(u) ---- */
 static int pr_send(const or_program* P, const or_graph* G, int64_t v, double prop, double* msg) {
     (void)P;
@@ -260,6 +425,19 @@ OR_EXPORT int64_t or_pagerank(const or_graph* G, double r, int64_t iters, int32_
     return it;
 }
 
+/* or_pagerank on the pull engine with `threads` threads (identical result). */
+OR_EXPORT int64_t or_pagerank_threads(const or_graph* G, double r, int64_t iters, int32_t apply_all_vertices,
+                                   double* rank_out, int32_t threads) {
+    uint8_t* active = (uint8_t*)malloc((size_t)(G->n > 0 ? G->n : 1));
+    if (!active) return -1;
+    memset(active, 1, (size_t)G->n);
+    for (int64_t v = 0; v < G->n; ++v) rank_out[v] = 1.0;
+    or_program P = {pr_send, pr_process, sum_reduce, pr_apply, 1, apply_all_vertices, 0.0, r, 0};
+    int64_t it = or_run_graph_program_pull(G, &P, rank_out, active, iters, threads);
+    free(active);
+    return it;
+}
+
 /* ---- BFS, Section 3.II: Distance(v) = min(Distance(v), t+1) ---- */
 static int dist_send(const or_program* P, const or_graph* G, int64_t v, double prop, double* msg) {
     (void)P; (void)G; (void)v;
@@ -285,8 +463,9 @@ static double sssp_process(const or_program* P, double msg, double ev, double dp
     return s >= OR_INF_U32 ? OR_INF_U32 : s;
 }
 
+/* threads 0: the serial engine; >= 1: the threaded push engine */
 static int64_t or_traverse(const or_graph* G, int bfs, const int32_t* sources, int64_t n_sources,
-                           int64_t max_iters, uint32_t* dist_out) {
+                           int64_t max_iters, uint32_t* dist_out, int threads) {
     double* prop = (double*)malloc(sizeof(double) * (size_t)(G->n > 0 ? G->n : 1));
     uint8_t* active = (uint8_t*)calloc((size_t)(G->n > 0 ? G->n : 1), 1);
     if (!prop || !active) { free(prop); free(active); return -1; }
@@ -294,7 +473,8 @@ static int64_t or_traverse(const or_graph* G, int bfs, const int32_t* sources, i
     for (int64_t i = 0; i < n_sources; ++i) { prop[sources[i]] = 0.0; active[sources[i]] = 1; }
     or_program P = {dist_send, bfs ? bfs_process : sssp_process, min_reduce, min_apply, 0, 0,
                     OR_INF_U32, 0.0, 0};
-    int64_t it = or_run_graph_program(G, &P, prop, active, max_iters);
+    int64_t it = threads > 0 ? or_run_min_program_threads(G, &P, prop, active, max_iters, threads)
+                             : or_run_graph_program(G, &P, prop, active, max_iters);
     for (int64_t v = 0; v < G->n; ++v) dist_out[v] = (uint32_t)prop[v];
     free(prop); free(active);
     return it;
@@ -302,12 +482,32 @@ static int64_t or_traverse(const or_graph* G, int bfs, const int32_t* sources, i
 
 OR_EXPORT int64_t or_bfs(const or_graph* G, const int32_t* sources, int64_t n_sources, int64_t max_iters,
                          uint32_t* depth_out) {
-    return or_traverse(G, 1, sources, n_sources, max_iters, depth_out);
+    return or_traverse(G, 1, sources, n_sources, max_iters, depth_out, 0);
 }
 
 OR_EXPORT int64_t or_sssp(const or_graph* G, const int32_t* sources, int64_t n_sources, int64_t max_iters,
                           uint32_t* dist_out) {
-    return or_traverse(G, 0, sources, n_sources, max_iters, dist_out);
+    return or_traverse(G, 0, sources, n_sources, max_iters, dist_out, 0);
+}
+
+/* or_bfs / or_sssp on `threads` OpenMP threads (identical results). */
+OR_EXPORT int64_t or_bfs_threads(const or_graph* G, const int32_t* sources, int64_t n_sources, int64_t max_iters,
+                              uint32_t* depth_out, int32_t threads) {
+    return or_traverse(G, 1, sources, n_sources, max_iters, depth_out, threads < 1 ? 1 : threads);
+}
+
+OR_EXPORT int64_t or_sssp_threads(const or_graph* G, const int32_t* sources, int64_t n_sources, int64_t max_iters,
+                               uint32_t* dist_out, int32_t threads) {
+    return or_traverse(G, 0, sources, n_sources, max_iters, dist_out, threads < 1 ? 1 : threads);
+}
+
+/* Whether the threaded engines were compiled with OpenMP (else they run one thread). */
+OR_EXPORT int32_t or_openmp(void) {
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 /* ---- Connected components by label propagation (a vertex program outside the
