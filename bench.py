@@ -270,8 +270,10 @@ def pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind):
     g.set_option(gm.GM_OPT_PROFILE, 0)
     achieved = byts / (ms / 1e3) / 1e9 if ms > 0 else None
     traffic = _recorded_traffic()
+    # the same launches measured by DRAM bytes (ncu) instead of algorithmic bytes
+    dram_frac = (traffic / (ms / max(launches, 1) / 1e3) / 1e9 / peak) if (traffic and ms > 0) else None
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic, "traffic_frac": dram_frac,
             "kernel": "trav_pull_a (SSSP pull)", "peak_source": peak_kind, "weight_bytes": wb,
             "bytes_per_launch": byts / max(launches, 1), "avg_launch_us": 1e3 * ms / max(launches, 1),
             "launches": launches,

@@ -210,7 +210,7 @@ enum {
     GM_SCALAR_PUSH_STEPS = 5,     /* int32: supersteps of the last gm_run run top-down (push) */
     GM_SCALAR_PULL_STEPS = 6,     /* int32: supersteps run bottom-up (pull) */
     GM_SCALAR_SCANNED_EDGES = 7,  /* int64: edges read by the relax kernels in the last gm_run */
-    GM_SCALAR_RELAX_MS = 8,       /* double: profile mode, summed relax-kernel time (CUDA events) */
+    GM_SCALAR_RELAX_MS = 8,       /* double: profile mode, summed superstep-kernel time (CUDA events) */
     GM_SCALAR_RELAX_LAUNCHES = 9, /* int32: profile mode, relax-kernel launches timed */
     GM_SCALAR_PROCESSED_VERTICES = 10, /* int64: vertices whose edge lists the relax kernels read */
     GM_SCALAR_PULL_WEIGHT_BYTES = 11   /* int32: bytes per in-edge weight the SSSP pull reads: 1 when
@@ -223,9 +223,10 @@ GM_API gm_status gm_get_scalar(gm_graph* g, int32_t which, void* out);
  * Per-superstep trace of the last gm_run in profile mode (GM_OPT_PROFILE = 1):
  * up to max_rows rows of 8 doubles -- superstep index, direction (0 push, 1 pull),
  * active work items at its start, edges read, vertices whose edge lists were read,
- * time of the push + pull kernels in ms (CUDA events), the out-edges of the next
- * frontier, and the time of the pull's first kernel alone (0 in push supersteps; SSSP:
- * the in-edge streaming kernel, BFS: the bottom-up kernel, which counts in-edges checked).
+ * time of the superstep's kernels in ms (push, pull and finalize, which holds the
+ * SSSP Apply after a pull; CUDA events), the out-edges of the next frontier, and
+ * the time of the pull kernel alone (0 in push supersteps; SSSP: the in-edge
+ * streaming kernel, BFS: the bottom-up kernel, which counts in-edges checked).
  * *n_rows receives the number of rows available.
  */
 GM_API gm_status gm_get_trace(gm_graph* g, double* rows, int32_t max_rows, int32_t* n_rows);

@@ -1,8 +1,8 @@
 // BFS and SSSP supersteps (Algorithms 1 and 2 with the min semiring).
 //
-// One superstep is four kernels for SSSP (push, the two pull kernels, finalize)
-// and three for BFS (push, the bottom-up pull, finalize); the direction not chosen
-// on the device returns at once:
+// One superstep is three kernels (push, pull, finalize); the direction not
+// chosen on the device returns at once, and inside the device loop a one-CTA
+// kernel (trav_small) first runs every superstep whose frontier is tiny:
 //   relax     the generalized SPMV with Process_Message/Reduce fused into the
 //             update of the vertex property (Apply = min), either
 //               push: over the out-edges (CSR) of the compacted frontier queue,
@@ -14,16 +14,18 @@
 //             vertices whose property changed join the next frontier (bitvector
 //             bit + binned queue, warp-aggregated) -- Algorithm 2's "mark changed
 //             vertices active" without a separate scan of the active array.
-//   finalize  SSSP after a push: writes the messages of the next frontier; the last CTA to
-//             finish counts the active vertices, stops at convergence or
+//   finalize  SSSP after a pull: Apply of the pull's per-column minima; SSSP
+//             after a push: the messages of the next frontier; then the last
+//             CTA to finish counts the active vertices, stops at convergence or
 //             max_iters, and picks push or pull for the next superstep.
 //
 // Work decomposition for HBM bandwidth: every lane handles 8 edges per step with
 // two 16-byte streaming loads per edge array, so each warp keeps 1-2 KB of edge
 // data in flight.  Push: frontier vertices of small degree go 32 to a warp with
 // their edge lists concatenated; the edges of medium vertices and of the
-// 2048-edge chunks of large ones are cut into 256-edge pieces dealt to all warps.  Pull: fixed 256-edge warp tiles over the doubly
-// compressed CSC, columns crossing tiles combined with atomics.
+// 2048-edge chunks of large ones are cut into 256-edge pieces dealt to all
+// warps.  Pull: fixed 256-edge warp tiles over the doubly compressed CSC,
+// columns crossing tiles combined with atomics.
 //
 // BSP semantics are exact: messages come from values fixed at the start of the
 // superstep (BFS: the constant t+1; SSSP: the message array), so the property
@@ -549,7 +551,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 // ---------------------------------------------------------------- pull
-// Pull in two kernels over the doubly compressed CSC (non-empty columns only).
+// Pull over the doubly compressed CSC (non-empty columns only).
 //  pull_a  (SSSP) streams the in-edges in warp tiles of kWTile: each lane reads 8
 //          consecutive edges with 16-byte loads (the next tile's edges are already
 //          in flight), evaluates Process_Message for each (msg[u] + w(u, v), msg
@@ -570,8 +572,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 //          at most t) and is skipped.  The result per column equals the full
 //          Reduce(min) wherever Apply can use it.
 //          It applies directly (one lane owns a column).
-//  pull_b  (SSSP) applies y to the vertex properties (Apply = min), makes changed
-//          vertices the next frontier and resets y to infinity.
+//  pull_apply (SSSP, in the finalize kernel) applies y to the vertex properties
+//          (Apply = min), makes changed vertices the next frontier and resets y
+//          to infinity.
 // One warp tile's streamed inputs per lane: 8 in-edge source ranks, their
 // weights (one-byte weights stay packed in two words until used), the lane's 8
 // first-edge bits and the tile's first column.
@@ -888,16 +891,11 @@ __global__ void __launch_bounds__(kThreads, 4) trav_pull_bu(TravArgs a) {
     flush_acc(a, acc, nxt, true, s_stat);
 }
 
-// SSSP Apply after trav_pull_a: four columns per lane per step (independent loads
-// in flight), coalesced across the warp for each of the four.
-
-__global__ void __launch_bounds__(kThreads, 4) trav_pull_b(TravArgs a) {
-    TravCtlDev* cd = a.ctl;
-    if (cd->c.done || cd->c.dir != 1u) return;
-    const uint32_t t = cd->c.iter;
+// SSSP Apply after trav_pull_a (run by the SSSP finalize kernel in a pull
+// superstep): four columns per lane per step (independent loads in flight),
+// coalesced across the warp for each of the four.  CTA-collective.
+__device__ __forceinline__ void pull_apply(const TravArgs& a, uint32_t t, WarpQ* s_q, unsigned long long* s_stat) {
     const int nxt = (int)((t + 1u) % 3u);
-    __shared__ WarpQ s_q[kWarps];
-    __shared__ unsigned long long s_stat[6];
     if (threadIdx.x < 6) s_stat[threadIdx.x] = 0ull;
     if ((threadIdx.x & 31) < 2) s_q[threadIdx.x >> 5].n[threadIdx.x & 31] = 0u;
     __syncthreads();
@@ -1031,12 +1029,17 @@ __device__ uint32_t finish_superstep(const TravArgs& a, TravCtlDev* cdp, uint32_
     return done;
 }
 
+// Last kernel of a superstep.  SSSP: after a pull, Apply (pull_apply); after a
+// push, the messages of superstep t+1.  Then each CTA takes a ticket and the
+// last one applies the end-of-superstep rule to the next frontier's counts.
 template <bool SSSP>
-__global__ void __launch_bounds__(kThreads) trav_finalize(TravArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) trav_finalize(TravArgs a) {
     TravCtlDev* cd = a.ctl;
     TravCtl* c = &cd->c;
     __shared__ uint32_t s_t, s_done, s_last, s_dir;
     __shared__ uint32_t s_cnt[4];
+    __shared__ WarpQ s_q[SSSP ? kWarps : 1];
+    __shared__ unsigned long long s_stat[6];
     if (threadIdx.x == 0) {
         s_t = c->iter;
         s_done = c->done;
@@ -1047,7 +1050,9 @@ __global__ void __launch_bounds__(kThreads) trav_finalize(TravArgs a) {
     if (s_done) return;
     const uint32_t t = s_t;
     const int nxt = (int)((t + 1u) % 3u);
-    if (SSSP && s_dir == 0u) {  // messages of superstep t+1 after a push (pull_b writes its own)
+    if (SSSP && s_dir == 1u) {
+        pull_apply(a, t, s_q, s_stat);
+    } else if (SSSP) {  // messages of superstep t+1 after a push (pull_apply writes its own)
         const uint32_t n1 = s_cnt[1], n2 = s_cnt[2], n3 = s_cnt[3];
         uint32_t* ms = a.msg[(t + 1u) & 1u];
         for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < (int64_t)n1 + n2 + n3;
@@ -1073,6 +1078,10 @@ __global__ void __launch_bounds__(kThreads) trav_finalize(TravArgs a) {
     // ---- last CTA: termination and direction for superstep t+1 ----
     __threadfence();
     c->ticket = 0;
+    if (SSSP && s_dir == 1u) {  // counted by pull_apply in this kernel: read them from L2
+        volatile uint32_t* vc = c->count[nxt];
+        for (int b = 0; b < 4; ++b) s_cnt[b] = vc[b];
+    }
     const uint32_t done = finish_superstep<SSSP>(a, cd, t, s_cnt);
     if (a.use_cond) cudaGraphSetConditional(a.cond, done ? 0u : 1u);
 }
@@ -1494,13 +1503,11 @@ int pull_bu_grid() {
     return blocks;
 }
 
-// SSSP's finalize writes the next messages after a push (a grid-stride loop);
-// BFS's only elects the last CTA, so one CTA is enough.
-int finalize_grid(bool sssp) { return sssp ? 2 * num_sms() : 1; }
-
-int pull_b_grid() {
-    static int blocks = grid_for(trav_pull_b);
-    return blocks;
+// SSSP's finalize applies a pull or writes the next messages after a push
+// (grid-stride loops); BFS's only elects the last CTA, so one CTA is enough.
+int finalize_grid(bool sssp) {
+    static int blocks = grid_for(trav_finalize<true>);
+    return sssp ? blocks : 1;
 }
 
 #define LAUNCH_OK()                                                                             \
@@ -1592,12 +1599,8 @@ gm_status build_loop_graph(gm_graph* g, bool sssp) {
         kp.blockDim = dim3(kThreads);
         kp.sharedMemBytes = 0u;
     }
-    if (e == cudaSuccess && sssp) {
-        kp.func = (void*)trav_pull_b;
-        kp.gridDim = dim3((unsigned)pull_b_grid());
-        e = cudaGraphAddKernelNode(&n1b, body, &n1, 1, &kp);
-    } else if (e == cudaSuccess) {
-        n1b = n1;  // the BFS pull applies in trav_pull_bu
+    if (e == cudaSuccess) {
+        n1b = n1;  // Apply: the BFS pull's own, the SSSP finalize's
     }
     if (e == cudaSuccess) {
         kp.func = sssp ? (void*)trav_finalize<true> : (void*)trav_finalize<false>;
@@ -1633,7 +1636,7 @@ gm_status trav_prepare(gm_graph* g) {
     fill_u32<<<num_sms() * 4, 256, 0, s>>>(as<uint32_t>(g->state), g->n, kInf);
     g_launches++;
     LAUNCH_OK();
-    // per-column pull results start at infinity; pull_b restores that after every use
+    // per-column pull results start at infinity; pull_apply restores that after every use
     GM_CUDA_TRY(cudaMemsetAsync(work_layout(g).ycol, 0xFF, sizeof(uint32_t) * n, s));
     GM_TRY(reset_frontier(g));
     g->reached_total = 0;  // every property is infinity
@@ -1734,12 +1737,11 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
             else if (sssp) trav_pull_a<4><<<lg, kPullThreads, (size_t)a.hot * 4u, s>>>(a);
             else trav_pull_bu<<<lg, kThreads, 0, s>>>(a);
             if (evB) cudaEventRecord(evB, s);
-            if (sssp) trav_pull_b<<<pull_b_grid(), kThreads, 0, s>>>(a);
-            if (ev1) cudaEventRecord(ev1, s);
-            g_launches += sssp ? 3 : 2;
+            g_launches += 2;
             LAUNCH_OK();
-            if (sssp) trav_finalize<true><<<fg, kThreads, 0, s>>>(a);
+            if (sssp) trav_finalize<true><<<fg, kThreads, 0, s>>>(a);  // SSSP Apply runs here
             else trav_finalize<false><<<fg, kThreads, 0, s>>>(a);
+            if (ev1) cudaEventRecord(ev1, s);
             g_launches++;
             LAUNCH_OK();
             GM_CUDA_TRY(cudaMemcpyAsync(&hp->c.done, &as<TravCtlDev>(g->ctl_buf)->c.done, sizeof(uint32_t),
@@ -1772,7 +1774,7 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
     }
     GM_CUDA_TRY(cudaMemcpyAsync(hp, g->ctl_buf.p, sizeof(TravCtlDev), cudaMemcpyDeviceToHost, s));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
-    if (!host_loop) g_launches += (sssp ? 5ull : 4ull) * hp->c.loops;
+    if (!host_loop) g_launches += 4ull * hp->c.loops;
     g->stats.supersteps = (int32_t)hp->c.iters_done;
     g->stats.pushes = (int32_t)hp->c.pushes;
     g->stats.pulls = (int32_t)hp->c.pulls;
