@@ -286,8 +286,8 @@ def pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind):
 # DRAM bytes (read + write) per trav_pull_a launch in the bench's timed step, from
 # one ncu capture of this bench command; valid only for the kernel source it was
 # taken on (hash of the traversal source files at capture time).
-PULL_A_TRAFFIC = {"source_sha256": "2e8a4d235ad54faf55a4c744ca2a2abb9119cb3c8548a57703a6a3b1bb7c0d05",
-                  "bytes_per_launch": 365.83e6}
+PULL_A_TRAFFIC = {"source_sha256": "4631a48ad08f5d42f62cb8bd3b72e0371bef644cef9360da9a594e0543a54699",
+                  "bytes_per_launch": 365.20e6}
 
 
 def _kernel_source_hash():
