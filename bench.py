@@ -414,11 +414,28 @@ def paper_shapes(gm):
         dev = torch.from_numpy(srcs).cuda()
         if "bfs" in programs:
             g.autotune(gm.GM_BFS, srcs[:2])
-        g.autotune(gm.GM_SSSP, srcs[4:6])
+        tuned = g.autotune(gm.GM_SSSP, srcs[4:6])
+        res["sssp_tuning"] = {k: tuned[k] for k in ("sssp_pull_frac", "bin_small", "bin_large", "pull_stage")}
         pq = per_query(gm, g, srcs[:4] if "bfs" in programs else srcs[:0], srcs[4:8], (dev[:4], dev[4:8]))
         if "bfs" in programs:
             res["bfs"] = pq["bfs"]
         res["sssp"] = pq["sssp"]
+        if name == "rmat24_sssp":  # where the time goes: one query's supersteps, and the pull fraction
+            g.set_option(gm.GM_OPT_PROFILE, 1)
+            g.program_set(gm.GM_SSSP)
+            g.set_active(dev[4:5])
+            g.run(-1)
+            res["trace_source4"] = [{"t": int(r[0]), "dir": "pull" if r[1] == 1 else "push", "active": int(r[2]),
+                                     "edges": int(r[3]), "ms": round(r[5], 4), "pull_kernel_ms": round(r[7], 4)}
+                                    for r in g.trace()]
+            g.set_option(gm.GM_OPT_PROFILE, 0)
+            sweep = []
+            for ppm in (20000, 50000, 100000, 200000):
+                g.set_option(gm.GM_OPT_SSSP_PULL_PPM, ppm)
+                one = per_query(gm, g, srcs[:0], srcs[4:5], (dev[:0], dev[4:5]))["sssp"]
+                sweep.append({"sssp_pull_frac": ppm / 1e6, "ms": one["median_ms"]})
+            g.set_option(gm.GM_OPT_SSSP_PULL_PPM, int(round(tuned["sssp_pull_frac"] * 1e6)))
+            res["pull_fraction_sweep_source4"] = sweep
         out[name] = res
         g.close()
         torch.cuda.empty_cache()
