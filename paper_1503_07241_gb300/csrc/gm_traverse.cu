@@ -1366,6 +1366,41 @@ __global__ void seed_all(TravArgs a, int bfs) {
     }
 }
 
+// The frontier's reset state in one launch: the three bitvectors clear, (SSSP)
+// both message arrays infinity, and a fresh control block holding the run
+// parameters (the superstep-0 direction from dir_mode).  Arrays start 256-byte
+// aligned: 16-byte stores, then the tail.
+__global__ void reset_kernel(TravCtlDev* cd, uint32_t* bv0, uint32_t* bv1, uint32_t* bv2, int64_t nwords,
+                             uint32_t* m0, uint32_t* m1, int64_t n, int32_t dir_mode, float alpha, float beta,
+                             float sssp_frac, unsigned long long m) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u), f = make_uint4(kInf, kInf, kInf, kInf);
+    for (int64_t i = tid; i < nwords >> 2; i += stride) {
+        reinterpret_cast<uint4*>(bv0)[i] = z;
+        reinterpret_cast<uint4*>(bv1)[i] = z;
+        reinterpret_cast<uint4*>(bv2)[i] = z;
+    }
+    for (int64_t i = ((nwords >> 2) << 2) + tid; i < nwords; i += stride) bv0[i] = bv1[i] = bv2[i] = 0u;
+    if (m0) {
+        for (int64_t i = tid; i < n >> 2; i += stride) {
+            reinterpret_cast<uint4*>(m0)[i] = f;
+            reinterpret_cast<uint4*>(m1)[i] = f;
+        }
+        for (int64_t i = ((n >> 2) << 2) + tid; i < n; i += stride) m0[i] = m1[i] = kInf;
+    }
+    if (tid == 0) {
+        TravCtlDev c = {};
+        c.max_iters = -1;
+        c.dir_mode = dir_mode;
+        c.alpha = alpha;
+        c.beta = beta;
+        c.sssp_frac = sssp_frac;
+        c.c.unvisited_in_edges = m;
+        c.c.dir = dir_mode == 2 ? 1u : 0u;
+        *cd = c;
+    }
+}
+
 __global__ void fill_u32(uint32_t* p, int64_t n, uint32_t v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
@@ -1529,12 +1564,11 @@ gm_status reset_frontier(gm_graph* g) {
     TravWork w = work_layout(g);
     const int64_t n = g->n > 0 ? g->n : 1;
     const int64_t nwords = (n + 31) / 32;
-    for (int k = 0; k < 3; ++k) GM_CUDA_TRY(cudaMemsetAsync(w.bv[k], 0, sizeof(uint32_t) * nwords, s));
-    if (g->kind == GM_SSSP)
-        for (int k = 0; k < 2; ++k) GM_CUDA_TRY(cudaMemsetAsync(w.msg[k], 0xFF, sizeof(uint32_t) * n, s));
-    GM_CUDA_TRY(cudaMemsetAsync(g->ctl_buf.p, 0, sizeof(TravCtlDev), s));
-    ctl_params<<<1, 1, 0, s>>>(as<TravCtlDev>(g->ctl_buf), -1, g->tune.direction, (float)g->tune.alpha,
-                               (float)g->tune.beta, (float)g->tune.sssp_pull_frac, (unsigned long long)g->m, 1);
+    const bool sssp = g->kind == GM_SSSP;
+    reset_kernel<<<num_sms() * 4, 256, 0, s>>>(as<TravCtlDev>(g->ctl_buf), w.bv[0], w.bv[1], w.bv[2], nwords,
+                                               sssp ? w.msg[0] : nullptr, sssp ? w.msg[1] : nullptr, n,
+                                               g->tune.direction, (float)g->tune.alpha, (float)g->tune.beta,
+                                               (float)g->tune.sssp_pull_frac, (unsigned long long)g->m);
     g_launches++;
     LAUNCH_OK();
     g->frontier_clean = true;
@@ -1773,6 +1807,10 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
         if (evB) cudaEventDestroy(evB);
     }
     GM_CUDA_TRY(cudaMemcpyAsync(hp, g->ctl_buf.p, sizeof(TravCtlDev), cudaMemcpyDeviceToHost, s));
+    // the frontier reset for the next run goes into the stream behind that copy,
+    // before the wait: seeds pending in the control block are in the copy
+    g->reached_pending = false;
+    GM_TRY(reset_frontier(g));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
     if (!host_loop) g_launches += 4ull * hp->c.loops;
     g->stats.supersteps = (int32_t)hp->c.iters_done;
@@ -1782,11 +1820,9 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
     g->stats.processed_vertices = (int64_t)hp->c.processed_vertices;
     if (iters_done) *iters_done = (int32_t)hp->c.iters_done;
     g->reached_total += (int64_t)hp->c.reached;  // seeds since the last reset and this run
-    g->reached_pending = false;
     const uint32_t bad = hp->c.bad_ids;
     const uint32_t guard = hp->c.guard_hit;
     const uint32_t stage_to = hp->c.stage_timeouts;
-    GM_TRY(reset_frontier(g));
     if (stage_to) {  // the results are still exact (those CTAs gathered every message from global memory)
         set_error("gm_run: %u pull CTAs timed out waiting for their shared-memory staging copy", stage_to);
         return GM_ERR_TIMEOUT;

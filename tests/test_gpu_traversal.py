@@ -264,9 +264,18 @@ def test_small_supersteps_match_host_loop(gm, kind):
     ps, pd = np.arange(n2 - 1, dtype=np.int32), np.arange(1, n2, dtype=np.int32)
     hs = np.concatenate([np.zeros(5000, np.int32), np.arange(1, 5001, dtype=np.int32)])
     hd = np.concatenate([np.arange(1, 5001, dtype=np.int32), (np.arange(5000, dtype=np.int32) * 7 + 3) % 5001])
+    # a star of 3000 leaves of which only the first 40 have an out-edge (to 40
+    # vertices chained one after another): the superstep over the centre sets 3000
+    # frontier bits (more than the small kernel lists), the following ones are
+    # small and must clear that bitvector whole
+    ss_ = np.concatenate([np.zeros(3000, np.int32), np.arange(1, 41, dtype=np.int32),
+                          np.arange(3001, 3040, dtype=np.int32)])
+    sd_ = np.concatenate([np.arange(1, 3001, dtype=np.int32), np.arange(3001, 3041, dtype=np.int32),
+                          np.arange(3002, 3041, dtype=np.int32)])
     cases = [(n, s, d, w, list(synth.pick_sources(n, s, d, 4, seed=31))),
              (n2, ps, pd, (ps % 7 + 1).astype(np.uint32), [0, 1500]),
-             (5001, hs, hd, ((hs + hd) % 11 + 1).astype(np.uint32), [0, 17])]
+             (5001, hs, hd, ((hs + hd) % 11 + 1).astype(np.uint32), [0, 17]),
+             (3041, ss_, sd_, ((ss_ * 3 + sd_) % 13 + 1).astype(np.uint32), [0])]
     for nn, ss, dd, ww, srcs in cases:
         g = gm.Graph(nn, ss, dd, ww)
         og = oracle.Graph(nn, ss, dd, ww)
