@@ -242,10 +242,14 @@ def reference_arm(args):
 
 def pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind):
     """trav_pull_a, the dominant kernel (SSSP pull): CUDA events around each of its
-    launches (profile mode); algorithmic bytes = in-edges read x (4 B source id +
-    the stored weight width) + 1 bit per in-edge (column starts).  The BFS pull
+    launches (profile mode); algorithmic bytes per launch = in-edges read x (4 B
+    source id + the stored weight width + 1 bit of column start) + the message
+    array once (4 B per vertex: vertex state counts once per superstep) + the
+    per-column result written once (4 B per non-empty column).  The BFS pull
     (trav_pull_bu, bottom-up) is timed beside it."""
     wb = g.scalar(gm.GM_SCALAR_PULL_WEIGHT_BYTES)
+    _, in_deg = g.degrees()
+    state_bytes = 4.0 * g.n + 4.0 * float(np.count_nonzero(in_deg))
     g.set_option(gm.GM_OPT_PROFILE, 1)
     byts, ms, launches = 0.0, 0.0, 0
     bu_ms, bu_edges, bu_launches = 0.0, 0.0, 0
@@ -260,7 +264,7 @@ def pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind):
                 relax_ms += row[5]
                 relax_bytes += row[3] * (4 + sw) + row[4] * 12
                 if row[1] == 1 and kind == gm.GM_SSSP:
-                    byts += row[3] * (4 + sw) + row[3] / 8.0
+                    byts += row[3] * (4 + sw) + row[3] / 8.0 + state_bytes
                     ms += row[7]
                     launches += 1
                 elif row[1] == 1:
