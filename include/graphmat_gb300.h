@@ -256,11 +256,15 @@ GM_API gm_status gm_wpagerank_backward(gm_graph* g, const float* dLdx, float* dL
  * loop.  Queries of one program on one graph are bundled, up to 8 per bundle,
  * and run as one multi-source SpMSpV: a frontier byte per vertex (a bit per
  * query) and, for SSSP, a 32-byte row of 8 messages per vertex, so one pass over
- * the in-edges per superstep serves the whole bundle.  All bundles advance in
- * lockstep supersteps; a device work queue hands vertex groups of every bundle
- * to the warps; the loop is one CUDA graph whose conditional node stops when no
- * query is active.  Each query's result and superstep count equal gm_run's for
- * the same graph, program and single source.
+ * the edges per superstep serves the whole bundle.  Each bundle pushes over its
+ * frontier's out-edges or pulls over every in-edge, chosen on the device each
+ * superstep from the frontier's out-edges and the graph handle's switch point
+ * and direction option (gm_set_option / gm_autotune: SSSP pulls above
+ * 4 x sssp_pull_frac of the edges, BFS above 1/alpha of them).  All bundles advance
+ * in lockstep supersteps; a device work queue hands work of every bundle to the
+ * warps; the loop is one CUDA graph whose conditional node stops when no query
+ * is active.  Each query's result and superstep count equal gm_run's for the
+ * same graph, program and single source.
  *   graphs     n_graphs handles (their programs and states are not touched).
  *   queries    n_queries entries: graph index, GM_BFS or GM_SSSP, source vertex.
  *   out_state  n_queries device pointers, uint32[n of the query's graph] each:
@@ -268,8 +272,9 @@ GM_API gm_status gm_wpagerank_backward(gm_graph* g, const float* dLdx, float* dL
  *   max_iters  -1: every query until convergence; k > 0: at most k supersteps.
  *   iters_done NULL or int32[n_queries] (host): supersteps of each query.
  *   stream     cudaStream_t (NULL = default); the call synchronises it.
- * Workspace (per bundle: two frontier bytes per vertex, and a reached byte per
- * vertex for BFS or two 32-byte message rows per vertex for SSSP) is allocated
+ * Workspace (per bundle: two frontier bytes and two frontier lists of 8-byte
+ * entries per vertex and per 256 edges, and a reached byte per vertex for BFS
+ * or two 32-byte message rows per vertex for SSSP) is allocated
  * for the call and released before it returns.
  */
 typedef struct gm_query {

@@ -128,3 +128,22 @@ def test_batch_full_bundles_duplicates_and_unweighted(gm):
             continue
         oref, oit = (og[gi].bfs if kind == 1 else og[gi].sssp)([x])
         assert np.array_equal(got, oref) and it == oit
+
+
+@pytest.mark.parametrize("direction", [0, 1, 2])
+def test_batch_every_direction(gm, direction):
+    """Bundles push or pull per superstep from the handle's switch point: forced
+    push, forced pull and the automatic switch all give every query's exact
+    result and superstep count (with and without max_iters), on graphs where the
+    automatic switch does both."""
+    graphs = _graphs(gm, [9, 12], synth.BASE_SEED + 120)
+    for t in graphs:
+        t[4].set_option(gm.GM_OPT_DIRECTION, direction)
+    queries = _queries(graphs, 9, 121)  # 9 per program and graph: a full bundle and one more
+    for max_iters in (-1, 3):
+        res, its = _run(gm, graphs, queries, max_iters)
+        for (gi, kind, src), got, it in zip(queries, res, its):
+            n, s, d, w, g = graphs[gi]
+            og = oracle.Graph(n, s, d, w)
+            oref, oit = (og.bfs if kind == 1 else og.sssp)([src], max_iters=max_iters)
+            assert np.array_equal(got, oref) and it == oit, (direction, max_iters, gi, kind, src)
