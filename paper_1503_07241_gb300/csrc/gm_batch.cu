@@ -30,8 +30,8 @@
 // pull that a push follows it lists the next frontier from its bytes.  A
 // one-CTA plan kernel retires the queries whose next frontier is empty
 // (recording their superstep counts), lays out the next work queue and stops the
-// loop when no query runs.  The three kernels are the body of a CUDA graph's
-// WHILE node.
+// loop when no query runs.  The pull and push kernels (side by side), finish
+// and plan are the body of a CUDA graph's WHILE node.
 #include <algorithm>
 #include <vector>
 
@@ -76,7 +76,8 @@ struct Bundle {
     uint32_t* msg[2];        // SSSP: n rows of 8 messages, by superstep parity
     int2* piece[2];          // frontier by parity: (vertex, piece) per 256 out-edges, (v, 0) if none
     uint32_t npiece[2];
-    uint32_t item0, n_items; // this superstep's work items
+    uint32_t item0[2];       // offset of this superstep's work items in the [0] push / [1] pull queue
+    uint32_t n_items;        // this superstep's work items (in its direction's queue)
     uint32_t n_small, n_big, n_zero;  // pull work items of each kind
     uint32_t dir;            // this superstep: 0 push, 1 pull
     uint32_t next_dir;       // the next superstep's, decided when this one's frontier is known
@@ -90,7 +91,7 @@ struct BCtl {
     uint32_t any_active;
     uint32_t guard_hit;
     uint32_t max_iters;    // 0: until convergence
-    uint32_t total_items;  // work items of this superstep over all bundles
+    uint32_t total[2];     // work items of this superstep over all bundles: [0] push, [1] pull
 };
 
 struct BArgs {
@@ -191,11 +192,15 @@ __device__ __forceinline__ void enqueue_next(Bundle& B, const BGraph& G, int nxt
     for (uint32_t p = 0; p < np; ++p) out[p] = make_int2(v, (int32_t)p);
 }
 
-__device__ __forceinline__ int32_t bundle_of(const Bundle* bs, int32_t nb, uint32_t item) {
+// The bundle holding work item `item` of direction d's queue: the last bundle
+// whose offset in that queue is at most `item` (offsets are exclusive prefixes
+// over all bundles, a bundle of the other direction counting zero items, so it
+// shares its offset with the next bundle and is never the last one found).
+__device__ __forceinline__ int32_t bundle_of(const Bundle* bs, int32_t nb, int d, uint32_t item) {
     int32_t lo = 0, hi = nb - 1;
     while (lo < hi) {
         const int32_t mid = (lo + hi + 1) >> 1;
-        if (bs[mid].item0 <= item) lo = mid;
+        if (bs[mid].item0[d] <= item) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -337,19 +342,31 @@ __device__ __forceinline__ void push_item(Bundle& B, const BGraph& G, uint32_t k
     if (lane == 0 && changed_all) atomicOr(&B.next_active, changed_all);
 }
 
-__global__ void __launch_bounds__(kThreads, 5) batch_relax(BArgs a) {
+// The pull and push work of a superstep: two kernels (each compiled for its own
+// register use), run side by side as two branches of the loop graph.
+__global__ void __launch_bounds__(kThreads) batch_pull(BArgs a) {
     const BCtl* c = a.ctl;
     if (c->any_active == 0u) return;
-    const uint32_t t = c->t, total = c->total_items;
+    const uint32_t t = c->t, total = c->total[1];
     const int cur = (int)(t & 1u), nxt = cur ^ 1;
     const uint32_t gwarp = (blockIdx.x * kThreads + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * kThreads) >> 5;
     for (uint32_t item = gwarp; item < total; item += nwarps) {
-        Bundle& B = a.bundles[bundle_of(a.bundles, a.nb, item)];
-        const BGraph& G = a.graphs[B.graph];
-        const uint32_t k = item - B.item0;
-        if (B.dir) pull_item(B, G, k, t, cur, nxt);
-        else push_item(B, G, k, t, cur, nxt);
+        Bundle& B = a.bundles[bundle_of(a.bundles, a.nb, 1, item)];
+        pull_item(B, a.graphs[B.graph], item - B.item0[1], t, cur, nxt);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) batch_push(BArgs a) {
+    const BCtl* c = a.ctl;
+    if (c->any_active == 0u) return;
+    const uint32_t t = c->t, total = c->total[0];
+    const int cur = (int)(t & 1u), nxt = cur ^ 1;
+    const uint32_t gwarp = (blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * kThreads) >> 5;
+    for (uint32_t item = gwarp; item < total; item += nwarps) {
+        Bundle& B = a.bundles[bundle_of(a.bundles, a.nb, 0, item)];
+        push_item(B, a.graphs[B.graph], item - B.item0[0], t, cur, nxt);
     }
 }
 
@@ -414,26 +431,29 @@ __global__ void __launch_bounds__(kThreads) batch_finish(BArgs a) {
     }
 }
 
-// Exclusive prefix of the bundles' n_items into item0, and the total.  One CTA
-// of kPlanThreads; every thread calls it.
+// Exclusive prefixes of the bundles' n_items into the push and the pull queue
+// offsets (item0[d]; a bundle counts in its direction's queue only), and the
+// totals.  One CTA of kPlanThreads; every thread calls it.
 __device__ void layout_items(BArgs& a, uint32_t* s_scan) {
-    uint32_t base = 0u;
-    for (int32_t b0 = 0; b0 < a.nb; b0 += kPlanThreads) {
-        const int32_t b = b0 + (int32_t)threadIdx.x;
-        const uint32_t x = b < a.nb ? a.bundles[b].n_items : 0u;
-        s_scan[threadIdx.x] = x;
-        __syncthreads();
-        for (int o = 1; o < kPlanThreads; o <<= 1) {  // Hillis-Steele inclusive scan
-            const uint32_t y = threadIdx.x >= (unsigned)o ? s_scan[threadIdx.x - o] : 0u;
+    for (int d = 0; d < 2; ++d) {
+        uint32_t base = 0u;
+        for (int32_t b0 = 0; b0 < a.nb; b0 += kPlanThreads) {
+            const int32_t b = b0 + (int32_t)threadIdx.x;
+            const uint32_t x = (b < a.nb && a.bundles[b].dir == (uint32_t)d) ? a.bundles[b].n_items : 0u;
+            s_scan[threadIdx.x] = x;
             __syncthreads();
-            s_scan[threadIdx.x] += y;
+            for (int o = 1; o < kPlanThreads; o <<= 1) {  // Hillis-Steele inclusive scan
+                const uint32_t y = threadIdx.x >= (unsigned)o ? s_scan[threadIdx.x - o] : 0u;
+                __syncthreads();
+                s_scan[threadIdx.x] += y;
+                __syncthreads();
+            }
+            if (b < a.nb) a.bundles[b].item0[d] = base + s_scan[threadIdx.x] - x;
+            base += s_scan[kPlanThreads - 1];
             __syncthreads();
         }
-        if (b < a.nb) a.bundles[b].item0 = base + s_scan[threadIdx.x] - x;
-        base += s_scan[kPlanThreads - 1];
-        __syncthreads();
+        if (threadIdx.x == 0) a.ctl->total[d] = base;
     }
-    if (threadIdx.x == 0) a.ctl->total_items = base;
 }
 
 // Bundle B's next superstep in direction d: its work items.
@@ -705,10 +725,12 @@ gm_status gm_run_batch(gm_graph* const* graphs, int32_t n_graphs, const gm_query
         g_launches += 2;
         GM_CUDA_TRY(cudaGetLastError());
     }
-    // the superstep loop: WHILE { relax every bundle; finish; plan }
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_relax, kThreads, 0);
-    if (per_sm <= 0) per_sm = 1;
+    // the superstep loop: WHILE { pull bundles || push bundles; finish; plan }
+    int per_sm_pull = 0, per_sm_push = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_pull, batch_pull, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_push, batch_push, kThreads, 0);
+    per_sm_pull = std::max(per_sm_pull, 1);
+    per_sm_push = std::max(per_sm_push, 1);
     cudaGraph_t graph;
     GM_CUDA_TRY(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle handle;
@@ -731,14 +753,19 @@ gm_status gm_run_batch(gm_graph* const* graphs, int32_t n_graphs, const gm_query
         cudaKernelNodeParams kp = {};
         kp.blockDim = dim3(kThreads);
         kp.kernelParams = kargs;
-        cudaGraphNode_t n1 = nullptr, n2 = nullptr, n3 = nullptr;
-        kp.func = (void*)batch_relax;
-        kp.gridDim = dim3((unsigned)(per_sm * num_sms()));
-        e = cudaGraphAddKernelNode(&n1, body, nullptr, 0, &kp);
+        cudaGraphNode_t nr[2] = {nullptr, nullptr}, n2 = nullptr, n3 = nullptr;
+        kp.func = (void*)batch_pull;
+        kp.gridDim = dim3((unsigned)(per_sm_pull * num_sms()));
+        e = cudaGraphAddKernelNode(&nr[0], body, nullptr, 0, &kp);
+        if (e == cudaSuccess) {
+            kp.func = (void*)batch_push;
+            kp.gridDim = dim3((unsigned)(per_sm_push * num_sms()));
+            e = cudaGraphAddKernelNode(&nr[1], body, nullptr, 0, &kp);
+        }
         if (e == cudaSuccess) {
             kp.func = (void*)batch_finish;
             kp.gridDim = dim3((unsigned)(2 * num_sms()));
-            e = cudaGraphAddKernelNode(&n2, body, &n1, 1, &kp);
+            e = cudaGraphAddKernelNode(&n2, body, nr, 2, &kp);
         }
         if (e == cudaSuccess) {
             kp.func = (void*)batch_plan;
@@ -759,7 +786,7 @@ gm_status gm_run_batch(gm_graph* const* graphs, int32_t n_graphs, const gm_query
     GM_CUDA_TRY(cudaMemcpyAsync(its.data(), diters.p, sizeof(int32_t) * (size_t)n_queries, cudaMemcpyDeviceToHost, s));
     GM_CUDA_TRY(cudaMemcpyAsync(&hc, ctl.p, sizeof(BCtl), cudaMemcpyDeviceToHost, s));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
-    g_launches += 3ull * hc.t;
+    g_launches += 4ull * hc.t;
     if (iters_done)
         for (int32_t i = 0; i < n_queries; ++i) iters_done[i] = its[(size_t)i];
     if (hc.guard_hit) {
