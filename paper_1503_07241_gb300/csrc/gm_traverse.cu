@@ -958,8 +958,9 @@ __device__ __forceinline__ void pull_apply(const TravArgs& a, uint32_t t, WarpQ*
                     vb[k] = out_bin_of(a, vd[k]);
                 }
             }
-            warp_set_bits(a.bv[nxt], vc[k], wa[k]);
         }
+        // (no frontier bits: an SSSP superstep reads its frontier from the queues
+        // and the message array, never from the bitvector)
         enqueue_batch_pre<false>(a, wa, va, vb, vd, vin, nxt, acc);
     }
     flush_acc(a, acc, nxt, false, s_stat);
