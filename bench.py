@@ -290,8 +290,8 @@ def pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind):
 # DRAM bytes (read + write) per trav_pull_a launch in the bench's timed step, from
 # one ncu capture of this bench command; valid only for the kernel source it was
 # taken on (hash of the traversal source files at capture time).
-PULL_A_TRAFFIC = {"source_sha256": "28634c9d03b172bcf2e329895898f9e9bee3ece20119f124e449c1678a54e051",
-                  "bytes_per_launch": 365.21e6}
+PULL_A_TRAFFIC = {"source_sha256": "e922245f19fd00516721ffe893acf1184c5168ea4e3882d80a630e412e421ef5",
+                  "bytes_per_launch": 365.16e6}
 
 
 def _kernel_source_hash():
