@@ -178,6 +178,7 @@ struct gm_graph {
     // an option that changes their launch shapes or the workspace is freed
     cudaGraph_t loop_graph[2] = {nullptr, nullptr};
     cudaGraphExec_t loop_exec[2] = {nullptr, nullptr};
+    cudaGraphNode_t loop_params[2] = {nullptr, nullptr};  // the run-parameter node, set per gm_run
     gm::DevBuf reached_buf;          // counter of gm_get_scalar(GM_SCALAR_REACHED_EDGES)
     // results
     uint64_t tc_total = 0;

@@ -1556,12 +1556,18 @@ int finalize_grid(bool sssp) {
     } while (0)
 
 // Reset the control block and the frontier before seeding.
-gm_status reset_frontier(gm_graph* g) {
-    cudaStream_t s = g->stream;
+// Host side of a frontier reset (the bookkeeping that goes with reset_kernel).
+void reset_frontier_flags(gm_graph* g) {
     if (g->reached_pending) {  // seeds counted in the control block that is about to be cleared
         g->reached_valid = false;
         g->reached_pending = false;
     }
+    g->frontier_clean = true;
+    if (g->kind == GM_SSSP) g->msg_clean = true;
+}
+
+gm_status reset_frontier(gm_graph* g) {
+    cudaStream_t s = g->stream;
     TravWork w = work_layout(g);
     const int64_t n = g->n > 0 ? g->n : 1;
     const int64_t nwords = (n + 31) / 32;
@@ -1572,8 +1578,7 @@ gm_status reset_frontier(gm_graph* g) {
                                                (float)g->tune.sssp_pull_frac, (unsigned long long)g->m);
     g_launches++;
     LAUNCH_OK();
-    g->frontier_clean = true;
-    if (g->kind == GM_SSSP) g->msg_clean = true;
+    reset_frontier_flags(g);
     return GM_OK;
 }
 
@@ -1596,16 +1601,55 @@ gm_status build_loop_graph(gm_graph* g, bool sssp) {
         set_error("cudaGraphConditionalHandleCreate: %s", cudaGetErrorString(e));
         return GM_ERR_CUDA;
     }
+    // run parameters (set per run), then the loop, then the copy of the control
+    // block to the host and the frontier reset for the next run
+    cudaGraphNode_t pnode = nullptr;
+    {
+        TravCtlDev* cd = as<TravCtlDev>(g->ctl_buf);
+        int32_t mi = -1, dm = g->tune.direction;
+        float al = (float)g->tune.alpha, be = (float)g->tune.beta, fr = (float)g->tune.sssp_pull_frac;
+        unsigned long long mm = (unsigned long long)g->m;
+        int fresh = 0;
+        void* pargs[] = {&cd, &mi, &dm, &al, &be, &fr, &mm, &fresh};
+        cudaKernelNodeParams pp = {};
+        pp.func = (void*)ctl_params;
+        pp.gridDim = dim3(1);
+        pp.blockDim = dim3(1);
+        pp.kernelParams = pargs;
+        e = cudaGraphAddKernelNode(&pnode, graph, nullptr, 0, &pp);
+    }
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = handle;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
-    cudaGraphNode_t cnode;
-    e = cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp);
+    cudaGraphNode_t cnode = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, graph, &pnode, nullptr, 1, &cp);
+    cudaGraphNode_t copy_node = nullptr, reset_node = nullptr;
+    if (e == cudaSuccess)
+        e = cudaGraphAddMemcpyNode1D(&copy_node, graph, &cnode, 1, g->host_pinned, g->ctl_buf.p, sizeof(TravCtlDev),
+                                     cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) {
+        TravWork w = work_layout(g);
+        TravCtlDev* cd = as<TravCtlDev>(g->ctl_buf);
+        const int64_t n = g->n > 0 ? g->n : 1;
+        int64_t nwords = (n + 31) / 32, nn = n;
+        uint32_t* m0 = sssp ? w.msg[0] : nullptr;
+        uint32_t* m1 = sssp ? w.msg[1] : nullptr;
+        int32_t dm = g->tune.direction;
+        float al = (float)g->tune.alpha, be = (float)g->tune.beta, fr = (float)g->tune.sssp_pull_frac;
+        unsigned long long mm = (unsigned long long)g->m;
+        void* rargs[] = {&cd, &w.bv[0], &w.bv[1], &w.bv[2], &nwords, &m0, &m1, &nn, &dm, &al, &be, &fr, &mm};
+        cudaKernelNodeParams rp = {};
+        rp.func = (void*)reset_kernel;
+        rp.gridDim = dim3((unsigned)(num_sms() * 4));
+        rp.blockDim = dim3(256);
+        rp.kernelParams = rargs;
+        e = cudaGraphAddKernelNode(&reset_node, graph, &copy_node, 1, &rp);
+    }
     if (e != cudaSuccess) {
         cudaGraphDestroy(graph);
-        set_error("cudaGraphAddNode(conditional): %s", cudaGetErrorString(e));
+        set_error("superstep loop graph: %s", cudaGetErrorString(e));
         return GM_ERR_CUDA;
     }
     cudaGraph_t body = cp.conditional.phGraph_out[0];
@@ -1651,6 +1695,7 @@ gm_status build_loop_graph(gm_graph* g, bool sssp) {
     }
     g->loop_graph[slot] = graph;
     g->loop_exec[slot] = exec;
+    g->loop_params[slot] = pnode;
     return GM_OK;
 }
 
@@ -1732,17 +1777,35 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
         return reset_frontier(g);
     }
     TravCtlDev* hp = static_cast<TravCtlDev*>(g->host_pinned);
-    // parameters that may have changed since the frontier was reset
-    ctl_params<<<1, 1, 0, s>>>(as<TravCtlDev>(g->ctl_buf), max_iters, g->tune.direction, (float)g->tune.alpha,
-                               (float)g->tune.beta, (float)g->tune.sssp_pull_frac, (unsigned long long)g->m, 0);
-    g_launches++;
-    LAUNCH_OK();
     const bool host_loop = g->tune.loop_mode == 1 || g->tune.profile;
     if (!host_loop) {
+        // one graph: the run parameters, the superstep loop, the copy of the
+        // control block to hp and the frontier reset for the next run
         const int slot = sssp ? 1 : 0;
         if (!g->loop_exec[slot]) GM_TRY(build_loop_graph(g, sssp));
+        TravCtlDev* cd = as<TravCtlDev>(g->ctl_buf);
+        int32_t mi = max_iters, dm = g->tune.direction;
+        float al = (float)g->tune.alpha, be = (float)g->tune.beta, fr = (float)g->tune.sssp_pull_frac;
+        unsigned long long mm = (unsigned long long)g->m;
+        int fresh = 0;
+        void* pargs[] = {&cd, &mi, &dm, &al, &be, &fr, &mm, &fresh};
+        cudaKernelNodeParams pp = {};
+        pp.func = (void*)ctl_params;
+        pp.gridDim = dim3(1);
+        pp.blockDim = dim3(1);
+        pp.kernelParams = pargs;
+        GM_CUDA_TRY(cudaGraphExecKernelNodeSetParams(g->loop_exec[slot], g->loop_params[slot], &pp));
         GM_CUDA_TRY(cudaGraphLaunch(g->loop_exec[slot], s));
+        g_launches += 2;  // parameters and reset
+        g->reached_pending = false;  // seeds pending in the control block are in the copy
+        reset_frontier_flags(g);
     } else {
+        // parameters that may have changed since the frontier was reset
+        ctl_params<<<1, 1, 0, s>>>(as<TravCtlDev>(g->ctl_buf), max_iters, g->tune.direction,
+                                   (float)g->tune.alpha, (float)g->tune.beta, (float)g->tune.sssp_pull_frac,
+                                   (unsigned long long)g->m, 0);
+        g_launches++;
+        LAUNCH_OK();
         TravArgs a = make_args(g);
         const int pg = push_grid(), lg = sssp ? pull_grid() : pull_bu_grid(), fg = finalize_grid(sssp);
         cudaEvent_t ev0 = nullptr, ev1 = nullptr, evA = nullptr, evB = nullptr;
@@ -1807,11 +1870,13 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
         if (evA) cudaEventDestroy(evA);
         if (evB) cudaEventDestroy(evB);
     }
-    GM_CUDA_TRY(cudaMemcpyAsync(hp, g->ctl_buf.p, sizeof(TravCtlDev), cudaMemcpyDeviceToHost, s));
-    // the frontier reset for the next run goes into the stream behind that copy,
-    // before the wait: seeds pending in the control block are in the copy
-    g->reached_pending = false;
-    GM_TRY(reset_frontier(g));
+    if (host_loop) {
+        GM_CUDA_TRY(cudaMemcpyAsync(hp, g->ctl_buf.p, sizeof(TravCtlDev), cudaMemcpyDeviceToHost, s));
+        // the frontier reset for the next run goes into the stream behind that
+        // copy, before the wait: seeds pending in the control block are in the copy
+        g->reached_pending = false;
+        GM_TRY(reset_frontier(g));
+    }
     GM_CUDA_TRY(cudaStreamSynchronize(s));
     if (!host_loop) g_launches += 4ull * hp->c.loops;
     g->stats.supersteps = (int32_t)hp->c.iters_done;
