@@ -446,6 +446,27 @@ def paper_shapes(gm):
     return out
 
 
+def probe_sssp23(gm):
+    """One SSSP query on the RMAT-23 graph of --paper-shapes (source 4 of its
+    sample), superstep kernels issued from the host so that profilers see them."""
+    import torch
+    import synth
+    n, s, d = synth.rmat(23, 16, synth.RMAT_PARAMS["graph500"], synth.BASE_SEED + 23)
+    w = synth.edge_weights_u32(s, d, synth.BASE_SEED + 24)
+    srcs = synth.pick_sources(n, s, d, 8, seed=synth.BASE_SEED + 223)
+    g = gm.Graph(n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda(), torch.from_numpy(w.view(np.int32)).cuda())
+    del s, d, w
+    g.set_option(gm.GM_OPT_LOOP_MODE, 1)
+    g.program_set(gm.GM_SSSP)
+    g.set_active([int(srcs[4])])
+    it = g.run(-1)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": "sssp23", "n": n, "m": g.m, "source": int(srcs[4]), "supersteps": it,
+                      "pulls": g.scalar(gm.GM_SCALAR_PULL_STEPS)}), flush=True)
+    g.close()
+    return 0
+
+
 def extras(gm):
     """The other workloads, each timed outside the main timed region."""
     import torch
@@ -568,12 +589,12 @@ def main():
     ap.add_argument("--ablation", action="store_true",
                     help="after the timed steps, time every query alone under each engine configuration "
                          "of the ablation (one option changed at a time) and print that table instead")
-    ap.add_argument("--probe", choices=["bfs", "sssp", "ingest", "pagerank", "wpagerank", "triangles", "cf",
-                                        "components"],
+    ap.add_argument("--probe", choices=["bfs", "sssp", "sssp23", "ingest", "pagerank", "wpagerank", "triangles",
+                                        "cf", "components"],
                     help="a short command for kernel profilers: bfs/sssp build the workload graph and run "
-                         "one query from the first source with --host-loop semantics; the others build "
-                         "that extra workload and run it twice, the second time inside the NVTX range "
-                         "'probe'")
+                         "one query from the first source with --host-loop semantics (sssp23: the same on "
+                         "the RMAT-23 graph of --paper-shapes); the others build that extra workload and run "
+                         "it twice, the second time inside the NVTX range 'probe'")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -589,6 +610,11 @@ def main():
         ge.build_cuda_library()
         import paper_1503_07241_gb300 as gm
         return probe_other(gm, args.probe)
+    if args.probe == "sssp23":
+        import __graft_entry__ as ge
+        ge.build_cuda_library()
+        import paper_1503_07241_gb300 as gm
+        return probe_sssp23(gm)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))
