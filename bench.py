@@ -290,8 +290,8 @@ def pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind):
 # DRAM bytes (read + write) per trav_pull_a launch in the bench's timed step, from
 # one ncu capture of this bench command; valid only for the kernel source it was
 # taken on (hash of the traversal source files at capture time).
-PULL_A_TRAFFIC = {"source_sha256": "e922245f19fd00516721ffe893acf1184c5168ea4e3882d80a630e412e421ef5",
-                  "bytes_per_launch": 365.16e6}
+PULL_A_TRAFFIC = {"source_sha256": "71d8e9daf29f6afac47967a1d20fd8ff92cdd433b99da93c585d6786999c8691",
+                  "bytes_per_launch": 365.08e6}
 
 
 def _kernel_source_hash():
