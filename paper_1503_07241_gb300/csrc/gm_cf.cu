@@ -14,7 +14,12 @@
 // user; for K = 8, 16, 32, 64 each rating is handled by K/8 lanes with 8 factor
 // components each, so a warp has 32/(K/8) ratings in flight, other K spread the
 // components over the 32 lanes, one rating at a time) computes and stores e_uv and
-// accumulates sum_v e_uv p_v; an item pass over the CSC gathers the stored e_uv
+// accumulates sum_v e_uv p_v.  Item degrees are skewed, so for K = 8..64 the
+// factor rows of the most-rated items are first copied into each CTA's shared
+// memory (one 1024-thread CTA per SM; for K = 32, 1792 rows carrying about 57 %
+// of the ratings of the Zipf-shaped workload) and each rating's item is stored
+// as a code: its row's slot there, or -1 - the item, so the gathers of those
+// ratings read shared memory instead of L2; an item pass over the CSC gathers the stored e_uv
 // and accumulates sum_u e_uv p_u; an update kernel applies Eqs. 4-5 to every
 // vertex.  Chunks of one long row are combined with
 // float atomics.  Arithmetic in FP32 on CUDA cores: every product is one
@@ -249,6 +254,75 @@ __global__ void __launch_bounds__(kThreads) cf_item_pass_g(const int4* __restric
     }
 }
 
+// cf_user_pass_g with the factor rows of the hottest items in shared memory:
+// code[e] >= 0 is rating e's item row in s_hot, else the item is -1 - code[e].
+// The same values in the same order as cf_user_pass_g, so the same results.
+template <int L>
+__global__ void __launch_bounds__(1024, 1) cf_user_pass_hot(const int4* __restrict__ chunks, int64_t nchunks,
+                                                            const int32_t* __restrict__ code,
+                                                            const uint32_t* __restrict__ rating,
+                                                            const float* __restrict__ p,
+                                                            const int32_t* __restrict__ hot_ids, int32_t n_hot,
+                                                            float* __restrict__ ebuf, float* __restrict__ acc) {
+    constexpr int K = 8 * L, R = 32 / L, K4 = K / 4;
+    extern __shared__ float4 s_hot[];  // n_hot rows of K floats
+    for (int32_t i = threadIdx.x; i < n_hot * K4; i += blockDim.x) {
+        const int32_t r = i / K4;
+        s_hot[i] = __ldg(reinterpret_cast<const float4*>(p) + (int64_t)hot_ids[r] * K4 + (i - r * K4));
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, grp = lane / L, sub = lane % L;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = gwarp; c < nchunks; c += nwarps) {
+        const int4 ch = chunks[c];
+        const int32_t u = ch.x;
+        float pu[8], ac[8];
+        load8f<L>(p, (int64_t)u * K + 8 * sub, pu);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ac[j] = 0.0f;
+        for (int32_t e0 = ch.y; e0 < ch.z; e0 += R) {
+            const int32_t e = e0 + grp;
+            const bool ok = e < ch.z;
+            const int32_t cd = ok ? __ldg(code + e) : -1 - u;  // a valid row to read; its terms are dropped
+            const float g = ok ? (float)__ldg(rating + e) : 0.0f;
+            float pv[8];
+            if (cd >= 0) {
+                const float4 a = s_hot[cd * K4 + 2 * sub], b = s_hot[cd * K4 + 2 * sub + 1];
+                pv[0] = a.x; pv[1] = a.y; pv[2] = a.z; pv[3] = a.w;
+                pv[4] = b.x; pv[5] = b.y; pv[6] = b.z; pv[7] = b.w;
+            } else {
+                load8f<L>(p, (int64_t)(-1 - cd) * K + 8 * sub, pv);
+            }
+            float part = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) part += pu[j] * pv[j];
+#pragma unroll
+            for (int o = L / 2; o >= 1; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+            const float err = ok ? g - part : 0.0f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) ac[j] += err * pv[j];
+            if (ok && sub == 0) ebuf[e] = err;
+        }
+        group_reduce8<L>(ac);
+        if (grp == 0)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) atomicAdd(&acc[(int64_t)u * K + 8 * sub + j], ac[j]);
+    }
+}
+
+// code[e] = slot of rating e's item among the staged rows, or -1 - the item.
+__global__ void cf_codes(const int32_t* __restrict__ col, int64_t m, const int32_t* __restrict__ slot_of,
+                         int32_t* __restrict__ code) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = col[e];
+        const int32_t s = slot_of[v];
+        code[e] = s >= 0 ? s : -1 - v;
+    }
+}
+
+constexpr int kHotSmem = 224 * 1024;  // shared memory for staged item rows per CTA
+
 // p <- p + gamma (acc - lambda p); acc <- 0
 __global__ void cf_update(float* __restrict__ p, float* __restrict__ acc, int64_t count, float gamma, float lambda) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
@@ -278,6 +352,8 @@ std::vector<int4> make_chunks(const std::vector<int32_t>& ptr, int64_t r0, int64
 
 struct CfState {
     DevBuf user_chunks, item_chunks, ebuf, acc, scalar;
+    DevBuf hot_ids, code;     // staged item rows (grouped K): their vertex ids; per-rating codes
+    int32_t n_hot = 0;
     int64_t n_user_chunks = 0, n_item_chunks = 0;
 };
 
@@ -307,7 +383,7 @@ gm_status by_group(int K, F f) {
 void cf_release(gm_graph* g) {
     CfState* c = static_cast<CfState*>(g->cf);
     if (!c) return;
-    DevBuf* bufs[] = {&c->user_chunks, &c->item_chunks, &c->ebuf, &c->acc, &c->scalar};
+    DevBuf* bufs[] = {&c->user_chunks, &c->item_chunks, &c->ebuf, &c->acc, &c->scalar, &c->hot_ids, &c->code};
     for (DevBuf* b : bufs) dev_free(*b, g->stream);
     delete c;
     g->cf = nullptr;
@@ -335,6 +411,31 @@ gm_status cf_prepare(gm_graph* g) {
         GM_CUDA_TRY(cudaMemcpyAsync(c->user_chunks.p, uc.data(), sizeof(int4) * uc.size(), cudaMemcpyHostToDevice, s));
     if (!ic.empty())
         GM_CUDA_TRY(cudaMemcpyAsync(c->item_chunks.p, ic.data(), sizeof(int4) * ic.size(), cudaMemcpyHostToDevice, s));
+    // the most-rated items' rows are staged in shared memory by the user pass
+    if (grouped(K) && g->m > 0 && n > g->n_left) {
+        const int64_t n_items = n - g->n_left;
+        const int32_t cap = (int32_t)std::min<int64_t>(n_items, kHotSmem / (int64_t)(sizeof(float) * K));
+        std::vector<int32_t> items((size_t)n_items);
+        for (int64_t i = 0; i < n_items; ++i) items[(size_t)i] = (int32_t)(g->n_left + i);
+        std::stable_sort(items.begin(), items.end(), [&](int32_t a, int32_t b) {
+            return cp[(size_t)a + 1] - cp[(size_t)a] > cp[(size_t)b + 1] - cp[(size_t)b];
+        });
+        items.resize((size_t)cap);
+        std::vector<int32_t> slot_of((size_t)n, -1);
+        for (int32_t i = 0; i < cap; ++i) slot_of[(size_t)items[(size_t)i]] = i;
+        DevBuf dslot;
+        GM_TRY(dev_alloc(c->hot_ids, sizeof(int32_t) * (size_t)std::max<int32_t>(cap, 1), s));
+        GM_TRY(dev_alloc(c->code, sizeof(int32_t) * (size_t)g->m, s));
+        GM_TRY(dev_alloc(dslot, sizeof(int32_t) * (size_t)n, s));
+        GM_CUDA_TRY(cudaMemcpyAsync(c->hot_ids.p, items.data(), sizeof(int32_t) * (size_t)cap, cudaMemcpyHostToDevice, s));
+        GM_CUDA_TRY(cudaMemcpyAsync(dslot.p, slot_of.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s));
+        cf_codes<<<num_sms() * 8, 256, 0, s>>>(as<int32_t>(g->col), g->m, as<int32_t>(dslot), as<int32_t>(c->code));
+        g_launches++;
+        GM_CUDA_TRY(cudaGetLastError());
+        GM_CUDA_TRY(cudaStreamSynchronize(s));  // the host copies above come from stack vectors
+        dev_free(dslot, s);
+        c->n_hot = cap;
+    }
     GM_TRY(dev_alloc(c->ebuf, sizeof(float) * (g->m > 0 ? g->m : 1), s));
     GM_TRY(dev_alloc(c->acc, sizeof(float) * (n > 0 ? n : 1) * K, s));
     GM_TRY(dev_alloc(c->scalar, sizeof(double) * 2, s));
@@ -363,7 +464,19 @@ gm_status cf_run(gm_graph* g, int32_t iters, int32_t* iters_done) {
         if (grouped(K)) {
             GM_TRY(by_group(K, [&](auto lc) -> gm_status {
                 constexpr int L = decltype(lc)::value;
-                if (c->n_user_chunks > 0) {
+                if (c->n_user_chunks > 0 && c->n_hot > 0) {
+                    const size_t smem = sizeof(float) * 8 * L * (size_t)c->n_hot;
+                    static const bool attr = [] {
+                        cudaFuncSetAttribute(cf_user_pass_hot<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kHotSmem);
+                        return true;
+                    }();
+                    (void)attr;
+                    cf_user_pass_hot<L><<<num_sms(), 1024, smem, s>>>(
+                        as<int4>(c->user_chunks), c->n_user_chunks, as<int32_t>(c->code), as<uint32_t>(g->w), p,
+                        as<int32_t>(c->hot_ids), c->n_hot, as<float>(c->ebuf), as<float>(c->acc));
+                    g_launches++;
+                } else if (c->n_user_chunks > 0) {
                     cf_user_pass_g<L><<<grid_cf(), kThreads, 0, s>>>(as<int4>(c->user_chunks), c->n_user_chunks,
                                                                       as<int32_t>(g->col), as<uint32_t>(g->w), p,
                                                                       as<float>(c->ebuf), as<float>(c->acc), nullptr);
