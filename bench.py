@@ -101,12 +101,33 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(pw) if pw else None}
 
 
+def rank_sources(n, s, d, rank, count=N_QUERIES):
+    """Each rank's own BFS and SSSP sources (a seed per rank): the ranks run
+    independent queries, so the job's work grows with the ranks (weak scaling)."""
+    import synth
+    srcs = synth.pick_sources(n, s, d, 2 * count, seed=synth.BASE_SEED + 100 + rank)
+    return srcs[:count], srcs[count:2 * count]
+
+
+def combine_ranks(dist, t, edges, device):
+    """The whole job's numbers from every rank's: the slowest rank's time and the
+    edges of all ranks.  dist is torch.distributed (or None for one process)."""
+    if not dist:
+        return t, edges
+    import torch
+    tt = torch.tensor([float(t)], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ee = torch.tensor([float(edges)], device=device, dtype=torch.float64)
+    dist.all_reduce(ee)
+    return float(tt.item()), float(ee.item())
+
+
 def make_workload(rank):
     import synth
     n, s, d = synth.rmat(SCALE, EDGE_FACTOR, synth.RMAT_PARAMS["graph500"], synth.BASE_SEED + 1)
     w = synth.edge_weights_u32(s, d, synth.BASE_SEED + 2)
-    srcs = synth.pick_sources(n, s, d, 2 * N_QUERIES, seed=synth.BASE_SEED + 100 + rank)
-    return n, s, d, w, srcs[:N_QUERIES], srcs[N_QUERIES:2 * N_QUERIES]
+    bfs_src, sssp_src = rank_sources(n, s, d, rank)
+    return n, s, d, w, bfs_src, sssp_src
 
 
 def run_queries(gm, g, bfs_src, sssp_src, src_dev, out_host=None):
@@ -702,15 +723,7 @@ def main():
         torch.cuda.nvtx.range_pop()
     launches = gm.kernel_launch_count() - launches0
     ms = ev0.elapsed_time(ev1)
-    tmax = ms
-    edges_all = edges
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
-        e = torch.tensor([float(edges)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(e)
-        edges_all = float(e.item())
+    tmax, edges_all = combine_ranks(dist, ms, edges, "cuda")
     value = edges_all / (tmax / 1e3) / 1e9
 
     peak, peak_kind = _peaks()
@@ -742,14 +755,7 @@ def main():
             e_edges += run_queries(gm, g2, bfs_src, sssp_src, (None, None), out_host=out)
             g2.close()
         barrier()
-        e_t = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e_t], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_t = float(t.item())
-            e = torch.tensor([float(e_edges)], device="cuda", dtype=torch.float64)
-            dist.all_reduce(e)
-            e_edges = float(e.item())
+        e_t, e_edges = combine_ranks(dist, time.perf_counter() - t0, e_edges, "cuda")
         e2e = {"value": e_edges / e_t / 1e9, "unit": "GTEPS",
                "h2d_bytes_per_step": int(s.nbytes + d.nbytes + w.nbytes + 8 * N_QUERIES),
                "d2h_bytes_per_step": int(2 * N_QUERIES * 4 * n), "steps": args.e2e_steps,
