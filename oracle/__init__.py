@@ -12,7 +12,8 @@ Every function follows a passage of the paper (Sundaram et al., VLDB 2015):
 Algorithm 1 (generalized SPMV) inside Algorithm 2 (Run_Graph_Program) for
 PageRank (Eq. 1), BFS (Section 3.II) and SSSP (Section 3.V, appendix program);
 the two triangle-counting programs of Section 4.2; Eqs. 3-5 for collaborative
-filtering; and weighted PageRank with its reverse-mode gradient (an added form
+filtering (gradient descent, and stochastic gradient descent in a stratified
+order); and weighted PageRank with its reverse-mode gradient (an added form
 with no counterpart in the paper; pinned by finite differences in the tests).
 """
 from __future__ import annotations
@@ -80,6 +81,7 @@ def _load():
         "or_cf_loss": ([P, i32, f64, P], f64),
         "or_cf_gd": ([P, i32, f64, f64, i64, P, P], i64),
         "or_cf_vertex_step": ([P, i32, f64, f64, P, i64, P], None),
+        "or_cf_sgd": ([P, i64, i32, f64, f64, i64, i64, P], i64),
         "or_wpr_forward": ([P, P, f64, i64, P, P], f64),
         "or_wpr_gradient": ([P, P, f64, i64, P, P], f64),
     }
@@ -186,6 +188,14 @@ class Graph:
         trace = np.empty(iters + 1, np.float64)
         _load().or_cf_gd(self._h, K, lam, gamma, iters, _p(p), _p(trace))
         return p, trace
+
+    def cf_sgd(self, K, lam, gamma, epochs, n_left, P, p0):
+        """Stochastic gradient descent (Section 3.III) for `epochs` epochs in the
+        stratified order of P blocks (see or_cf_sgd); returns the factors."""
+        p = np.array(p0, dtype=np.float64, copy=True).reshape(self.n, K)
+        if _load().or_cf_sgd(self._h, n_left, K, lam, gamma, epochs, P, _p(p)) < 0:
+            raise ValueError("or_cf_sgd: bad argument")
+        return p
 
     def cf_vertex_step(self, K, lam, gamma, p, v):
         p = np.ascontiguousarray(p, dtype=np.float64)

@@ -14,7 +14,8 @@
  *    the out-edges of each present column), with FP64 vertex state.
  *  - PageRank follows Eq. 1, BFS the distance update of Section 3.II, SSSP the
  *    min-plus update of Section 3.V and the appendix program, triangle counting
- *    the two vertex programs of Section 4.2, collaborative filtering Eqs. 3-5,
+ *    the two vertex programs of Section 4.2, collaborative filtering Eqs. 3-5
+ *    (gradient descent, and stochastic gradient descent in a stratified order),
  *    and weighted PageRank (an added form) Eq. 1 with row-normalised edge
  *    weights plus its reverse-mode derivative.
  *
@@ -685,6 +686,70 @@ OR_EXPORT void or_cf_vertex_step(const or_graph* G, int32_t K, double lambda, do
         for (int32_t k = 0; k < K; ++k) out[k] += err * other[k];
     }
     for (int32_t k = 0; k < K; ++k) out[k] = p[v * K + k] + gamma * (out[k] - lambda * p[v * K + k]);
+}
+
+/*
+ * Collaborative filtering by stochastic gradient descent (Section 3.III: the
+ * updates of Eqs. 4-5 without their sums, applied one rating at a time).  For a
+ * rating (u, v) with value G_uv both factor vectors move from their values
+ * before that rating:
+ *   e   = G_uv - p_u . p_v
+ *   p_u = p_u + gamma (e p_v - lambda p_u)
+ *   p_v = p_v + gamma (e p_u - lambda p_v)
+ * Order of the ratings.  Section 3.III asks for a random order; this oracle
+ * takes the stratified order of distributed SGD (Gemulla, Nijkamp, Haas and
+ * Sismanis, KDD 2011): user u lies in block u mod P, item v in block
+ * (v - n_left) mod P, and a rating lies in stratum
+ *   s = (item block - user block) mod P.
+ * One epoch visits the strata 0..P-1 in turn; inside a stratum the user blocks
+ * 0..P-1 in turn; inside a block the ratings in (user, item) order, the order of
+ * the edge list.  `p` (n*K, row-major) holds the start factors on entry and the
+ * result on return.  Returns the epochs run, or -1 for a bad argument (users
+ * must be sources in [0, n_left) and items destinations in [n_left, n)).
+ */
+typedef struct { uint64_t key; int64_t e; } or_sgd_slot;
+
+static int or_sgd_slot_cmp(const void* a, const void* b) {
+    const or_sgd_slot* x = (const or_sgd_slot*)a;
+    const or_sgd_slot* y = (const or_sgd_slot*)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    if (x->e != y->e) return x->e < y->e ? -1 : 1;
+    return 0;
+}
+
+OR_EXPORT int64_t or_cf_sgd(const or_graph* G, int64_t n_left, int32_t K, double lambda, double gamma,
+                            int64_t epochs, int64_t P, double* p) {
+    const int64_t m = G->m;
+    if (P < 1 || K < 1 || epochs < 0 || n_left <= 0 || n_left >= G->n) return -1;
+    for (int64_t e = 0; e < m; ++e)
+        if (G->src[e] >= n_left || G->dst[e] < n_left) return -1;
+    or_sgd_slot* order = (or_sgd_slot*)malloc(sizeof(or_sgd_slot) * (size_t)(m > 0 ? m : 1));
+    double* pu_old = (double*)malloc(sizeof(double) * (size_t)K);
+    if (!order || !pu_old) { free(order); free(pu_old); return -1; }
+    for (int64_t e = 0; e < m; ++e) {
+        const uint64_t bu = (uint64_t)G->src[e] % (uint64_t)P;
+        const uint64_t bv = (uint64_t)(G->dst[e] - n_left) % (uint64_t)P;
+        const uint64_t stratum = (bv + (uint64_t)P - bu) % (uint64_t)P;
+        order[e].key = stratum * (uint64_t)P + bu;
+        order[e].e = e;
+    }
+    qsort(order, (size_t)m, sizeof(or_sgd_slot), or_sgd_slot_cmp);
+    for (int64_t t = 0; t < epochs; ++t) {
+        for (int64_t i = 0; i < m; ++i) {
+            const int64_t e = order[i].e;
+            double* pu = p + (int64_t)G->src[e] * K;
+            double* pv = p + (int64_t)G->dst[e] * K;
+            double dot = 0.0;
+            for (int32_t k = 0; k < K; ++k) dot += pu[k] * pv[k];
+            const double err = G->val[e] - dot;
+            for (int32_t k = 0; k < K; ++k) pu_old[k] = pu[k];
+            for (int32_t k = 0; k < K; ++k) pu[k] = pu[k] + gamma * (err * pv[k] - lambda * pu[k]);
+            for (int32_t k = 0; k < K; ++k) pv[k] = pv[k] + gamma * (err * pu_old[k] - lambda * pv[k]);
+        }
+    }
+    free(order);
+    free(pu_old);
+    return epochs;
 }
 
 /* ---- Weighted PageRank (added form) ----

@@ -379,6 +379,132 @@ def test_cf_init_normal_moments():
     assert np.array_equal(p[:64], oracle.cf_init(2, 32, seed=1).ravel())
 
 
+# ---------------------------------------------------------------- CF by SGD
+@pytest.mark.parametrize("case", range(2))
+def test_cf_sgd_golden_hand_steps(case):
+    gd = _golden("cf_sgd_tiny.json")["cases"][case]
+    g = oracle.Graph(gd["n"], np.array(gd["src"], np.int32), np.array(gd["dst"], np.int32),
+                     np.array(gd["rating"], np.uint32))
+    p0 = np.array(gd["p0"]).reshape(gd["n"], gd["K"])
+    p1 = g.cf_sgd(gd["K"], gd["lambda"], gd["gamma"], 1, gd["n_left"], gd["P"], p0)
+    np.testing.assert_allclose(p1.ravel(), gd["p1"], rtol=0, atol=1e-15)
+
+
+def _perfect_matching(rng, n_pairs):
+    u = np.arange(n_pairs, dtype=np.int32)
+    v = (n_pairs + rng.permutation(n_pairs)).astype(np.int32)
+    r = rng.integers(1, 6, n_pairs).astype(np.uint32)
+    return u, v, r
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 7, 64])
+def test_cf_sgd_epoch_on_a_perfect_matching_is_one_gd_step(P):
+    """When every user and every item has exactly one rating, no two updates
+    touch the same vector: one SGD epoch in any order is one Jacobi GD step of
+    Eqs. 3-5 (regulariser once per vertex = once per rating)."""
+    rng = np.random.default_rng(21)
+    n_pairs, K = 40, 5
+    u, v, r = _perfect_matching(rng, n_pairs)
+    g = oracle.Graph(2 * n_pairs, u, v, r)
+    p0 = rng.normal(0, 0.5, (2 * n_pairs, K))
+    gd, _ = g.cf_gd(K, 0.05, 0.02, 1, p0)
+    sgd = g.cf_sgd(K, 0.05, 0.02, 1, n_pairs, P, p0)
+    np.testing.assert_allclose(sgd, gd, rtol=1e-14, atol=1e-15)
+
+
+def test_cf_sgd_epoch_is_gd_step_to_first_order_in_gamma():
+    """With lambda = 0, an epoch applies every rating's gradient once: it differs
+    from one GD step by O(gamma^2) (a dropped or doubled rating would leave an
+    O(gamma) gap)."""
+    rng = np.random.default_rng(22)
+    nu, ni, K = 12, 6, 4
+    u, v, r = _bipartite(rng, nu, ni, 50)
+    g = oracle.Graph(nu + ni, u, v, r)
+    p0 = rng.normal(0, 0.5, (nu + ni, K))
+    gaps = []
+    for gamma in (1e-3, 5e-4, 2.5e-4):
+        gd, _ = g.cf_gd(K, 0.0, gamma, 1, p0)
+        sgd = g.cf_sgd(K, 0.0, gamma, 1, nu, 5, p0)
+        gaps.append(np.abs(sgd - gd).max())
+    assert gaps[0] > 0
+    for a, b in zip(gaps, gaps[1:]):
+        assert 3.5 < a / b < 4.5
+
+
+@pytest.mark.parametrize("P", [3, 5])
+def test_cf_sgd_visits_ratings_in_the_stratified_order(P):
+    """Every user rates one item and items are shared, so the result depends on
+    the order.  The order is enumerated here by nested loops (stratum, then user
+    block, then edge-list position); relabelling the users in that order and
+    running with P = 1 (plain edge-list order) must give the same factors."""
+    rng = np.random.default_rng(25)
+    nu, ni, K = 40, 6, 3
+    u = np.arange(nu, dtype=np.int32)
+    v = rng.integers(nu, nu + ni, nu).astype(np.int32)
+    r = rng.integers(1, 6, nu).astype(np.uint32)
+    g = oracle.Graph(nu + ni, u, v, r)
+    p0 = rng.normal(0, 0.5, (nu + ni, K))
+    want = g.cf_sgd(K, 0.05, 0.05, 1, nu, P, p0)
+    order = [e for s in range(P) for b in range(P) for e in range(nu)
+             if u[e] % P == b and (v[e] - nu) % P == (b + s) % P]
+    assert sorted(order) == list(range(nu))
+    label = np.empty(nu, np.int32)
+    label[order] = np.arange(nu)  # the rating of user order[i] becomes user i's
+    g2 = oracle.Graph(nu + ni, label, v, r)
+    p0_2 = p0.copy()
+    p0_2[label] = p0[:nu]
+    got = g2.cf_sgd(K, 0.05, 0.05, 1, nu, 1, p0_2)
+    np.testing.assert_array_equal(got[label], want[:nu])
+    np.testing.assert_array_equal(got[nu:], want[nu:])
+    assert not np.array_equal(want, g.cf_sgd(K, 0.05, 0.05, 1, nu, 1, p0))
+
+
+@pytest.mark.parametrize("P", [2, 5, 16])
+def test_cf_sgd_strata_blocks_are_disjoint(P):
+    """The blocks of one stratum share no user and no item, so the blocks of a
+    stratum may run at the same time and give the serial order's result."""
+    rng = np.random.default_rng(23)
+    nu, ni = 50, 30
+    u, v, _ = _bipartite(rng, nu, ni, 400)
+    bu, bv = u % P, (v - nu) % P
+    stratum = (bv - bu) % P
+    for s in range(P):
+        sel = stratum == s
+        for b in range(P):
+            mine = sel & (bu == b)
+            other = sel & (bu != b)
+            assert not np.isin(u[mine], u[other]).any()
+            assert not np.isin(v[mine], v[other]).any()
+
+
+def test_cf_sgd_fits_a_rank_one_matrix():
+    """Fully observed rank-1 ratings G_uv = a_u b_v, K = 1, lambda = 0: SGD at a
+    small step drives the Eq. 2 loss towards 0."""
+    a = np.array([1, 2, 3, 2])
+    b = np.array([2, 1, 3])
+    uu, vv = np.meshgrid(np.arange(4), np.arange(3), indexing="ij")
+    g = oracle.Graph(7, uu.ravel().astype(np.int32), (4 + vv.ravel()).astype(np.int32),
+                     (a[uu] * b[vv]).ravel().astype(np.uint32))
+    p0 = np.full((7, 1), 1.0)
+    loss0 = g.cf_loss(1, 0.0, p0)
+    p = g.cf_sgd(1, 0.0, 0.01, 400, 4, 3, p0)
+    assert g.cf_loss(1, 0.0, p) < 1e-6 * loss0
+
+
+def test_cf_sgd_epochs_compose_and_arguments_are_checked():
+    rng = np.random.default_rng(24)
+    nu, ni, K = 10, 8, 3
+    u, v, r = _bipartite(rng, nu, ni, 60)
+    g = oracle.Graph(nu + ni, u, v, r)
+    p0 = rng.normal(0, 0.3, (nu + ni, K))
+    two = g.cf_sgd(K, 0.05, 0.01, 2, nu, 4, p0)
+    np.testing.assert_array_equal(two, g.cf_sgd(K, 0.05, 0.01, 1, nu, 4, g.cf_sgd(K, 0.05, 0.01, 1, nu, 4, p0)))
+    with pytest.raises(ValueError):
+        g.cf_sgd(K, 0.05, 0.01, 1, nu, 0, p0)
+    with pytest.raises(ValueError):
+        g.cf_sgd(K, 0.05, 0.01, 1, nu - 1, 4, p0)  # a user would be an item
+
+
 # ---------------------------------------------------------------- weighted PageRank
 @pytest.mark.parametrize("seed", range(3))
 def test_wpr_gradient_matches_central_differences(seed):
