@@ -383,6 +383,41 @@ def case_components(gm, synth):
     return g, lambda: (g.program_set(gm.GM_CONNECTED_COMPONENTS), g.run(-1))
 
 
+def cf_sgd_summary(gm, g, ms_epoch):
+    """One SGD epoch's figures.  The ratings of one item are serial in every order
+    that reproduces serial SGD, so an epoch takes at least (ratings of the
+    most-rated item) x (latency of one dependent update): chain_ns_per_update is
+    the epoch time divided by that chain."""
+    _, in_deg = g.degrees()
+    chain = int(in_deg.max())
+    return {"ms_per_epoch": ms_epoch, "ratings": g.m, "strata": g.scalar(gm.GM_SCALAR_CF_STRATA),
+            "ratings_per_s": g.m / (ms_epoch / 1e3), "longest_item_chain": chain,
+            "chain_ns_per_update": ms_epoch * 1e6 / max(chain, 1), "bound": "latency (longest item chain)",
+            "loss": g.scalar(gm.GM_SCALAR_CF_LOSS)}
+
+
+def probe_cf_sgd(gm):
+    """SGD on the 100M-rating workload for several strata counts: ms per epoch
+    (two timed epochs after one warm-up epoch each)."""
+    import torch
+    import synth
+    g, _ = case_cf(gm, synth)
+    ev0, ev1 = _events()
+    rows = []
+    for P in (128, 256, 512, 1024, 2048):
+        g.program_set(gm.GM_CF_SGD, K=32, lam=0.05, gamma=1e-3, init_sigma=0.1, seed=5, cf_strata=P)
+        g.run(1)
+        torch.cuda.synchronize()
+        ev0.record()
+        g.run(2)
+        ev1.record()
+        torch.cuda.synchronize()
+        rows.append(cf_sgd_summary(gm, g, ev0.elapsed_time(ev1) / 2))
+    print(json.dumps({"probe": "cf_sgd", "sweep": rows}), flush=True)
+    g.close()
+    return 0
+
+
 def probe_other(gm, name):
     """One warm-up run, then one run inside the NVTX range "probe" (for profilers)."""
     import torch
@@ -585,6 +620,11 @@ def extras(gm):
         out["cf_100M_k32"] = {"ms_10_iters": ms, "ratings": g.m,
                               "ratings_per_s": 10 * g.m / (ms / 1e3),
                               "gflops": 10 * g.m * 6 * 32 / (ms / 1e3) / 1e9}
+        # the same ratings by stochastic gradient descent, 3 epochs in the default strata
+        g.program_set(gm.GM_CF_SGD, K=32, lam=0.05, gamma=1e-3, init_sigma=0.1, seed=5)
+        g.run(1)
+        ms, _ = timed(lambda: g.run(3))
+        out["cf_sgd_100M_k32"] = cf_sgd_summary(gm, g, ms / 3)
         g.close()
     except Exception as e:  # pragma: no cover
         out["cf_100M_k32"] = {"error": str(e)}
@@ -611,11 +651,12 @@ def main():
                     help="after the timed steps, time every query alone under each engine configuration "
                          "of the ablation (one option changed at a time) and print that table instead")
     ap.add_argument("--probe", choices=["bfs", "sssp", "sssp23", "ingest", "pagerank", "wpagerank", "triangles",
-                                        "cf", "components"],
+                                        "cf", "components", "cf_sgd"],
                     help="a short command for kernel profilers: bfs/sssp build the workload graph and run "
                          "one query from the first source with --host-loop semantics (sssp23: the same on "
                          "the RMAT-23 graph of --paper-shapes); the others build that extra workload and run "
-                         "it twice, the second time inside the NVTX range 'probe'")
+                         "it twice, the second time inside the NVTX range 'probe'; cf_sgd times SGD epochs "
+                         "of the CF workload for several strata counts")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -636,6 +677,11 @@ def main():
         ge.build_cuda_library()
         import paper_1503_07241_gb300 as gm
         return probe_sssp23(gm)
+    if args.probe == "cf_sgd":
+        import __graft_entry__ as ge
+        ge.build_cuda_library()
+        import paper_1503_07241_gb300 as gm
+        return probe_cf_sgd(gm)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))

@@ -114,11 +114,19 @@ typedef enum gm_program_kind {
     GM_SSSP = 2,            /* Section 3.V and the appendix program */
     GM_TRIANGLE_COUNT = 3,  /* Section 3.IV, two vertex programs (Section 4.2) */
     GM_CF = 4,              /* Section 3.III, Eqs. 2-5, gradient descent */
-    GM_CONNECTED_COMPONENTS = 5  /* not one of the paper's programs: label propagation written with the
+    GM_CONNECTED_COMPONENTS = 5, /* not one of the paper's programs: label propagation written with the
                                     user-program API of graphmat_program.cuh (Section 4's four functions);
                                     label(v) = min(label(v), labels received), labels start at the vertex
                                     id, every vertex active at the start; uint32 labels.  On a symmetrised
                                     graph the result is the smallest id of each connected component. */
+    GM_CF_SGD = 6           /* Section 3.III, stochastic gradient descent: Eqs. 4-5 without their
+                               sums, one rating at a time, each from the factors before that rating.
+                               Order (Section 3.III asks for a random one): the stratified order of
+                               distributed SGD -- user u in block u mod P, item v in block
+                               (v - n_left) mod P, rating (u, v) in stratum (item block - user block)
+                               mod P; an epoch runs strata 0..P-1, in a stratum user blocks 0..P-1,
+                               in a block the ratings in (user, item) order.  gm_run(g, E) runs E
+                               epochs.  Same state, parameters and loss as GM_CF, plus cf_strata. */
 } gm_program_kind;
 
 typedef struct gm_program_params {
@@ -130,6 +138,9 @@ typedef struct gm_program_params {
     double gamma;          /* CF step size of Eqs. 4, 5 */
     double init_sigma;     /* CF initial factors ~ N(0, init_sigma) */
     uint64_t seed;         /* CF initial-factor seed (counter-based SplitMix64 + Box-Muller) */
+    int32_t cf_strata;     /* GM_CF_SGD: blocks per side P of the stratified order, 1..4096; 0 = about
+                              sqrt(ratings) / 10 rounded to a power of two (GM_SCALAR_CF_STRATA
+                              reads the value used) */
 } gm_program_params;
 
 /*
@@ -140,7 +151,11 @@ typedef struct gm_program_params {
  * (except PageRank and CF, where all vertices are active every superstep).
  * `params` may be NULL for BFS, SSSP and triangle counting.
  * SSSP needs a GM_W_U32 graph (an unweighted graph uses weight 1); CF needs
- * n_left > 0 and GM_W_U32 ratings.
+ * n_left > 0 and GM_W_U32 ratings; GM_CF_SGD also needs every rating to go from
+ * a user [0, n_left) to an item [n_left, n) (else GM_ERR_INVALID_ARG) and fewer
+ * than 2^32 ratings.  GM_CF_SGD sorts the ratings into the stratified order here
+ * (device memory: 16 bytes per rating kept, about 24 more during the sort, and
+ * 4 (P^2 + 1) bytes of block pointers).
  */
 GM_API gm_status gm_program_set(gm_graph* g, int32_t kind, const gm_program_params* params);
 
@@ -184,7 +199,7 @@ GM_API gm_status gm_set_active(gm_graph* g, const int32_t* vertices, int64_t cou
  * gm_run -- Algorithm 2: run supersteps until no vertex is active or
  * `max_iters` supersteps have run (max_iters = -1: until no vertex is active, as
  * run_graph_program(..., -1, ...) in the appendix).  PageRank and CF run exactly
- * max_iters >= 0 supersteps.  Triangle counting runs its two programs and
+ * max_iters >= 0 supersteps (GM_CF_SGD: epochs).  Triangle counting runs its two programs and
  * ignores max_iters.  iters_done (may be NULL) receives the number of supersteps
  * executed, counting the final one that found no active vertex.
  * The call synchronises the stream.
@@ -193,7 +208,7 @@ GM_API gm_status gm_run(gm_graph* g, int32_t max_iters, int32_t* iters_done);
 
 /*
  * Copy the vertex property array out: BFS/SSSP uint32[n], PageRank float[n],
- * triangle counting uint64[n] (triangles incident to each vertex), CF float[n*K]
+ * triangle counting uint64[n] (triangles incident to each vertex), CF (both forms) float[n*K]
  * row-major.  `bytes` must equal that size.
  */
 GM_API gm_status gm_get_vertex_state(gm_graph* g, void* dst, int64_t bytes, int dst_is_device);
@@ -213,9 +228,10 @@ enum {
     GM_SCALAR_RELAX_MS = 8,       /* double: profile mode, summed superstep-kernel time (CUDA events) */
     GM_SCALAR_RELAX_LAUNCHES = 9, /* int32: profile mode, relax-kernel launches timed */
     GM_SCALAR_PROCESSED_VERTICES = 10, /* int64: vertices whose edge lists the relax kernels read */
-    GM_SCALAR_PULL_WEIGHT_BYTES = 11   /* int32: bytes per in-edge weight the SSSP pull reads: 1 when
+    GM_SCALAR_PULL_WEIGHT_BYTES = 11,  /* int32: bytes per in-edge weight the SSSP pull reads: 1 when
                                           every uint32 weight is below 256 (a one-byte copy is kept),
                                           4 otherwise, 0 for an unweighted graph; set at creation */
+    GM_SCALAR_CF_STRATA = 12           /* int32: blocks per side P of the GM_CF_SGD order in use */
 };
 GM_API gm_status gm_get_scalar(gm_graph* g, int32_t which, void* out);
 

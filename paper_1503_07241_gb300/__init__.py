@@ -19,10 +19,11 @@ GM_OK, GM_ERR_INVALID_ARG, GM_ERR_OUT_OF_MEMORY, GM_ERR_CUDA, GM_ERR_STATE, GM_E
     GM_ERR_UNSUPPORTED = range(7)
 GM_W_NONE, GM_W_U32, GM_W_F32 = 0, 1, 2
 GM_DROP_SELF_LOOPS, GM_DEDUP, GM_SYMMETRIZE, GM_ORIENT_BY_DEGREE = 1, 2, 4, 8
-GM_PAGERANK, GM_BFS, GM_SSSP, GM_TRIANGLE_COUNT, GM_CF, GM_CONNECTED_COMPONENTS = range(6)
+GM_PAGERANK, GM_BFS, GM_SSSP, GM_TRIANGLE_COUNT, GM_CF, GM_CONNECTED_COMPONENTS, GM_CF_SGD = range(7)
 (GM_SCALAR_TC_TOTAL, GM_SCALAR_CF_LOSS, GM_SCALAR_REACHED_EDGES, GM_SCALAR_SUPERSTEPS,
  GM_SCALAR_PUSH_STEPS, GM_SCALAR_PULL_STEPS, GM_SCALAR_SCANNED_EDGES, GM_SCALAR_RELAX_MS,
- GM_SCALAR_RELAX_LAUNCHES, GM_SCALAR_PROCESSED_VERTICES, GM_SCALAR_PULL_WEIGHT_BYTES) = range(1, 12)
+ GM_SCALAR_RELAX_LAUNCHES, GM_SCALAR_PROCESSED_VERTICES, GM_SCALAR_PULL_WEIGHT_BYTES,
+ GM_SCALAR_CF_STRATA) = range(1, 13)
 (GM_OPT_DIRECTION, GM_OPT_LOOP_MODE, GM_OPT_PROFILE, GM_OPT_BIN_SMALL, GM_OPT_BIN_LARGE,
  GM_OPT_ALPHA_X1000, GM_OPT_BETA_X1000, GM_OPT_SSSP_PULL_PPM, GM_OPT_PULL_STAGE,
  GM_OPT_TEST_STALL_STAGE) = range(1, 11)
@@ -34,7 +35,7 @@ _SCALAR_TYPES = {
     GM_SCALAR_PUSH_STEPS: ctypes.c_int32, GM_SCALAR_PULL_STEPS: ctypes.c_int32,
     GM_SCALAR_SCANNED_EDGES: ctypes.c_int64, GM_SCALAR_RELAX_MS: ctypes.c_double,
     GM_SCALAR_RELAX_LAUNCHES: ctypes.c_int32, GM_SCALAR_PROCESSED_VERTICES: ctypes.c_int64,
-    GM_SCALAR_PULL_WEIGHT_BYTES: ctypes.c_int32,
+    GM_SCALAR_PULL_WEIGHT_BYTES: ctypes.c_int32, GM_SCALAR_CF_STRATA: ctypes.c_int32,
 }
 
 
@@ -54,7 +55,7 @@ class gm_edge_list(ctypes.Structure):
 class gm_program_params(ctypes.Structure):
     _fields_ = [("r", ctypes.c_double), ("pr_apply_all", ctypes.c_int32), ("K", ctypes.c_int32),
                 ("lam", ctypes.c_double), ("gamma", ctypes.c_double), ("init_sigma", ctypes.c_double),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("cf_strata", ctypes.c_int32)]
 
 
 _lib = None
@@ -241,8 +242,9 @@ class Graph:
         return o, i
 
     # -- programs --------------------------------------------------------
-    def program_set(self, kind, r=0.15, pr_apply_all=True, K=32, lam=0.05, gamma=1e-3, init_sigma=0.1, seed=0):
-        p = gm_program_params(r, 1 if pr_apply_all else 0, K, lam, gamma, init_sigma, seed)
+    def program_set(self, kind, r=0.15, pr_apply_all=True, K=32, lam=0.05, gamma=1e-3, init_sigma=0.1, seed=0,
+                    cf_strata=0):
+        p = gm_program_params(r, 1 if pr_apply_all else 0, K, lam, gamma, init_sigma, seed, cf_strata)
         _check(lib().gm_program_set(self._h, kind, ctypes.byref(p)), "gm_program_set")
         self.kind, self.K = kind, K
 
@@ -267,7 +269,7 @@ class Graph:
             return np.float32, (self.n,)
         if self.kind == GM_TRIANGLE_COUNT:
             return np.uint64, (self.n,)
-        if self.kind == GM_CF:
+        if self.kind in (GM_CF, GM_CF_SGD):
             return np.float32, (self.n, self.K)
         raise GMError(GM_ERR_STATE, "state", "no program set")
 

@@ -22,7 +22,8 @@ int64_t state_bytes(const gm_graph* g) {
         case GM_SSSP: return 4 * g->n;
         case GM_PAGERANK: return 4 * g->n;
         case GM_TRIANGLE_COUNT: return 8 * g->n;
-        case GM_CF: return 4 * g->n * (int64_t)g->params.K;
+        case GM_CF:
+        case GM_CF_SGD: return 4 * g->n * (int64_t)g->params.K;
         case GM_CONNECTED_COMPONENTS: return 4 * g->n;
         default: return -1;
     }
@@ -66,6 +67,7 @@ gm_status gm_program_set(gm_graph* g, int32_t kind, const gm_program_params* par
     p.gamma = 1e-3;
     p.init_sigma = 0.1;
     p.seed = 0;
+    p.cf_strata = 0;
     if (params) p = *params;
     switch (kind) {
         case GM_PAGERANK:
@@ -78,6 +80,7 @@ gm_status gm_program_set(gm_graph* g, int32_t kind, const gm_program_params* par
         case GM_CONNECTED_COMPONENTS:
             break;
         case GM_CF:
+        case GM_CF_SGD:
             if (g->n_left <= 0 || g->n_left >= g->n) {
                 set_error("gm_program_set: CF needs a bipartite graph with 0 < n_left < n");
                 return GM_ERR_INVALID_ARG;
@@ -127,7 +130,7 @@ gm_status gm_program_set(gm_graph* g, int32_t kind, const gm_program_params* par
             cudaError_t e = cudaMemsetAsync(g->state.p, 0, sizeof(uint64_t) * g->n, g->stream);
             if (e != cudaSuccess) { set_error("gm_program_set: %s", cudaGetErrorString(e)); st = GM_ERR_CUDA; }
         }
-    } else if (kind == GM_CF) {
+    } else if (kind == GM_CF || kind == GM_CF_SGD) {
         st = cf_prepare(g);
     } else if (kind == GM_CONNECTED_COMPONENTS) {
         st = cc_prepare(g);
@@ -172,7 +175,8 @@ gm_status gm_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
         case GM_SSSP: return trav_run(g, max_iters, iters_done);
         case GM_PAGERANK: return pr_run(g, max_iters, iters_done);
         case GM_TRIANGLE_COUNT: return tc_run(g, iters_done);
-        case GM_CF: return cf_run(g, max_iters, iters_done);
+        case GM_CF:
+        case GM_CF_SGD: return cf_run(g, max_iters, iters_done);
         case GM_CONNECTED_COMPONENTS: return cc_run(g, max_iters, iters_done);
         default: break;
     }
@@ -240,8 +244,15 @@ gm_status gm_get_scalar(gm_graph* g, int32_t which, void* out) {
             *static_cast<uint64_t*>(out) = g->tc_total;
             return GM_OK;
         case GM_SCALAR_CF_LOSS:
-            if (g->kind != GM_CF) { set_error("gm_get_scalar: not a CF program"); return GM_ERR_STATE; }
+            if (g->kind != GM_CF && g->kind != GM_CF_SGD) {
+                set_error("gm_get_scalar: not a CF program");
+                return GM_ERR_STATE;
+            }
             return cf_loss(g, static_cast<double*>(out));
+        case GM_SCALAR_CF_STRATA:
+            if (g->kind != GM_CF_SGD) { set_error("gm_get_scalar: not an SGD program"); return GM_ERR_STATE; }
+            *static_cast<int32_t*>(out) = g->params.cf_strata;
+            return GM_OK;
         case GM_SCALAR_REACHED_EDGES:
             if (g->kind != GM_BFS && g->kind != GM_SSSP) { set_error("gm_get_scalar: not a traversal program"); return GM_ERR_STATE; }
             return reached_edges(g, static_cast<int64_t*>(out));

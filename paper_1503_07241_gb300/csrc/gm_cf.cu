@@ -355,6 +355,7 @@ struct CfState {
     DevBuf hot_ids, code;     // staged item rows (grouped K): their vertex ids; per-rating codes
     int32_t n_hot = 0;
     int64_t n_user_chunks = 0, n_item_chunks = 0;
+    void* sgd = nullptr;      // stochastic gradient descent (gm_cf_sgd.cu)
 };
 
 int grid_cf() { return num_sms() * 8; }
@@ -380,9 +381,17 @@ gm_status by_group(int K, F f) {
 
 }  // namespace
 
+// Stochastic gradient descent (gm_cf_sgd.cu): rating records in the stratified
+// order, and the epochs.
+gm_status sgd_prepare(gm_graph* g, void** state);
+gm_status sgd_run(gm_graph* g, void* state, int32_t epochs);
+void sgd_release(void* state, cudaStream_t s);
+
 void cf_release(gm_graph* g) {
     CfState* c = static_cast<CfState*>(g->cf);
     if (!c) return;
+    sgd_release(c->sgd, g->stream);
+    c->sgd = nullptr;
     DevBuf* bufs[] = {&c->user_chunks, &c->item_chunks, &c->ebuf, &c->acc, &c->scalar, &c->hot_ids, &c->code};
     for (DevBuf* b : bufs) dev_free(*b, g->stream);
     delete c;
@@ -411,8 +420,9 @@ gm_status cf_prepare(gm_graph* g) {
         GM_CUDA_TRY(cudaMemcpyAsync(c->user_chunks.p, uc.data(), sizeof(int4) * uc.size(), cudaMemcpyHostToDevice, s));
     if (!ic.empty())
         GM_CUDA_TRY(cudaMemcpyAsync(c->item_chunks.p, ic.data(), sizeof(int4) * ic.size(), cudaMemcpyHostToDevice, s));
+    const bool sgd = g->kind == GM_CF_SGD;
     // the most-rated items' rows are staged in shared memory by the user pass
-    if (grouped(K) && g->m > 0 && n > g->n_left) {
+    if (!sgd && grouped(K) && g->m > 0 && n > g->n_left) {
         const int64_t n_items = n - g->n_left;
         const int32_t cap = (int32_t)std::min<int64_t>(n_items, kHotSmem / (int64_t)(sizeof(float) * K));
         std::vector<int32_t> items((size_t)n_items);
@@ -436,10 +446,14 @@ gm_status cf_prepare(gm_graph* g) {
         dev_free(dslot, s);
         c->n_hot = cap;
     }
-    GM_TRY(dev_alloc(c->ebuf, sizeof(float) * (g->m > 0 ? g->m : 1), s));
-    GM_TRY(dev_alloc(c->acc, sizeof(float) * (n > 0 ? n : 1) * K, s));
+    if (sgd) {
+        GM_TRY(sgd_prepare(g, &c->sgd));
+    } else {
+        GM_TRY(dev_alloc(c->ebuf, sizeof(float) * (g->m > 0 ? g->m : 1), s));
+        GM_TRY(dev_alloc(c->acc, sizeof(float) * (n > 0 ? n : 1) * K, s));
+        GM_CUDA_TRY(cudaMemsetAsync(c->acc.p, 0, sizeof(float) * (n > 0 ? n : 1) * K, s));
+    }
     GM_TRY(dev_alloc(c->scalar, sizeof(double) * 2, s));
-    GM_CUDA_TRY(cudaMemsetAsync(c->acc.p, 0, sizeof(float) * (n > 0 ? n : 1) * K, s));
     GM_TRY(dev_alloc(g->state, sizeof(float) * (n > 0 ? n : 1) * K, s));
     if (n > 0) {
         cf_init<<<num_sms() * 4, 256, 0, s>>>(as<float>(g->state), n * K, g->params.seed, g->params.init_sigma);
@@ -460,6 +474,13 @@ gm_status cf_run(gm_graph* g, int32_t iters, int32_t* iters_done) {
     const int K = g->params.K;
     const int64_t nk = g->n * K;
     float* p = as<float>(g->state);
+    if (g->kind == GM_CF_SGD) {
+        GM_TRY(sgd_run(g, c->sgd, iters));
+        g->stats = RunStats{};
+        g->stats.supersteps = iters;
+        if (iters_done) *iters_done = iters;
+        return GM_OK;
+    }
     for (int32_t it = 0; it < iters; ++it) {
         if (grouped(K)) {
             GM_TRY(by_group(K, [&](auto lc) -> gm_status {
