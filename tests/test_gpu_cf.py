@@ -8,9 +8,9 @@ strata, K with one and two components per lane, item rows in shared memory
 and in L2, and one epoch of the full workload.
 
 SGD tolerance: the kernel computes in FP32 with a different dot-product order;
-a sequential FP32 replay of the oracle's order on the 150k-rating case differs
-from FP64 by at most 3e-6 after two epochs, so every factor must lie within
-5e-5 + 1e-4 |oracle|."""
+a sequential FP32 replay of the oracle's order differs from FP64 by at most
+3e-6 after two epochs of the 150k-rating case and 1.2e-5 after one epoch of the
+100M-rating workload, so every factor must lie within 5e-5 + 1e-4 |oracle|."""
 import numpy as np
 import pytest
 
