@@ -199,10 +199,17 @@ GM_API gm_status gm_set_active(gm_graph* g, const int32_t* vertices, int64_t cou
  * gm_run -- Algorithm 2: run supersteps until no vertex is active or
  * `max_iters` supersteps have run (max_iters = -1: until no vertex is active, as
  * run_graph_program(..., -1, ...) in the appendix).  PageRank and CF run exactly
- * max_iters >= 0 supersteps (GM_CF_SGD: epochs).  Triangle counting runs its two programs and
- * ignores max_iters.  iters_done (may be NULL) receives the number of supersteps
- * executed, counting the final one that found no active vertex.
- * The call synchronises the stream.
+ * max_iters >= 0 supersteps (GM_CF_SGD: epochs, all in one cooperative launch).
+ * Triangle counting runs its two programs and ignores max_iters.  iters_done
+ * (may be NULL) receives the number of supersteps executed, counting the final
+ * one that found no active vertex.  The call synchronises the stream.
+ * Errors: GM_ERR_STATE before gm_program_set; GM_ERR_INVALID_ARG for
+ * max_iters < -1 (and for -1 with PageRank or CF); GM_ERR_TIMEOUT when a bounded
+ * device wait or guard gave up: an SSSP pull CTA's wait for its shared-memory
+ * staging copy (the results stay exact: that CTA read the messages from global
+ * memory), the traversal's n + 2 superstep guard (an internal error), or a
+ * GM_CF_SGD grid barrier between strata that waited about ten seconds (the
+ * factors are then unspecified; gm_program_set makes the handle usable again).
  */
 GM_API gm_status gm_run(gm_graph* g, int32_t max_iters, int32_t* iters_done);
 
