@@ -21,3 +21,91 @@ def test_cf_sgd_oracle_sample_counts_the_chosen_users():
     assert out["kind"] == "oracle" and out["cores"] == 1 and out["unit"] == "ratings/s"
     assert out["value"] > 0
     assert f"the {want} ratings of users 1000..1499" in out["sample"]
+
+
+def test_clock_summary_reads_median_under_load_and_reasons(tmp_path):
+    """nvidia-smi rows (csv, noheader, nounits): the SM clock median over samples
+    above half the maximum, the maximum, and every throttle reason seen active."""
+    import bench
+    cs = bench.ClockSampler(0)
+    cs.path = str(tmp_path / "clocks.csv")
+    rows = [
+        "0, 345, 2070, 120.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1965, 2070, 900.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 1980, 2070, 1100.25, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 1995, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "[N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",
+    ]
+    with open(cs.path, "w") as f:
+        f.write("\n".join(rows) + "\n")
+    cs.proc = object()  # as if the sampler had run
+    out = cs.summary()
+    assert out["sm_mhz"] == 1980.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+    assert out["samples"] == 4 and out["power_w_max"] == 1100.25
+
+
+def test_pull_roofline_adds_the_sssp_pull_launches_only():
+    """Algorithmic bytes of trav_pull_a launches: in-edges x (4 B id + weight
+    width + 1/8 B first-edge bit) + the vertex state once per launch; BFS pull
+    launches are reported apart and push supersteps count only in the
+    whole-superstep figure."""
+    import bench
+
+    class FakeGM:
+        GM_BFS, GM_SSSP = 1, 2
+        GM_SCALAR_PULL_WEIGHT_BYTES = 11
+        GM_OPT_PROFILE = 3
+
+    class FakeGraph:
+        n = 10
+        # (superstep, dir, active, edges, vertices, superstep ms, next edges, pull ms)
+        traces = {FakeGM.GM_BFS: [[0, 0, 1, 100, 1, 0.1, 0, 0.0], [1, 1, 5, 800, 6, 0.2, 0, 0.15]],
+                  FakeGM.GM_SSSP: [[0, 0, 1, 100, 1, 0.1, 0, 0.0], [1, 1, 9, 1000, 6, 0.5, 0, 0.4]]}
+
+        def __init__(self):
+            self.kind = None
+            self.options = []
+
+        def scalar(self, which):
+            assert which == FakeGM.GM_SCALAR_PULL_WEIGHT_BYTES
+            return 1
+
+        def degrees(self):
+            return np.zeros(10, np.int32), np.array([0, 1, 2, 0, 3, 1, 0, 0, 5, 1], np.int32)
+
+        def set_option(self, opt, val):
+            self.options.append((opt, val))
+
+        def program_set(self, kind):
+            self.kind = kind
+
+        def set_active(self, v):
+            pass
+
+        def run(self, it):
+            return 2
+
+        def trace(self):
+            return np.array(self.traces[self.kind], np.float64)
+
+    g = FakeGraph()
+    srcs = np.array([0, 1], np.int32)
+    r = bench.pull_roofline(FakeGM, g, srcs, srcs, (srcs, srcs), peak=6000.0, peak_kind="measured")
+    assert g.options == [(FakeGM.GM_OPT_PROFILE, 1), (FakeGM.GM_OPT_PROFILE, 0)]
+    state = 4.0 * 10 + 4.0 * 6  # every message once + the 6 non-empty columns written once
+    per_launch = 1000 * (4 + 1) + 1000 / 8 + state
+    assert r["launches"] == 2 and r["bytes_per_launch"] == per_launch
+    assert abs(r["avg_launch_us"] - 400.0) < 1e-9
+    assert abs(r["achieved"] - per_launch / 0.4e-3 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 6000.0) < 1e-12
+    assert r["bfs_pull_bottom_up"]["launches"] == 2
+    assert r["bfs_pull_bottom_up"]["in_edges_checked_per_launch"] == 800
+
+
+def test_recorded_traffic_is_dropped_when_the_kernel_source_changes(monkeypatch):
+    import bench
+    monkeypatch.setattr(bench, "_kernel_source_hash", lambda: "0" * 64)
+    assert bench._recorded_traffic() is None
+    monkeypatch.setattr(bench, "_kernel_source_hash", lambda: bench.PULL_A_TRAFFIC["source_sha256"])
+    assert bench._recorded_traffic() == bench.PULL_A_TRAFFIC["bytes_per_launch"]
