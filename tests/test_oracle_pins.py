@@ -503,6 +503,8 @@ def test_cf_sgd_epochs_compose_and_arguments_are_checked():
         g.cf_sgd(K, 0.05, 0.01, 1, nu, 0, p0)
     with pytest.raises(ValueError):
         g.cf_sgd(K, 0.05, 0.01, 1, nu - 1, 4, p0)  # a user would be an item
+    empty = oracle.Graph(nu + ni, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.uint32))
+    np.testing.assert_array_equal(empty.cf_sgd(K, 0.05, 0.01, 3, nu, 4, p0), p0)  # no rating, no update
 
 
 # ---------------------------------------------------------------- weighted PageRank
