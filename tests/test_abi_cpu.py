@@ -63,3 +63,44 @@ def test_null_arguments_rejected_without_gpu(L):
     assert L.gm_graph_create(ctypes.byref(el), 0, None, ctypes.byref(out)) == pkg.GM_ERR_INVALID_ARG
     el = pkg.gm_edge_list(10, 0, None, None, None, 0, 0, 0)
     assert L.gm_graph_create(ctypes.byref(el), 1 << 10, None, ctypes.byref(out)) == pkg.GM_ERR_INVALID_ARG
+
+
+# C field names of every struct the binding mirrors, in declaration order
+_C_FIELDS = {
+    "gm_edge_list": ["n_vertices", "n_edges", "src", "dst", "weight", "weight_type", "on_device", "n_left"],
+    "gm_program_params": ["r", "pr_apply_all", "K", "lambda", "gamma", "init_sigma", "seed", "cf_strata"],
+    "gm_tuning": ["alpha", "beta", "sssp_pull_frac", "bin_small", "bin_large", "best_ms", "pull_stage"],
+    "gm_query": ["graph", "kind", "source", "reserved"],
+}
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """sizeof and every field offset of the header's structs, as the host C
+    compiler lays them out, equal those of the ctypes mirrors."""
+    import shutil
+    import subprocess
+    import paper_1503_07241_gb300 as pkg
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "graphmat_gb300.h"', "int main(void) {"]
+    for st, fields in _C_FIELDS.items():
+        lines.append(f'printf("{st} size %zu\\n", sizeof({st}));')
+        for f in fields:
+            lines.append(f'printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", HEADER_DIR, str(src), "-o", str(exe)], check=True)
+    c = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        st, f, v = line.split()
+        c[(st, f)] = int(v)
+    for st, fields in _C_FIELDS.items():
+        cls = getattr(pkg, st)
+        assert ctypes.sizeof(cls) == c[(st, "size")], st
+        py_fields = [name for name, _ in cls._fields_]
+        assert len(py_fields) == len(fields), st
+        for cf, pf in zip(fields, py_fields):
+            assert getattr(cls, pf).offset == c[(st, cf)], (st, cf)
