@@ -229,28 +229,29 @@ def cpu_baseline(n, s, d, w, bfs_src, sssp_src, n_pairs=1):
 
 
 def reference_arm(args):
+    """The FP64 oracle as it stands, on one host core: each step is one BFS and one
+    SSSP query of the scale-22 workload (the GPU arm's step runs 16 of each; the
+    metric is edges per second either way)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     n, s, d, w, bfs_src, sssp_src = make_workload(0)
     import oracle
     og = oracle.Graph(n, s, d, w)
-    both = (args.steps + args.warmup) <= 20
     edges_total, t_total = 0, 0.0
     for step in range(args.warmup + args.steps):
         i = step % N_QUERIES
         t0 = time.perf_counter()
         dd, _ = og.bfs([bfs_src[i]])
         e = og.reached_edges(dd)
-        if both:
-            dd, _ = og.sssp([sssp_src[i]])
-            e += og.reached_edges(dd)
+        dd, _ = og.sssp([sssp_src[i]])
+        e += og.reached_edges(dd)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             edges_total += e
             t_total += dt
     val = edges_total / t_total / 1e9
-    sample = ("1 BFS + 1 SSSP query" if both else "1 BFS query") + " of the scale-22 workload per step"
+    sample = "1 BFS + 1 SSSP query of the scale-22 workload per step (sources cycle through the GPU arm's 16 + 16)"
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GTEPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
@@ -269,29 +270,49 @@ def pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind):
     per-column result written once (4 B per non-empty column).  The BFS pull
     (trav_pull_bu, bottom-up) is timed beside it."""
     wb = g.scalar(gm.GM_SCALAR_PULL_WEIGHT_BYTES)
+    eb = g.scalar(gm.GM_SCALAR_PULL_EDGE_BYTES) if hasattr(gm, "GM_SCALAR_PULL_EDGE_BYTES") else 4 + wb
     _, in_deg = g.degrees()
     state_bytes = 4.0 * g.n + 4.0 * float(np.count_nonzero(in_deg))
+    ncols = float(np.count_nonzero(in_deg))
     g.set_option(gm.GM_OPT_PROFILE, 1)
-    byts, ms, launches = 0.0, 0.0, 0
+    byts, ms, launches, read_bytes = 0.0, 0.0, 0, 0.0
     bu_ms, bu_edges, bu_launches = 0.0, 0.0, 0
     relax_ms, relax_bytes = 0.0, 0.0
+    # the SSSP superstep's other kernels: push supersteps' trav_push<1> and the
+    # finalize kernel after a pull (Apply) and after a push (next messages)
+    push = {"ms": 0.0, "bytes": 0.0, "launches": 0}
+    fin_pull = {"ms": 0.0, "bytes": 0.0, "launches": 0}
+    fin_push = {"ms": 0.0, "bytes": 0.0, "launches": 0}
     for kind, srcs, dev in ((gm.GM_BFS, bfs_src, src_dev[0]), (gm.GM_SSSP, sssp_src, src_dev[1])):
         sw = wb if kind == gm.GM_SSSP else 0
         for i in range(len(srcs)):
             g.program_set(kind)
             g.set_active(dev[i:i + 1])
             g.run(-1)
-            for row in g.trace():
+            tr = g.trace()
+            for j, row in enumerate(tr):
                 relax_ms += row[5]
                 relax_bytes += row[3] * (4 + sw) + row[4] * 12
+                changed = tr[j + 1][2] if j + 1 < len(tr) else 0.0  # the next superstep's frontier
                 if row[1] == 1 and kind == gm.GM_SSSP:
                     byts += row[3] * (4 + sw) + row[3] / 8.0 + state_bytes
+                    read_bytes += row[3] * eb + row[3] / 8.0 + state_bytes
                     ms += row[7]
                     launches += 1
+                    fin_pull["ms"] += row[9]
+                    fin_pull["bytes"] += finalize_pull_bytes(ncols, row[4], changed)
+                    fin_pull["launches"] += 1
                 elif row[1] == 1:
                     bu_ms += row[7]
                     bu_edges += row[3]
                     bu_launches += 1
+                elif kind == gm.GM_SSSP:
+                    push["ms"] += row[8]
+                    push["bytes"] += push_bytes(row[3], row[4])
+                    push["launches"] += 1
+                    fin_push["ms"] += row[9]
+                    fin_push["bytes"] += 16.0 * changed
+                    fin_push["launches"] += 1
     g.set_option(gm.GM_OPT_PROFILE, 0)
     achieved = byts / (ms / 1e3) / 1e9 if ms > 0 else None
     traffic = _recorded_traffic()
@@ -301,11 +322,45 @@ def pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind):
             "frac": (achieved / peak) if achieved else None, "traffic": traffic, "traffic_frac": dram_frac,
             "kernel": "trav_pull_a (SSSP pull)", "peak_source": peak_kind, "weight_bytes": wb,
             "bytes_per_launch": byts / max(launches, 1), "avg_launch_us": 1e3 * ms / max(launches, 1),
+            # what the kernel streams: with the packed layout 4 B per in-edge carry both
+            # the source and its weight, so fewer bytes than the algorithmic figure above
+            "edge_bytes_read": eb, "bytes_read_per_launch": read_bytes / max(launches, 1),
+            "frac_of_bytes_read": (read_bytes / (ms / 1e3) / 1e9 / peak) if ms > 0 else None,
             "launches": launches,
             "bfs_pull_bottom_up": {"launches": bu_launches, "avg_launch_us": 1e3 * bu_ms / max(bu_launches, 1),
                                    "in_edges_checked_per_launch": bu_edges / max(bu_launches, 1)},
             "superstep_all_kernels": {"achieved_gbs": relax_bytes / (relax_ms / 1e3) / 1e9 if relax_ms else None,
-                                      "ms": relax_ms}}
+                                      "frac": (relax_bytes / (relax_ms / 1e3) / 1e9 / peak) if relax_ms else None,
+                                      "ms": relax_ms},
+            "sssp_push": _kernel_line("trav_push<1> (SSSP push supersteps)", push, peak),
+            "sssp_finalize_after_pull": _kernel_line("trav_finalize<1> after a pull (Apply)", fin_pull, peak),
+            "sssp_finalize_after_push": _kernel_line("trav_finalize<1> after a push (next messages)", fin_push,
+                                                     peak)}
+
+
+def push_bytes(edges, vertices):
+    """Algorithmic bytes of an SSSP push superstep: per frontier vertex its offset
+    pair and queue entry (12 B), per out-edge its destination and uint32 weight
+    (8 B) and the destination's distance read and written (8 B)."""
+    return 12.0 * vertices + 16.0 * edges
+
+
+def finalize_pull_bytes(ncols, received, changed):
+    """Algorithmic bytes of the SSSP Apply after a pull: every non-empty column's
+    reduced value, vertex and source rank (12 B); for each column that received a
+    message its distance and out-degree read and the reduced value reset (12 B);
+    for each changed vertex its distance, next message and queue entry written
+    (12 B)."""
+    return 12.0 * ncols + 12.0 * received + 12.0 * changed
+
+
+def _kernel_line(name, acc, peak):
+    if not acc["launches"] or acc["ms"] <= 0:
+        return {"kernel": name, "launches": acc["launches"]}
+    gbs = acc["bytes"] / (acc["ms"] / 1e3) / 1e9
+    return {"kernel": name, "bound": "latency", "launches": acc["launches"],
+            "avg_launch_us": 1e3 * acc["ms"] / acc["launches"], "bytes_per_launch": acc["bytes"] / acc["launches"],
+            "achieved": gbs, "unit": "GB/s", "peak": peak, "frac": gbs / peak}
 
 
 # DRAM bytes (read + write) per trav_pull_a launch in the bench's timed step, from
@@ -367,11 +422,18 @@ def case_triangles(gm, synth):
     return g, lambda: g.run()
 
 
+# Gradient-descent step of the CF workload.  At the specified 1e-3 full-batch
+# gradient descent diverges on this workload, in FP64 too (loss overflow by the
+# seventh step); 1e-5 is the largest power of ten <= 1e-3 at which the FP64
+# oracle's loss decreases in all ten steps, so the timed run is one that converges.
+CF_GAMMA = 1e-5
+
+
 def case_cf(gm, synth):
     """Collaborative filtering, 480k users x 17.8k items, ~1e8 ratings, K = 32."""
     n, s, d, r = synth.chung_lu_bipartite(480_000, 17_800, 1.1, 1e8, seed=synth.BASE_SEED + 2)
     g = gm.Graph(n, s, d, r, n_left=480_000)
-    g.program_set(gm.GM_CF, K=32, lam=0.05, gamma=1e-3, init_sigma=0.1, seed=5)
+    g.program_set(gm.GM_CF, K=32, lam=0.05, gamma=CF_GAMMA, init_sigma=0.1, seed=5)
     return g, lambda: g.run(10)
 
 
@@ -637,8 +699,11 @@ def extras(gm):
     try:  # collaborative filtering, 480k x 17.8k, ~1e8 ratings, K = 32, 10 iterations
         g, run = case_cf(gm, synth)
         g.run(1)
+        loss_a = g.scalar(gm.GM_SCALAR_CF_LOSS)
         ms, _ = timed(run)
-        out["cf_100M_k32"] = {"ms_10_iters": ms, "ratings": g.m,
+        loss_b = g.scalar(gm.GM_SCALAR_CF_LOSS)
+        out["cf_100M_k32"] = {"ms_10_iters": ms, "ratings": g.m, "gamma": CF_GAMMA,
+                              "loss_after_1": loss_a, "loss_after_11": loss_b, "loss_decreased": loss_b < loss_a,
                               "ratings_per_s": 10 * g.m / (ms / 1e3),
                               "gflops": 10 * g.m * 6 * 32 / (ms / 1e3) / 1e9}
     except Exception as e:  # pragma: no cover
@@ -666,7 +731,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="end-to-end repetitions (each: ingest from pinned host memory, the 32 queries, every "
+                         "result back to the host); the median is reported")
     ap.add_argument("--host-loop", action="store_true",
                     help="issue every superstep's kernels from the host instead of one CUDA graph "
                          "(same kernels; profilers do not see kernels inside conditional graph nodes)")
@@ -813,10 +880,10 @@ def main():
         pin = lambda a: torch.from_numpy(a).pin_memory()
         hs, hd, hw = pin(s), pin(d), pin(w.view(np.int32))
         out = torch.empty(n, dtype=torch.int32).pin_memory()
-        barrier()
-        t0 = time.perf_counter()
-        e_edges = 0
+        reps = []
         for _ in range(args.e2e_steps):
+            barrier()
+            t0 = time.perf_counter()
             g2 = gm.Graph(n, hs, hd, hw, stream=stream)
             if tuning:
                 for opt, key, scale in ((gm.GM_OPT_ALPHA_X1000, "alpha", 1e3), (gm.GM_OPT_BETA_X1000, "beta", 1e3),
@@ -824,14 +891,16 @@ def main():
                                         (gm.GM_OPT_BIN_LARGE, "bin_large", 1), (gm.GM_OPT_BIN_SMALL, "bin_small", 1),
                                         (gm.GM_OPT_PULL_STAGE, "pull_stage", 1)):
                     g2.set_option(opt, round(tuning[key] * scale))
-            e_edges += run_queries(gm, g2, bfs_src, sssp_src, (None, None), out_host=out)
+            e_edges = run_queries(gm, g2, bfs_src, sssp_src, (None, None), out_host=out)
             g2.close()
-        barrier()
-        e_t, e_edges = combine_ranks(dist, time.perf_counter() - t0, e_edges, "cuda")
-        e2e = {"value": e_edges / e_t / 1e9, "unit": "GTEPS",
+            barrier()
+            e_t, e_all = combine_ranks(dist, time.perf_counter() - t0, e_edges, "cuda")
+            reps.append(e_all / e_t / 1e9)
+        e2e = {"value": statistics.median(reps), "unit": "GTEPS",
                "h2d_bytes_per_step": int(s.nbytes + d.nbytes + w.nbytes + 8 * N_QUERIES),
-               "d2h_bytes_per_step": int(2 * N_QUERIES * 4 * n), "steps": args.e2e_steps,
-               "includes": "graph ingest from pinned host edge list + 32 queries + results to host"}
+               "d2h_bytes_per_step": int(2 * N_QUERIES * 4 * n), "steps": args.e2e_steps, "reps_gteps": reps,
+               "includes": "graph ingest from pinned host edge list + 32 queries + results to host; "
+                           "median of the repetitions"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

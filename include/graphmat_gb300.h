@@ -238,18 +238,25 @@ enum {
     GM_SCALAR_PULL_WEIGHT_BYTES = 11,  /* int32: bytes per in-edge weight the SSSP pull reads: 1 when
                                           every uint32 weight is below 256 (a one-byte copy is kept),
                                           4 otherwise, 0 for an unweighted graph; set at creation */
-    GM_SCALAR_CF_STRATA = 12           /* int32: blocks per side P of the GM_CF_SGD order in use */
+    GM_SCALAR_CF_STRATA = 12,          /* int32: blocks per side P of the GM_CF_SGD order in use */
+    GM_SCALAR_PULL_EDGE_BYTES = 13     /* int32: bytes per in-edge the SSSP pull streams for its source and
+                                          weight: 4 when both share one word (GM_OPT_PULL_PACKED), else 4 +
+                                          the weight width (GM_SCALAR_PULL_WEIGHT_BYTES) */
 };
 GM_API gm_status gm_get_scalar(gm_graph* g, int32_t which, void* out);
 
 /*
  * Per-superstep trace of the last gm_run in profile mode (GM_OPT_PROFILE = 1):
- * up to max_rows rows of 8 doubles -- superstep index, direction (0 push, 1 pull),
+ * up to max_rows rows of 10 doubles -- superstep index, direction (0 push, 1 pull),
  * active work items at its start, edges read, vertices whose edge lists were read,
  * time of the superstep's kernels in ms (push, pull and finalize, which holds the
- * SSSP Apply after a pull; CUDA events), the out-edges of the next frontier, and
- * the time of the pull kernel alone (0 in push supersteps; SSSP: the in-edge
- * streaming kernel, BFS: the bottom-up kernel, which counts in-edges checked).
+ * SSSP Apply after a pull; CUDA events), the out-edges of the next frontier, the
+ * time of the pull kernel alone (SSSP: the in-edge streaming kernel, BFS: the
+ * bottom-up kernel, which counts in-edges checked), the time of the push kernel
+ * alone and the time of the finalize kernel alone.  Both directions' kernels are
+ * launched every superstep and the one not chosen returns at once, so the push
+ * time of a pull superstep (and the pull time of a push superstep) is that early
+ * return.
  * *n_rows receives the number of rows available.
  */
 GM_API gm_status gm_get_trace(gm_graph* g, double* rows, int32_t max_rows, int32_t* n_rows);
@@ -313,29 +320,30 @@ GM_API gm_status gm_run_batch(gm_graph* const* graphs, int32_t n_graphs, const g
  * gm_bfs_csr_noalloc -- BFS over caller-provided CSR arrays that allocates no
  * memory.  The paper has no counterpart: this is a library convenience for callers
  * that cannot allocate device memory when they need a traversal, such as code
- * running while a CUDA stream is being captured (cudaMalloc is not allowed there),
- * code that manages all device memory through its own arena or caching allocator,
+ * whose device memory is all owned by its own arena or caching allocator (a
+ * cudaMalloc outside it can fail once the arena has reserved the free memory),
  * and latency-critical loops that must not pay for cudaMalloc/cudaFree (which can
  * synchronise the device and can fail under memory pressure).
  *
- * The result equals gm_run with GM_BFS from one source on the same edges
- * (Section 3.II): depth[v] = number of edges on a shortest path from `source`,
- * UINT32_MAX if unreachable; *iters_done (may be NULL) = supersteps executed,
- * counting the final one that finds no new vertex.
+ * The result equals gm_run with GM_BFS from one source on the same edges:
+ * depth[v] = number of edges on a shortest path from `source`, UINT32_MAX if
+ * unreachable; *iters_done (may be NULL) = supersteps executed, counting the
+ * final one that finds no new vertex.
  *   n        vertices, 1 <= n <= gm_bfs_csr_noalloc_max_vertices() (1,048,576);
  *            larger n returns GM_ERR_INVALID_ARG without touching the GPU.
  *   row_ptr  device int32[n+1], col device int32[row_ptr[n]]: out-edges of each
  *            vertex; ids in [0, n).  Read only; owned by the caller.
  *   depth    device uint32[n], written.
- *   stream   cudaStream_t for all work (NULL = default stream); the call
- *            synchronises it once per superstep to read the frontier size.
+ *   stream   cudaStream_t for all work (NULL = default stream); the call copies
+ *            the next frontier's size to the host and synchronises the stream
+ *            once per superstep.
  * Scratch: two frontier queues and counters live in one fixed device array of
- * 8 MiB + 256 bytes that each GPU holds until the library is unloaded.  Its
- * device address is looked up (cudaGetSymbolAddress) on the first call on each
- * device, with that device current; make that first call before any stream
- * capture.  Every call shares the array and clears what it needs at the start,
- * so calls that overlap on the GPU (on different streams or host threads) race
- * and must not be issued.
+ * 8 MiB + 256 bytes that each GPU holds until the library is unloaded.  The
+ * first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call shares the array and clears what it needs at
+ * the start, so calls that overlap on the GPU (on different streams or host
+ * threads) race and must not be issued.
  */
 GM_API gm_status gm_bfs_csr_noalloc(int64_t n, const int32_t* row_ptr, const int32_t* col, int32_t source,
                                     uint32_t* depth, int32_t* iters_done, void* stream);
@@ -354,10 +362,19 @@ enum {
     GM_OPT_SSSP_PULL_PPM = 8, /* SSSP: pull when frontier edges > ppm * 1e-6 * m */
     GM_OPT_PULL_STAGE = 9,    /* SSSP pull: messages of the highest-out-degree sources each CTA stages in
                                  shared memory, 0..49152 (rounded down to a multiple of 4; default 40960) */
-    GM_OPT_TEST_STALL_STAGE = 10  /* test hook, 0 or 1: the SSSP pull's staging barrier expects 16 bytes more
+    GM_OPT_TEST_STALL_STAGE = 10, /* test hook, 0 or 1: the SSSP pull's staging barrier expects 16 bytes more
                                      than its copies bring, so every CTA's bounded wait (about a second)
                                      runs out; those CTAs gather every message from global memory, the
                                      results stay exact, and gm_run returns GM_ERR_TIMEOUT */
+    GM_OPT_TEST_STALL_SGD = 11,   /* test hook, 0 or 1: in GM_CF_SGD runs one CTA never arrives at the
+                                     first grid barrier between strata and the barrier's wait limit is
+                                     cut from about ten seconds to about half a second, so every CTA's
+                                     wait runs out, the kernel ends, gm_run returns GM_ERR_TIMEOUT and
+                                     the factors are left part-way through the first stratum */
+    GM_OPT_PULL_PACKED = 12       /* SSSP pull in-edge layout: 1 (default) one 32-bit word per in-edge,
+                                     source rank << 8 | weight, when every weight is below 256 and
+                                     n <= 2^24; 0 the source rank and the weight as separate arrays.
+                                     Results are identical. */
 };
 GM_API gm_status gm_set_option(gm_graph* g, int32_t option, int64_t value);
 

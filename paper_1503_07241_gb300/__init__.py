@@ -23,11 +23,12 @@ GM_PAGERANK, GM_BFS, GM_SSSP, GM_TRIANGLE_COUNT, GM_CF, GM_CONNECTED_COMPONENTS,
 (GM_SCALAR_TC_TOTAL, GM_SCALAR_CF_LOSS, GM_SCALAR_REACHED_EDGES, GM_SCALAR_SUPERSTEPS,
  GM_SCALAR_PUSH_STEPS, GM_SCALAR_PULL_STEPS, GM_SCALAR_SCANNED_EDGES, GM_SCALAR_RELAX_MS,
  GM_SCALAR_RELAX_LAUNCHES, GM_SCALAR_PROCESSED_VERTICES, GM_SCALAR_PULL_WEIGHT_BYTES,
- GM_SCALAR_CF_STRATA) = range(1, 13)
+ GM_SCALAR_CF_STRATA, GM_SCALAR_PULL_EDGE_BYTES) = range(1, 14)
 (GM_OPT_DIRECTION, GM_OPT_LOOP_MODE, GM_OPT_PROFILE, GM_OPT_BIN_SMALL, GM_OPT_BIN_LARGE,
  GM_OPT_ALPHA_X1000, GM_OPT_BETA_X1000, GM_OPT_SSSP_PULL_PPM, GM_OPT_PULL_STAGE,
- GM_OPT_TEST_STALL_STAGE) = range(1, 11)
+ GM_OPT_TEST_STALL_STAGE, GM_OPT_TEST_STALL_SGD, GM_OPT_PULL_PACKED) = range(1, 13)
 INF_U32 = 0xFFFFFFFF
+TRACE_COLS = 10  # doubles per row of gm_get_trace
 
 _SCALAR_TYPES = {
     GM_SCALAR_TC_TOTAL: ctypes.c_uint64, GM_SCALAR_CF_LOSS: ctypes.c_double,
@@ -36,6 +37,7 @@ _SCALAR_TYPES = {
     GM_SCALAR_SCANNED_EDGES: ctypes.c_int64, GM_SCALAR_RELAX_MS: ctypes.c_double,
     GM_SCALAR_RELAX_LAUNCHES: ctypes.c_int32, GM_SCALAR_PROCESSED_VERTICES: ctypes.c_int64,
     GM_SCALAR_PULL_WEIGHT_BYTES: ctypes.c_int32, GM_SCALAR_CF_STRATA: ctypes.c_int32,
+    GM_SCALAR_PULL_EDGE_BYTES: ctypes.c_int32,
 }
 
 
@@ -297,7 +299,7 @@ class Graph:
         """Per-superstep rows of the last profiled run (see gm_get_trace)."""
         k = ctypes.c_int32()
         _check(lib().gm_get_trace(self._h, None, 0, ctypes.byref(k)), "gm_get_trace")
-        rows = np.empty((k.value, 8), np.float64)
+        rows = np.empty((k.value, TRACE_COLS), np.float64)
         if k.value:
             _check(lib().gm_get_trace(self._h, rows.ctypes.data, k.value, ctypes.byref(k)), "gm_get_trace")
         return rows

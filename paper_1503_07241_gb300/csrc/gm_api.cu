@@ -266,6 +266,12 @@ gm_status gm_get_scalar(gm_graph* g, int32_t which, void* out) {
         case GM_SCALAR_PULL_WEIGHT_BYTES:
             *static_cast<int32_t*>(out) = g->wtype == GM_W_NONE ? 0 : g->cw8.p ? 1 : 4;
             return GM_OK;
+        case GM_SCALAR_PULL_EDGE_BYTES: {
+            // the layout build_pull_edge_words chooses (or has chosen)
+            const bool packed = g->tune.pull_packed && g->cw8.p != nullptr && g->n <= kPackedMaxVertices;
+            *static_cast<int32_t*>(out) = packed ? 4 : 4 + (g->cw8.p ? 1 : 4);
+            return GM_OK;
+        }
         default: break;
     }
     set_error("gm_get_scalar: unknown scalar %d", which);
@@ -327,6 +333,20 @@ gm_status gm_set_option(gm_graph* g, int32_t option, int64_t value) {
             if (value < 0 || value > 1) break;
             t.test_stall_stage = (int32_t)value;
             trav_release(g);
+            return GM_OK;
+        case GM_OPT_TEST_STALL_SGD:
+            if (value < 0 || value > 1) break;
+            t.test_stall_sgd = (int32_t)value;
+            return GM_OK;
+        case GM_OPT_PULL_PACKED:
+            if (value < 0 || value > 1) break;
+            if (t.pull_packed == (int32_t)value) return GM_OK;
+            t.pull_packed = (int32_t)value;
+            trav_release(g);  // the loop graph bakes the pull variant in
+            if (g->src_rank.p) {  // ranks exist: rebuild the in-edge stream in the chosen layout
+                GM_TRY(build_pull_edge_words(g));
+                GM_CUDA_TRY(cudaStreamSynchronize(g->stream));
+            }
             return GM_OK;
         default:
             set_error("gm_set_option: unknown option %d", option);

@@ -31,7 +31,8 @@
 // item: its ratings are serial in every order that reproduces serial SGD.
 // Strata are separated by a grid barrier whose wait gives up after about ten
 // seconds (or 2^30 tries), sets an error flag and ends the kernel; the host
-// then returns GM_ERR_TIMEOUT.
+// then returns GM_ERR_TIMEOUT.  The test option GM_OPT_TEST_STALL_SGD keeps one
+// CTA from arriving at the first barrier and cuts the limit to half a second.
 #include <algorithm>
 #include <cmath>
 
@@ -105,14 +106,17 @@ __global__ void sgd_records(const uint64_t* __restrict__ key, const uint32_t* __
 
 // Grid barrier between strata (all CTAs are resident: cooperative launch).
 // Returns false, with the error flag set, when the wait gave up or another CTA
-// gave up.
-__device__ __forceinline__ bool sgd_grid_sync(SgdSync* sy, unsigned& gen, int* s_ok) {
+// gave up.  The wait gives up after wait_ns by the global timer or 2^30 tries.
+// `skip_arrival` (the test hook) makes this CTA wait without arriving, so no
+// CTA's wait can end but by its limit.
+__device__ __forceinline__ bool sgd_grid_sync(SgdSync* sy, unsigned& gen, int* s_ok, bool skip_arrival,
+                                              uint64_t wait_ns) {
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned target = gen + 1u;
         int ok = 1;
-        if (atomicAdd(&sy->count, 1u) == gridDim.x - 1u) {
+        if (!skip_arrival && atomicAdd(&sy->count, 1u) == gridDim.x - 1u) {
             atomicExch(&sy->count, 0u);
             __threadfence();
             atomicExch(&sy->gen, target);
@@ -121,7 +125,7 @@ __device__ __forceinline__ bool sgd_grid_sync(SgdSync* sy, unsigned& gen, int* s
             for (uint32_t i = 0;; ++i) {
                 if (*(volatile unsigned*)&sy->gen == target) break;
                 if (*(volatile unsigned*)&sy->error != 0u) { ok = 0; break; }
-                if (i >= (1u << 30) || ((i & 63u) == 63u && sgd_ns() - t0 > 10000000000ull)) {
+                if (i >= (1u << 30) || ((i & 63u) == 63u && sgd_ns() - t0 > wait_ns)) {
                     atomicExch(&sy->error, 1u);
                     ok = 0;
                     break;
@@ -276,7 +280,7 @@ template <int KL, bool kSmem>
 __global__ void __launch_bounds__(kSgdThreads, 1)
     cf_sgd_epochs(const int4* __restrict__ rec, const uint32_t* __restrict__ blk, int32_t P, int32_t J,
                   float* __restrict__ p, int64_t n_left, int64_t n_items, int K, float gamma, float lambda,
-                  int32_t epochs, SgdSync* __restrict__ sync) {
+                  int32_t epochs, SgdSync* __restrict__ sync, int32_t stall_cta, uint64_t wait_ns) {
     extern __shared__ float sgd_items[];
     __shared__ int s_ok;
     const int lane = threadIdx.x & 31;
@@ -293,7 +297,8 @@ __global__ void __launch_bounds__(kSgdThreads, 1)
                     sgd_block<KL, kSmem>(rec, lo, hi, (b + s) % P, P, p, n_left, n_items, K, gamma, lambda, my,
                                          lane);
             }
-            if (!sgd_grid_sync(sync, gen, &s_ok)) return;
+            const bool skip = (int32_t)blockIdx.x == stall_cta && gen == 0u;  // test hook: first barrier only
+            if (!sgd_grid_sync(sync, gen, &s_ok, skip, wait_ns)) return;
         }
     }
 }
@@ -308,7 +313,13 @@ gm_status sgd_launch(const SgdState* st, gm_graph* g, int32_t epochs) {
     int K = g->params.K;
     float gamma = (float)g->params.gamma, lambda = (float)g->params.lambda;
     SgdSync* sync = as<SgdSync>(st->sync);
-    void* args[] = {&rec, &blk, &P, &J, &p, &n_left, &n_items, &K, &gamma, &lambda, &epochs, &sync};
+    // the barrier's wait limit: about ten seconds (a stratum of a very skewed
+    // matrix may legitimately take long), half a second under the test hook,
+    // which keeps the last CTA from arriving at the first barrier
+    int32_t stall_cta = g->tune.test_stall_sgd ? st->grid - 1 : -1;
+    uint64_t wait_ns = g->tune.test_stall_sgd ? 500000000ull : 10000000000ull;
+    void* args[] = {&rec, &blk, &P, &J, &p, &n_left, &n_items, &K, &gamma, &lambda, &epochs, &sync,
+                    &stall_cta, &wait_ns};
     GM_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)cf_sgd_epochs<KL, kSmem>, dim3(st->grid),
                                             dim3(kSgdThreads), args, st->smem_bytes, g->stream));
     g_launches++;
@@ -467,7 +478,8 @@ gm_status sgd_run(gm_graph* g, void* state, int32_t epochs) {
     GM_CUDA_TRY(cudaMemcpyAsync(&h, st->sync.p, sizeof(SgdSync), cudaMemcpyDeviceToHost, s));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
     if (h.error) {
-        set_error("gm_run: an SGD grid barrier wait gave up (a stratum took over ten seconds)");
+        set_error(g->tune.test_stall_sgd ? "gm_run: an SGD grid barrier wait gave up (test hook: one CTA never arrived)"
+                                         : "gm_run: an SGD grid barrier wait gave up (a stratum took over ten seconds)");
         return GM_ERR_TIMEOUT;
     }
     return GM_OK;

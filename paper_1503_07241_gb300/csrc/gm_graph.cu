@@ -543,6 +543,38 @@ __global__ void gather_i32(const int32_t* __restrict__ idx, int64_t len, const i
         out[i] = table[idx[i]];
 }
 
+// One word per in-edge for the SSSP pull: the source's rank in the high 24 bits,
+// the one-byte weight in the low 8.
+__global__ void pack_rank_weight(const int32_t* __restrict__ row, const uint8_t* __restrict__ w8, int64_t m,
+                                 const int32_t* __restrict__ rank, uint32_t* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = ((uint32_t)rank[row[i]] << 8) | (uint32_t)w8[i];
+}
+
+// The SSSP pull's in-edge stream from the source ranks: one word per in-edge,
+// (rank << 8) | weight, when every weight fits a byte, n <= 2^24 and the layout
+// option allows it (row_rw); otherwise the ranks alone (row_r), the weights then
+// coming from cw8 or cw.  Replaces whichever of the two exists.
+gm_status build_pull_edge_words(gm_graph* g) {
+    cudaStream_t s = g->stream;
+    const int64_t m = g->m;
+    dev_free(g->row_r, s);
+    dev_free(g->row_rw, s);
+    const bool packed = g->tune.pull_packed && g->cw8.p != nullptr && g->n <= kPackedMaxVertices;
+    DevBuf& words = packed ? g->row_rw : g->row_r;
+    GM_TRY(dev_alloc(words, sizeof(int32_t) * (m + kEdgePad), s));
+    GM_CUDA_TRY(cudaMemsetAsync(words.p, 0, sizeof(int32_t) * (m + kEdgePad), s));
+    if (m > 0 && packed) {
+        pack_rank_weight<<<blocks_for(m), 256, 0, s>>>(as<int32_t>(g->row), as<uint8_t>(g->cw8), m,
+                                                       as<int32_t>(g->src_rank), as<uint32_t>(g->row_rw));
+        LAUNCH_CHECK();
+    } else if (m > 0) {
+        gather_i32<<<blocks_for(m), 256, 0, s>>>(as<int32_t>(g->row), m, as<int32_t>(g->src_rank), as<int32_t>(g->row_r));
+        LAUNCH_CHECK();
+    }
+    return GM_OK;
+}
+
 gm_status build_source_ranks(gm_graph* g) {
     if (g->src_rank.p) return GM_OK;
     cudaStream_t s = g->stream;
@@ -555,9 +587,7 @@ gm_status build_source_ranks(gm_graph* g) {
     DevBuf &keys = tmp.b[0], &vals = tmp.b[1], &keys2 = tmp.b[2], &vals2 = tmp.b[3];
     const int64_t n1 = n > 0 ? n : 1;
     GM_TRY(dev_alloc(g->src_rank, sizeof(int32_t) * n1, s));
-    GM_TRY(dev_alloc(g->row_r, sizeof(int32_t) * (m + kEdgePad), s));
     GM_TRY(dev_alloc(g->dc_rank, sizeof(int32_t) * (g->dc_ncols > 0 ? g->dc_ncols : 1), s));
-    GM_CUDA_TRY(cudaMemsetAsync(g->row_r.p, 0, sizeof(int32_t) * (m + kEdgePad), s));
     if (n > 0) {
         GM_TRY(dev_alloc(keys, sizeof(uint64_t) * n, s));
         GM_TRY(dev_alloc(vals, sizeof(uint32_t) * n, s));
@@ -570,10 +600,7 @@ gm_status build_source_ranks(gm_graph* g) {
         invert_order<<<blocks_for(n), 256, 0, s>>>(as<uint32_t>(vals), n, as<int32_t>(g->src_rank));
         LAUNCH_CHECK();
     }
-    if (m > 0) {
-        gather_i32<<<blocks_for(m), 256, 0, s>>>(as<int32_t>(g->row), m, as<int32_t>(g->src_rank), as<int32_t>(g->row_r));
-        LAUNCH_CHECK();
-    }
+    GM_TRY(build_pull_edge_words(g));
     if (g->dc_ncols > 0) {
         gather_i32<<<blocks_for(g->dc_ncols), 256, 0, s>>>(as<int32_t>(g->dc_jc), g->dc_ncols, as<int32_t>(g->src_rank),
                                                            as<int32_t>(g->dc_rank));
@@ -728,7 +755,7 @@ void release_graph(gm_graph* g) {
     DevBuf* bufs[] = {&g->row_ptr, &g->col, &g->w, &g->col_ptr, &g->row, &g->cw, &g->cw8, &g->csc_pos,
                       &g->out_deg, &g->in_deg, &g->out_bin, &g->in_bin, &g->in_list, &g->zero_in_list,
                       &g->out_list, &g->zero_out_list, &g->dc_jc, &g->dc_cp, &g->dc_tile, &g->dc_head,
-                      &g->src_rank, &g->row_r, &g->dc_rank, &g->state, &g->work, &g->ctl_buf,
+                      &g->src_rank, &g->row_r, &g->row_rw, &g->dc_rank, &g->state, &g->work, &g->ctl_buf,
                       &g->reached_buf};
     for (DevBuf* b : bufs) dev_free(*b, s);
     if (g->host_pinned) cudaFreeHost(g->host_pinned);

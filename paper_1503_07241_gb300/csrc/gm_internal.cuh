@@ -19,6 +19,7 @@ constexpr int kEdgePad = 16;            // per-edge arrays carry this many spare
                                         // vector loads that start inside a row never leave the buffer
 constexpr int kChunk = 2048;            // edges of one large-vertex work item (256 threads x 8 edges)
 constexpr int kWTile = 256;             // in-edges of one warp tile of the pull side (32 lanes x 8 edges)
+constexpr int64_t kPackedMaxVertices = 1ll << 24;  // ranks that fit the 24 bits of a packed in-edge word
 
 // Library-wide count of kernel launches issued (a graph replay counts each
 // kernel node it runs).
@@ -96,6 +97,8 @@ struct Tuning {
     double sssp_pull_frac = 0.05;  // SSSP: pull when frontier edges > sssp_pull_frac * m
     int32_t pull_stage = 40960;    // SSSP pull: hottest messages staged in shared memory per CTA
     int32_t test_stall_stage = 0;  // test hook: the staging barrier waits for bytes that never come
+    int32_t test_stall_sgd = 0;    // test hook: one CTA never arrives at the first SGD grid barrier
+    int32_t pull_packed = 1;       // SSSP pull: rank and one-byte weight in one word per in-edge when possible
     int32_t direction = 0;      // 0 auto, 1 push only, 2 pull only
     int32_t loop_mode = 0;      // 0 device loop (CUDA graph with a conditional WHILE node), 1 host loop
     int32_t profile = 0;        // 1: host loop with CUDA events around every relax launch
@@ -112,7 +115,7 @@ struct RunStats {
     // profile mode: one row per superstep (see gm_get_trace)
     std::vector<double> trace;
 };
-constexpr int kTraceCols = 8;
+constexpr int kTraceCols = 10;
 
 }  // namespace gm
 
@@ -131,7 +134,9 @@ struct gm_graph {
     // program_set: the SSSP messages live in rank order so that the hottest sources'
     // messages are one contiguous prefix the pull can keep in shared memory.
     gm::DevBuf src_rank;             // rank of each vertex (int32[n])
-    gm::DevBuf row_r;                // CSC sources as ranks (int32[m + pad])
+    gm::DevBuf row_r;                // CSC sources as ranks (int32[m + pad]); empty when row_rw is built
+    gm::DevBuf row_rw;               // CSC source rank and weight in one word, (rank << 8) | weight
+                                     // (uint32[m + pad]), when every weight fits a byte and n <= 2^24
     gm::DevBuf dc_rank;              // rank of each non-empty column's vertex (int32[ncols])
     gm::DevBuf out_deg, in_deg;      // int32
     gm::DevBuf out_bin, in_bin;      // uint8 bin of each vertex by out/in degree (0 = degree zero)
@@ -191,6 +196,7 @@ namespace gm {
 gm_status trav_prepare(gm_graph* g);
 gm_status trav_reuse(gm_graph* g);  // program_set between BFS and SSSP with the workspace kept
 gm_status build_source_ranks(gm_graph* g);  // gm_graph.cu
+gm_status build_pull_edge_words(gm_graph* g);  // gm_graph.cu
 gm_status trav_set_active(gm_graph* g, const int32_t* vertices_dev, int64_t count);
 gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done);
 void trav_release(gm_graph* g);

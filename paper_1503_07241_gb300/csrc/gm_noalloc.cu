@@ -2,20 +2,21 @@
 // allocates no memory.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// traversal: code that runs while a CUDA stream is being captured (cudaMalloc is
-// not allowed there), code that owns all device memory through its own caching
-// allocator or a fixed arena, and latency-critical loops that must not pay for
-// cudaMalloc/cudaFree, which can synchronise the device and fail under memory
-// pressure.  This entry point keeps its scratch (two frontier queues and a few
-// counters) in one file-scope device array of fixed size that every GPU holds
-// for as long as the library is loaded.  The caller supplies the graph and the
-// output buffer.
+// traversal: code whose device memory is all owned by its own caching allocator
+// or a fixed arena (a cudaMalloc behind that allocator's back can fail once the
+// arena has reserved the free memory, or fragments it), and latency-critical
+// loops that must not pay for cudaMalloc/cudaFree, which can synchronise the
+// device and fail under memory pressure.  This entry point keeps its scratch
+// (two frontier queues and a few counters) in one file-scope device array of
+// fixed size that every GPU holds for as long as the library is loaded.  The
+// caller supplies the graph and the output buffer.
 //
-// The traversal is the same BFS as gm_run with GM_BFS (Section 3.II): depth 0
-// at the source, depth t+1 for every unvisited out-neighbour of a vertex reached
-// in superstep t, one superstep per level plus the final one that finds nothing.
+// The traversal gives the same result as gm_run with GM_BFS: depth 0 at the
+// source, depth t+1 for every unvisited out-neighbour of a vertex reached in
+// superstep t, one superstep per level plus the final one that finds nothing.
 // Each superstep is one launch of a top-down (push) kernel over the current
-// frontier queue.
+// frontier queue, after which the host reads the next frontier's size (the
+// call synchronises its stream once per superstep).
 #include <mutex>
 
 #include "gm_internal.cuh"

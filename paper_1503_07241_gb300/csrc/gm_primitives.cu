@@ -4,6 +4,8 @@
 #include <cstdarg>
 #include <cstdio>
 
+#include <atomic>
+
 #include "gm_internal.cuh"
 
 namespace gm {
@@ -51,13 +53,19 @@ void dev_free(DevBuf& b, cudaStream_t s) {
     b.bytes = 0;
 }
 
+// SM count of the current device, cached per device ordinal (grids sized from
+// it must fit the device they run on, e.g. a cooperative launch).
 int num_sms() {
-    static int sms = 0;
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const bool cacheable = dev >= 0 && dev < kMaxDev;
+    int sms = cacheable ? cache[dev].load(std::memory_order_relaxed) : 0;
     if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 1;
+        if (cacheable) cache[dev].store(sms, std::memory_order_relaxed);
     }
     return sms;
 }

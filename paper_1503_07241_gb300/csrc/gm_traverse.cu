@@ -66,6 +66,7 @@ struct TravArgs {
                              // indexed by source rank (msg[.][rank[v]] is vertex v's message)
     const int32_t* rank;     // SSSP: rank of each vertex by out-degree (descending)
     const int32_t* row_r;    // SSSP: CSC sources as ranks
+    const uint32_t* row_rw;  // SSSP: (rank << 8) | one-byte weight per in-edge, or nullptr
     const int32_t* dc_rank;  // SSSP: rank of each non-empty column's vertex
     int32_t hot;             // SSSP pull: messages of ranks [0, hot) are staged in shared memory
     uint32_t stage_extra;    // test hook: bytes the staging barrier expects beyond its copies (0 or 16)
@@ -575,16 +576,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 //  pull_apply (SSSP, in the finalize kernel) applies y to the vertex properties
 //          (Apply = min), makes changed vertices the next frontier and resets y
 //          to infinity.
-// One warp tile's streamed inputs per lane: 8 in-edge source ranks, their
-// weights (one-byte weights stay packed in two words until used), the lane's 8
-// first-edge bits and the tile's first column.
+// One warp tile's streamed inputs per lane: 8 in-edges (WB = 0: one word each
+// holding the source rank in its high 24 bits and the weight in its low 8;
+// otherwise source ranks plus their weights, one-byte weights packed in two words
+// until used), the lane's 8 first-edge bits and the tile's first column.
 template <int WB>
 struct PullTile {
     int32_t r[kEPT];
-    uint32_t w[WB == 1 ? 2 : kEPT];
+    uint32_t w[WB == 0 ? 1 : (WB == 1 ? 2 : kEPT)];
     uint32_t hw;
     int32_t c0;
+    __device__ __forceinline__ int32_t rank(int q) const {
+        if (WB == 0) return (int32_t)((uint32_t)r[q] >> 8);
+        return r[q];
+    }
     __device__ __forceinline__ uint32_t weight(int q) const {
+        if (WB == 0) return (uint32_t)r[q] & 0xFFu;
         if (WB == 1) return (w[q >> 2] >> (8 * (q & 3))) & 0xFFu;
         return w[q];
     }
@@ -595,12 +602,16 @@ template <int WB>
 __device__ __forceinline__ void pull_load_tile(const TravArgs& a, uint32_t k, int lane, PullTile<WB>& x) {
     const uint32_t p = k * (uint32_t)kWTile + (uint32_t)lane * kEPT;
     if (p < (uint32_t)a.m) {
-        load8(a.row_r, (int32_t)p, x.r);
+        if (WB == 0) {
+            load8(reinterpret_cast<const int32_t*>(a.row_rw), (int32_t)p, x.r);
+        } else {
+            load8(a.row_r, (int32_t)p, x.r);
+        }
         if (WB == 1) {
             const uint2 v = __ldcs(reinterpret_cast<const uint2*>(a.cw8 + p));
             x.w[0] = v.x;
             x.w[1] = v.y;
-        } else {
+        } else if (WB == 4) {
             uint32_t (&w8)[kEPT] = *reinterpret_cast<uint32_t(*)[kEPT]>(&x.w[0]);
             load8(a.cw, (int32_t)p, w8);
         }
@@ -616,21 +627,26 @@ __device__ __forceinline__ uint32_t lane_valid(uint32_t e0, uint32_t m) { return
 // global memory.  Only the last tile can hold edges at or past m: there
 // (`last`) they read rank 0's message (present whenever there is an edge) and
 // are masked later; every other tile skips the masking.
+template <int WB>
 __device__ __forceinline__ void pull_gather(const uint32_t* __restrict__ msgc, const uint32_t* s_hot, int32_t hlim,
-                                            bool last, uint32_t nv, const int32_t (&r)[kEPT], uint32_t (&mv)[kEPT]) {
+                                            bool last, uint32_t nv, const PullTile<WB>& x, uint32_t (&mv)[kEPT]) {
     if (!last) {
 #pragma unroll
-        for (int q = 0; q < kEPT; ++q) mv[q] = r[q] < hlim ? s_hot[r[q]] : __ldg(msgc + r[q]);
+        for (int q = 0; q < kEPT; ++q) {
+            const int32_t rq = x.rank(q);
+            mv[q] = rq < hlim ? s_hot[rq] : __ldg(msgc + rq);
+        }
         return;
     }
 #pragma unroll
     for (int q = 0; q < kEPT; ++q) {
-        const int32_t rq = (uint32_t)q < nv ? r[q] : 0;
+        const int32_t rq = (uint32_t)q < nv ? x.rank(q) : 0;
         mv[q] = rq < hlim ? s_hot[rq] : __ldg(msgc + rq);
     }
 }
 
-// WB: bytes per in-edge weight read (1: the uint8 copy, 4: the uint32 array).
+// WB: bytes per in-edge weight read (0: packed with the rank in one word,
+// 1: the uint8 copy, 4: the uint32 array).
 // One CTA of kPullThreads per SM; dynamic shared memory holds a.hot messages.
 // Software pipeline per warp: while tile k is reduced, the messages of tile k+1
 // are being gathered and the sources of tile k+2 streamed in.
@@ -672,7 +688,7 @@ __global__ void __launch_bounds__(kPullThreads, 1) trav_pull_a(TravArgs a) {
     const int32_t hlim = staged ? hot : 0;  // without the staged block every message is gathered
     uint32_t mv[kEPT];
     if (gwarp < ntiles)
-        pull_gather(msgc, s_hot, hlim, gwarp + 1 == ntiles, lane_valid(gwarp * kWTile + lane * kEPT, m), cur.r, mv);
+        pull_gather<WB>(msgc, s_hot, hlim, gwarp + 1 == ntiles, lane_valid(gwarp * kWTile + lane * kEPT, m), cur, mv);
 
     for (uint32_t k = gwarp; k < ntiles; k += nwarps) {
         const uint32_t nv = lane_valid(k * kWTile + lane * kEPT, m);
@@ -690,7 +706,7 @@ __global__ void __launch_bounds__(kPullThreads, 1) trav_pull_a(TravArgs a) {
         // pipeline: gather tile k+1's messages, stream tile k+2's sources
         const uint32_t k1 = k + nwarps, k2 = k1 + nwarps;
         if (k1 < ntiles)
-            pull_gather(msgc, s_hot, hlim, k1 + 1 == ntiles, lane_valid(k1 * kWTile + lane * kEPT, m), nxt.r, mv);
+            pull_gather<WB>(msgc, s_hot, hlim, k1 + 1 == ntiles, lane_valid(k1 * kWTile + lane * kEPT, m), nxt, mv);
         cur = nxt;
         if (k2 < ntiles) pull_load_tile<WB>(a, k2, lane, nxt);
         scanned += nv;
@@ -1498,6 +1514,7 @@ TravArgs make_args(gm_graph* g) {
     }
     a.rank = as<int32_t>(g->src_rank);
     a.row_r = as<int32_t>(g->row_r);
+    a.row_rw = as<uint32_t>(g->row_rw);
     a.dc_rank = as<int32_t>(g->dc_rank);
     a.hot = g->src_rank.p ? (int32_t)std::min<int64_t>(std::min<int64_t>(kHotMax, g->tune.pull_stage),
                                                          g->n & ~(int64_t)3)
@@ -1527,11 +1544,18 @@ int push_grid() {
 int pull_grid() {
     static int blocks = [] {
         const int bytes = (int)(kHotMax * sizeof(uint32_t));
+        cudaFuncSetAttribute(trav_pull_a<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         cudaFuncSetAttribute(trav_pull_a<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         cudaFuncSetAttribute(trav_pull_a<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         return num_sms();
     }();
     return blocks;
+}
+
+// The SSSP pull variant for the handle's in-edge layout.
+const void* pull_a_kernel(const TravArgs& a) {
+    if (a.row_rw) return (const void*)trav_pull_a<0>;
+    return a.cw8 ? (const void*)trav_pull_a<1> : (const void*)trav_pull_a<4>;
 }
 
 int pull_bu_grid() {
@@ -1670,7 +1694,7 @@ gm_status build_loop_graph(gm_graph* g, bool sssp) {
     if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n0, body, &ns, 1, &kp);
     cudaGraphNode_t n1b = nullptr;
     if (e == cudaSuccess) {
-        kp.func = !sssp ? (void*)trav_pull_bu : a.cw8 ? (void*)trav_pull_a<1> : (void*)trav_pull_a<4>;
+        kp.func = !sssp ? (void*)trav_pull_bu : const_cast<void*>(pull_a_kernel(a));
         kp.gridDim = dim3((unsigned)(sssp ? pull_grid() : pull_bu_grid()));
         kp.blockDim = dim3(sssp ? kPullThreads : kThreads);
         kp.sharedMemBytes = sssp ? (unsigned)a.hot * 4u : 0u;
@@ -1831,9 +1855,13 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
             if (sssp) trav_push<true><<<pg, kThreads, 0, s>>>(a);
             else trav_push<false><<<pg, kThreads, 0, s>>>(a);
             if (evA) cudaEventRecord(evA, s);
-            if (sssp && a.cw8) trav_pull_a<1><<<lg, kPullThreads, (size_t)a.hot * 4u, s>>>(a);
-            else if (sssp) trav_pull_a<4><<<lg, kPullThreads, (size_t)a.hot * 4u, s>>>(a);
-            else trav_pull_bu<<<lg, kThreads, 0, s>>>(a);
+            if (sssp) {
+                void* pargs[] = {&a};
+                GM_CUDA_TRY(cudaLaunchKernel(pull_a_kernel(a), dim3(lg), dim3(kPullThreads), pargs,
+                                             (size_t)a.hot * 4u, s));
+            } else {
+                trav_pull_bu<<<lg, kThreads, 0, s>>>(a);
+            }
             if (evB) cudaEventRecord(evB, s);
             g_launches += 2;
             LAUNCH_OK();
@@ -1846,9 +1874,11 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
                                         cudaMemcpyDeviceToHost, s));
             GM_CUDA_TRY(cudaStreamSynchronize(s));
             if (ev0) {
-                float ms = 0.f, ms_pull = 0.f;
+                float ms = 0.f, ms_pull = 0.f, ms_push = 0.f, ms_fin = 0.f;
                 cudaEventElapsedTime(&ms, ev0, ev1);
                 cudaEventElapsedTime(&ms_pull, evA, evB);
+                cudaEventElapsedTime(&ms_push, ev0, evA);
+                cudaEventElapsedTime(&ms_fin, evB, ev1);
                 g->stats.relax_ms += ms;
                 g->stats.relax_launches++;
                 const uint32_t done = hp->c.done;
@@ -1857,7 +1887,8 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
                 const double row[kTraceCols] = {(double)it, (double)dir_before, (double)frontier_before,
                                                 (double)(hp->c.scanned_edges - prev_e),
                                                 (double)(hp->c.processed_vertices - prev_v), (double)ms,
-                                                (double)hp->c.medges[(it + 1) % 3], (double)ms_pull};
+                                                (double)hp->c.medges[(it + 1) % 3], (double)ms_pull,
+                                                (double)ms_push, (double)ms_fin};
                 prev_e = hp->c.scanned_edges;
                 prev_v = hp->c.processed_vertices;
                 g->stats.trace.insert(g->stats.trace.end(), row, row + kTraceCols);

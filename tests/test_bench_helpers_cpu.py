@@ -59,9 +59,10 @@ def test_pull_roofline_adds_the_sssp_pull_launches_only():
 
     class FakeGraph:
         n = 10
-        # (superstep, dir, active, edges, vertices, superstep ms, next edges, pull ms)
-        traces = {FakeGM.GM_BFS: [[0, 0, 1, 100, 1, 0.1, 0, 0.0], [1, 1, 5, 800, 6, 0.2, 0, 0.15]],
-                  FakeGM.GM_SSSP: [[0, 0, 1, 100, 1, 0.1, 0, 0.0], [1, 1, 9, 1000, 6, 0.5, 0, 0.4]]}
+        # (superstep, dir, active, edges, vertices, superstep ms, next edges, pull ms, push ms, finalize ms)
+        traces = {FakeGM.GM_BFS: [[0, 0, 1, 100, 1, 0.1, 0, 0.0, 0.05, 0.02], [1, 1, 5, 800, 6, 0.2, 0, 0.15, 0, 0]],
+                  FakeGM.GM_SSSP: [[0, 0, 1, 100, 1, 0.1, 0, 0.0, 0.06, 0.02],
+                                   [1, 1, 9, 1000, 6, 0.5, 0, 0.4, 0.003, 0.08]]}
 
         def __init__(self):
             self.kind = None
@@ -101,6 +102,15 @@ def test_pull_roofline_adds_the_sssp_pull_launches_only():
     assert abs(r["frac"] - r["achieved"] / 6000.0) < 1e-12
     assert r["bfs_pull_bottom_up"]["launches"] == 2
     assert r["bfs_pull_bottom_up"]["in_edges_checked_per_launch"] == 800
+    # SSSP push superstep 0 (1 frontier vertex, 100 edges): 12 B + 16 B per edge, 0.06 ms
+    push = r["sssp_push"]
+    assert push["launches"] == 2 and push["bytes_per_launch"] == 12 + 1600
+    assert abs(push["achieved"] - (12 + 1600) / 0.06e-3 / 1e9) < 1e-9
+    # finalize after that push: the 9 vertices of the next frontier, 16 B each
+    assert r["sssp_finalize_after_push"]["bytes_per_launch"] == 16 * 9
+    # finalize after the pull: 6 non-empty columns x 12 B + 6 received x 12 B, no next frontier
+    fp = r["sssp_finalize_after_pull"]
+    assert fp["bytes_per_launch"] == 12 * 6 + 12 * 6 and abs(fp["avg_launch_us"] - 80.0) < 1e-9
 
 
 def test_recorded_traffic_is_dropped_when_the_kernel_source_changes(monkeypatch):

@@ -189,3 +189,41 @@ def test_full_config_one_step_on_sampled_vertices(gm, full_cf):
     for v in list(rng.choice(nu, 8, replace=False)) + list(nu + rng.choice(ni, 4, replace=False)):
         ref = og.cf_vertex_step(K, LAM, gamma, p0, int(v))
         assert np.max(np.abs(p1[v] - ref)) <= 1e-4 * max(np.max(np.abs(ref)), 1e-3)
+
+
+# Step size of the full-workload gradient-descent check.  With the specified
+# gamma = 1e-3 full-batch gradient descent on this workload diverges in FP64 as
+# well (the users with ~17,800 ratings take steps that grow their factors
+# geometrically; the oracle's loss overflows by the seventh step), and at 1e-4 its
+# loss rises again after the seventh step; 1e-5 is the largest power of ten
+# <= 1e-3 at which the FP64 oracle's loss decreases in all 10 steps
+# (tests/golden/cf_full_gamma_search.json, written by the script beside it).
+CF_FULL_GAMMA = 1e-5
+
+
+@pytest.mark.slow
+def test_full_config_ten_steps_match_oracle(gm, full_cf):
+    """480,000 users x 17,800 items, ~100M ratings, K = 32, lambda 0.05: ten
+    Jacobi gradient steps of Eqs. 3-5 at CF_FULL_GAMMA.  Every factor against
+    the FP64 oracle's ten steps from the same initial factors: relative
+    Frobenius error and max-abs error over the largest factor both <= 1e-4, the
+    Eq. 2 loss within 1e-5 relative, and the oracle's loss decreasing."""
+    nu, ni, n, s, d, r, og = full_cf
+    g = gm.Graph(n, s, d, r, n_left=nu)
+    K = 32
+    g.program_set(gm.GM_CF, K=K, lam=LAM, gamma=CF_FULL_GAMMA, init_sigma=0.1, seed=5)
+    p0 = g.state().astype(np.float64)
+    assert g.run(10) == 10
+    got = g.state().astype(np.float64)
+    loss = g.scalar(gm.GM_SCALAR_CF_LOSS)
+    g.close()
+    ref, trace = og.cf_gd(K, LAM, CF_FULL_GAMMA, 10, p0)
+    assert np.all(np.diff(trace) < 0), "the oracle's loss decreases at this step size"
+    err_fro = _rel_fro(got, ref)
+    err_max = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    err_upd = _rel_fro(got - p0, ref - p0)
+    print(f"full CF GD: rel fro {err_fro:.3e}, max-abs/max {err_max:.3e}, update rel fro {err_upd:.3e}, "
+          f"loss {loss:.6e} vs {trace[-1]:.6e}")
+    assert err_fro <= 1e-4
+    assert err_max <= 1e-4
+    assert abs(loss - trace[-1]) <= 1e-5 * trace[-1]

@@ -65,3 +65,29 @@ def test_staging_wait_runs_out(gm):
     it = g.run(-1)
     want, wit = og.sssp([0])
     assert np.array_equal(g.state(), want) and it == wit
+
+
+def test_sgd_grid_barrier_wait_runs_out(gm):
+    """The grid barrier between SGD strata is made to wait for a CTA that never
+    arrives (test hook GM_OPT_TEST_STALL_SGD: the last CTA skips its arrival at
+    the first barrier and the wait limit drops to half a second): every CTA's
+    bounded wait gives up, the kernel ends, gm_run reports GM_ERR_TIMEOUT, and
+    after the hook is cleared the same handle runs two epochs that equal the
+    oracle's serial SGD (Section 3.III; stratified order)."""
+    import synth
+    nu, ni = 2000, 300
+    n, s, d, r = synth.chung_lu_bipartite(nu, ni, 1.1, 5e4, seed=17)
+    g = gm.Graph(n, s, d, r, n_left=nu)
+    og = oracle.Graph(n, s, d, r)
+    g.set_option(gm.GM_OPT_TEST_STALL_SGD, 1)
+    g.program_set(gm.GM_CF_SGD, K=32, lam=0.05, gamma=1e-2, init_sigma=0.1, seed=3, cf_strata=64)
+    with pytest.raises(gm.GMError) as ei:
+        g.run(1)
+    assert ei.value.status == gm.GM_ERR_TIMEOUT
+    assert "never arrived" in str(ei.value)
+    g.set_option(gm.GM_OPT_TEST_STALL_SGD, 0)
+    g.program_set(gm.GM_CF_SGD, K=32, lam=0.05, gamma=1e-2, init_sigma=0.1, seed=3, cf_strata=64)
+    p0 = g.state().astype(np.float64)
+    ref = og.cf_sgd(32, 0.05, 1e-2, 2, nu, 64, p0)
+    assert g.run(2) == 2
+    np.testing.assert_allclose(g.state().astype(np.float64), ref, rtol=1e-4, atol=2e-5)

@@ -42,6 +42,31 @@ def test_rmat_small_parity(gm, kind, direction):
         assert it == rit
 
 
+@pytest.mark.parametrize("packed", [1, 0])
+@pytest.mark.parametrize("stage", [40960, 0])
+def test_sssp_pull_in_edge_layouts(gm, packed, stage):
+    """The SSSP pull with each in-edge as one word (source rank << 8 | weight)
+    and with separate rank and one-byte weight arrays, with and without the
+    shared-memory stage, forced to pull every superstep and automatic: exact
+    distances and superstep counts on an RMAT graph of several thousand warp
+    tiles and a ragged last tile.  The layout option switched back and forth on
+    one handle rebuilds the in-edge stream."""
+    n, s, d, w = rmat_case(14, weighted=True)
+    g = gm.Graph(n, s, d, w)
+    og = oracle.Graph(n, s, d, w)
+    assert g.m % 256 != 0
+    g.program_set(gm.GM_SSSP)  # ranks and the default (packed) layout
+    g.set_option(gm.GM_OPT_PULL_PACKED, 1 - packed)
+    g.set_option(gm.GM_OPT_PULL_PACKED, packed)
+    g.set_option(gm.GM_OPT_PULL_STAGE, stage)
+    for direction in (2, 0):
+        g.set_option(gm.GM_OPT_DIRECTION, direction)
+        for src in synth.pick_sources(n, s, d, 3, seed=12):
+            got, it = _run(gm, g, gm.GM_SSSP, [src])
+            ref, rit = og.sssp([src])
+            assert np.array_equal(got, ref) and it == rit
+
+
 @pytest.mark.parametrize("loop_mode", [0, 1])
 @pytest.mark.parametrize("seed", range(3))
 def test_random_graphs_multi_source(gm, seed, loop_mode):

@@ -1,16 +1,18 @@
 """gm_bfs_csr_noalloc: the allocation-free BFS entry point, called through the C
-ABI, against the regular graph-handle BFS (gm_run with GM_BFS).
+ABI, against the regular graph-handle BFS (gm_run with GM_BFS) and the oracle.
 
 The entry point exists for callers that cannot allocate device memory when they
-need a traversal (during stream capture, under their own memory arena, or in
-loops that must not pay for cudaMalloc).  Its scratch is a fixed device array
-shared by every call, so the test makes two calls in a row on the same graph and
-checks that the second is not disturbed by what the first left behind.  This file
-is collected last so that a failure here does not hide any other test.
+need a traversal: code whose device memory is all owned by its own arena or
+caching allocator, and loops that must not pay for cudaMalloc/cudaFree.  Its
+scratch is a fixed device array shared by every call, so the test makes two
+calls in a row on the same graph and checks that the second is not disturbed by
+what the first left behind.  This file is collected last so that a failure here
+does not hide any other test.
 """
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -38,6 +40,7 @@ def test_noalloc_bfs_matches_graph_bfs_twice(gm):
     g = gm.Graph(n, s, d)
     row_ptr, col = _csr_tensors(g)
     srcs = synth.pick_sources(n, s, d, 2, seed=41)
+    og = oracle.Graph(n, s, d)
     depth = torch.empty(n, dtype=torch.int32, device="cuda")
     for src in srcs:  # two calls in a row share the fixed scratch
         it = gm.bfs_csr_noalloc(row_ptr, col, int(src), depth)
@@ -45,6 +48,9 @@ def test_noalloc_bfs_matches_graph_bfs_twice(gm):
         ref, rit = _reference(gm, g, int(src))
         assert np.array_equal(got, ref)
         assert it == rit
+        oref, oit = og.bfs([int(src)])  # the FP64 oracle's Algorithm 2 BFS
+        assert np.array_equal(got, oref)
+        assert it == oit
 
 
 def test_noalloc_bfs_rejects_too_many_vertices(gm):
