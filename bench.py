@@ -179,7 +179,10 @@ ABLATIONS = (("tuned", {}),
              ("pull only", {"GM_OPT_DIRECTION": 2}),
              ("no degree bins (a warp per vertex)", {"GM_OPT_BIN_LARGE": 1 << 30, "GM_OPT_BIN_SMALL": 1}),
              ("no shared-memory stage in the SSSP pull", {"GM_OPT_PULL_STAGE": 0}),
-             ("host-driven superstep loop (no CUDA graph)", {"GM_OPT_LOOP_MODE": 1}))
+             ("source rank and weight as separate arrays in the SSSP pull", {"GM_OPT_PULL_PACKED": 0}),
+             ("host-driven superstep loop (no CUDA graph)", {"GM_OPT_LOOP_MODE": 1}),
+             ("sorted (index, value) list instead of bitvector + dense array (host-driven loop)",
+              {"GM_OPT_SPARSE_LIST": 1}))
 
 
 def ablation(gm, g, bfs_src, sssp_src, src_dev, tuning):
@@ -196,6 +199,8 @@ def ablation(gm, g, bfs_src, sssp_src, src_dev, tuning):
         # back to the tuned setting
         g.set_option(gm.GM_OPT_DIRECTION, 0)
         g.set_option(gm.GM_OPT_LOOP_MODE, 0)
+        g.set_option(gm.GM_OPT_SPARSE_LIST, 0)
+        g.set_option(gm.GM_OPT_PULL_PACKED, 1)
         g.set_option(gm.GM_OPT_BIN_LARGE, int(tuning["bin_large"]) if tuning else 2048)
         g.set_option(gm.GM_OPT_BIN_SMALL, int(tuning["bin_small"]) if tuning else 32)
         g.set_option(gm.GM_OPT_PULL_STAGE, int(tuning["pull_stage"]) if tuning else 40960)

@@ -371,10 +371,16 @@ enum {
                                      cut from about ten seconds to about half a second, so every CTA's
                                      wait runs out, the kernel ends, gm_run returns GM_ERR_TIMEOUT and
                                      the factors are left part-way through the first stratum */
-    GM_OPT_PULL_PACKED = 12       /* SSSP pull in-edge layout: 1 (default) one 32-bit word per in-edge,
+    GM_OPT_PULL_PACKED = 12,      /* SSSP pull in-edge layout: 1 (default) one 32-bit word per in-edge,
                                      source rank << 8 | weight, when every weight is below 256 and
                                      n <= 2^24; 0 the source rank and the weight as separate arrays.
                                      Results are identical. */
+    GM_OPT_SPARSE_LIST = 13       /* ablation of the sparse-vector form (Section 4.3.2, Fig. 7): 1 keeps
+                                     each pull superstep's frontier as a sorted array of (index, value)
+                                     tuples, rebuilt at its start, and the BFS/SSSP pull finds a source
+                                     by binary search in it instead of one bitvector / dense-array load;
+                                     runs the superstep loop from the host (as GM_OPT_LOOP_MODE = 1).
+                                     0 (default): bitvector + dense array.  Results are identical. */
 };
 GM_API gm_status gm_set_option(gm_graph* g, int32_t option, int64_t value);
 

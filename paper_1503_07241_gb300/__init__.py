@@ -26,7 +26,7 @@ GM_PAGERANK, GM_BFS, GM_SSSP, GM_TRIANGLE_COUNT, GM_CF, GM_CONNECTED_COMPONENTS,
  GM_SCALAR_CF_STRATA, GM_SCALAR_PULL_EDGE_BYTES) = range(1, 14)
 (GM_OPT_DIRECTION, GM_OPT_LOOP_MODE, GM_OPT_PROFILE, GM_OPT_BIN_SMALL, GM_OPT_BIN_LARGE,
  GM_OPT_ALPHA_X1000, GM_OPT_BETA_X1000, GM_OPT_SSSP_PULL_PPM, GM_OPT_PULL_STAGE,
- GM_OPT_TEST_STALL_STAGE, GM_OPT_TEST_STALL_SGD, GM_OPT_PULL_PACKED) = range(1, 13)
+ GM_OPT_TEST_STALL_STAGE, GM_OPT_TEST_STALL_SGD, GM_OPT_PULL_PACKED, GM_OPT_SPARSE_LIST) = range(1, 14)
 INF_U32 = 0xFFFFFFFF
 TRACE_COLS = 10  # doubles per row of gm_get_trace
 

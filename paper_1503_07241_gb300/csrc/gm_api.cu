@@ -338,6 +338,10 @@ gm_status gm_set_option(gm_graph* g, int32_t option, int64_t value) {
             if (value < 0 || value > 1) break;
             t.test_stall_sgd = (int32_t)value;
             return GM_OK;
+        case GM_OPT_SPARSE_LIST:
+            if (value < 0 || value > 1) break;
+            t.sparse_list = (int32_t)value;
+            return GM_OK;
         case GM_OPT_PULL_PACKED:
             if (value < 0 || value > 1) break;
             if (t.pull_packed == (int32_t)value) return GM_OK;

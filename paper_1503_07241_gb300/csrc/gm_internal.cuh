@@ -86,6 +86,8 @@ struct TravCtl {
     uint32_t stage_timeouts;      // pull CTAs whose shared-memory staging copy did not complete in time
     uint32_t loops;               // iterations of the device loop (for the launch count)
     unsigned long long reached;   // out-degrees of the vertices whose property became finite since the reset
+    uint32_t list_len;            // sorted-list sparse vector: entries of the current superstep's list
+    uint32_t list_pad;
 };
 
 // Options and tuning knobs of a graph handle.
@@ -99,6 +101,7 @@ struct Tuning {
     int32_t test_stall_stage = 0;  // test hook: the staging barrier waits for bytes that never come
     int32_t test_stall_sgd = 0;    // test hook: one CTA never arrives at the first SGD grid barrier
     int32_t pull_packed = 1;       // SSSP pull: rank and one-byte weight in one word per in-edge when possible
+    int32_t sparse_list = 0;       // 1: pull supersteps look the frontier up in a sorted (index, value) list
     int32_t direction = 0;      // 0 auto, 1 push only, 2 pull only
     int32_t loop_mode = 0;      // 0 device loop (CUDA graph with a conditional WHILE node), 1 host loop
     int32_t profile = 0;        // 1: host loop with CUDA events around every relax launch

@@ -70,6 +70,9 @@ struct TravArgs {
     const int32_t* dc_rank;  // SSSP: rank of each non-empty column's vertex
     int32_t hot;             // SSSP pull: messages of ranks [0, hot) are staged in shared memory
     uint32_t stage_extra;    // test hook: bytes the staging barrier expects beyond its copies (0 or 16)
+    uint32_t* lkey;          // sorted-list sparse vector (GM_OPT_SPARSE_LIST): indices, ascending
+    uint32_t* lval;          //   and values (SSSP messages) of the current pull superstep's frontier
+    uint32_t* ltile;         //   per-tile counts, then offsets, of the list build
     uint32_t* ycol;          // pull: reduced value per non-empty column, infinity between supersteps
     const uint32_t* dc_head; // pull: first-edge-of-column bits
     uint32_t* bv[3];         // frontier bitvectors, rotating by superstep
@@ -551,6 +554,153 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 
+// ---------------------------------------------------------------- sorted-list sparse vector
+// Section 4.3.2 names two forms of the sparse vector: a variable-sized array of
+// (index, value) tuples sorted by index, and a bitvector of valid indices beside
+// a dense value array; the paper keeps the second because the test "is j present
+// in x" of Algorithm 1 becomes one bit lookup (its Fig. 7 measures the gain).
+// The engine keeps the second form too (the frontier bitvector, and for SSSP a
+// dense message array holding infinity off the frontier).  For that ablation the
+// option GM_OPT_SPARSE_LIST rebuilds, at the start of every pull superstep, the
+// frontier as the first form -- indices ascending (SSSP: source ranks with their
+// messages; BFS: vertex ids) -- in three kernels (count per tile, scan of the
+// tile counts, scatter), and the pull kernels find a source's message or
+// membership by binary search in that list instead of one load.
+constexpr int kListThreads = 256;
+constexpr int kListPer = 8;
+constexpr int kListTile = kListThreads * kListPer;  // 2048 indices per tile
+
+template <bool SSSP>
+__device__ __forceinline__ bool list_valid(const TravArgs& a, uint32_t t, int64_t i, uint32_t* val) {
+    if (SSSP) {
+        const uint32_t m = a.msg[t & 1u][i];
+        *val = m;
+        return m != kInf;
+    }
+    *val = 0u;
+    return (a.bv[t % 3u][i >> 5] >> (i & 31)) & 1u;
+}
+
+// Entries of every tile of 2048 indices into ltile[tile].
+template <bool SSSP>
+__global__ void __launch_bounds__(kListThreads) list_count(TravArgs a) {
+    TravCtlDev* cd = a.ctl;
+    if (cd->c.done || cd->c.dir != 1u) return;
+    const uint32_t t = cd->c.iter;
+    __shared__ uint32_t s_w[kListThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t ntiles = (a.n + kListTile - 1) / kListTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int k = 0; k < kListPer; ++k) {
+            const int64_t i = tile * kListTile + k * kListThreads + threadIdx.x;
+            uint32_t v;
+            if (i < a.n && list_valid<SSSP>(a, t, i, &v)) ++c;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+        if (lane == 0) s_w[wid] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (int w = 0; w < kListThreads / 32; ++w) tot += s_w[w];
+            a.ltile[tile] = tot;
+        }
+        __syncthreads();
+    }
+}
+
+// One CTA: exclusive scan of the tile counts in place; the total is the list length.
+constexpr int kListScanThreads = 1024;
+__global__ void __launch_bounds__(kListScanThreads) list_scan(TravArgs a) {
+    TravCtlDev* cd = a.ctl;
+    if (cd->c.done || cd->c.dir != 1u) return;
+    __shared__ uint32_t s_w[kListScanThreads / 32];
+    const int64_t ntiles = (a.n + kListTile - 1) / kListTile;
+    const int64_t per = (ntiles + kListScanThreads - 1) / kListScanThreads;
+    const int64_t b = threadIdx.x * per, e = min(b + per, ntiles);
+    uint32_t sum = 0;
+    for (int64_t i = b; i < e; ++i) sum += a.ltile[i];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t incl = warp_incl_scan(sum);
+    if (lane == 31) s_w[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const uint32_t x = warp_incl_scan(s_w[lane]);
+        s_w[lane] = x;
+    }
+    __syncthreads();
+    uint32_t run = incl - sum + (wid > 0 ? s_w[wid - 1] : 0u);  // exclusive prefix of this thread
+    for (int64_t i = b; i < e; ++i) {
+        const uint32_t c = a.ltile[i];
+        a.ltile[i] = run;
+        run += c;
+    }
+    if (threadIdx.x == kListScanThreads - 1) cd->c.list_len = s_w[31];
+}
+
+// Every tile's entries at its offset, in index order (eight block-wide rounds of
+// 256 consecutive indices, each ranked with a ballot).
+template <bool SSSP>
+__global__ void __launch_bounds__(kListThreads) list_scatter(TravArgs a) {
+    TravCtlDev* cd = a.ctl;
+    if (cd->c.done || cd->c.dir != 1u) return;
+    const uint32_t t = cd->c.iter;
+    __shared__ uint32_t s_w[kListThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t ntiles = (a.n + kListTile - 1) / kListTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        uint32_t base = a.ltile[tile];
+#pragma unroll 1
+        for (int k = 0; k < kListPer; ++k) {
+            const int64_t i = tile * kListTile + k * kListThreads + threadIdx.x;
+            uint32_t v = 0;
+            const bool f = i < a.n && list_valid<SSSP>(a, t, i, &v);
+            const uint32_t bal = __ballot_sync(kFull, f);
+            if (lane == 0) s_w[wid] = (uint32_t)__popc(bal);
+            __syncthreads();
+            uint32_t before = 0, total = 0;
+#pragma unroll
+            for (int w = 0; w < kListThreads / 32; ++w) {
+                const uint32_t c = s_w[w];
+                before += w < wid ? c : 0u;
+                total += c;
+            }
+            if (f) {
+                const uint32_t pos = base + before + (uint32_t)__popc(bal & ((1u << lane) - 1u));
+                a.lkey[pos] = (uint32_t)i;
+                if (SSSP) a.lval[pos] = v;
+            }
+            base += total;
+            __syncthreads();
+        }
+    }
+}
+
+// Position of the first list entry whose index is >= k (binary search).
+__device__ __forceinline__ uint32_t list_lower(const uint32_t* __restrict__ key, uint32_t len, uint32_t k) {
+    uint32_t lo = 0, cnt = len;
+    while (cnt > 0) {
+        const uint32_t half = cnt >> 1;
+        if (__ldg(key + lo + half) < k) {
+            lo += half + 1u;
+            cnt -= half + 1u;
+        } else {
+            cnt = half;
+        }
+    }
+    return lo;
+}
+
+// Whether source u is in the frontier (BFS pull): bitvector, or list search.
+template <bool LIST>
+__device__ __forceinline__ bool in_frontier(const TravArgs& a, const uint32_t* bvc, uint32_t len, int32_t u) {
+    if (!LIST) return test_bit(bvc, u);
+    const uint32_t p = list_lower(a.lkey, len, (uint32_t)u);
+    return p < len && __ldg(a.lkey + p) == (uint32_t)u;
+}
+
 // ---------------------------------------------------------------- pull
 // Pull over the doubly compressed CSC (non-empty columns only).
 //  pull_a  (SSSP) streams the in-edges in warp tiles of kWTile: each lane reads 8
@@ -645,12 +795,26 @@ __device__ __forceinline__ void pull_gather(const uint32_t* __restrict__ msgc, c
     }
 }
 
+// Messages of a tile's sources looked up in the sorted list (GM_OPT_SPARSE_LIST):
+// infinity for a source not in it.
+template <int WB>
+__device__ __forceinline__ void pull_gather_list(const TravArgs& a, uint32_t len, bool last, uint32_t nv,
+                                                 const PullTile<WB>& x, uint32_t (&mv)[kEPT]) {
+#pragma unroll
+    for (int q = 0; q < kEPT; ++q) {
+        const uint32_t rq = (last && (uint32_t)q >= nv) ? 0u : (uint32_t)x.rank(q);
+        const uint32_t p = list_lower(a.lkey, len, rq);
+        mv[q] = (p < len && __ldg(a.lkey + p) == rq) ? __ldg(a.lval + p) : kInf;
+    }
+}
+
 // WB: bytes per in-edge weight read (0: packed with the rank in one word,
-// 1: the uint8 copy, 4: the uint32 array).
+// 1: the uint8 copy, 4: the uint32 array).  LIST: sources are looked up in the
+// sorted-list sparse vector (no shared-memory stage).
 // One CTA of kPullThreads per SM; dynamic shared memory holds a.hot messages.
 // Software pipeline per warp: while tile k is reduced, the messages of tile k+1
 // are being gathered and the sources of tile k+2 streamed in.
-template <int WB>
+template <int WB, bool LIST>
 __global__ void __launch_bounds__(kPullThreads, 1) trav_pull_a(TravArgs a) {
     extern __shared__ __align__(128) uint32_t s_hot[];
     __shared__ __align__(8) uint64_t s_bar;
@@ -659,7 +823,8 @@ __global__ void __launch_bounds__(kPullThreads, 1) trav_pull_a(TravArgs a) {
     const uint32_t t = cd->c.iter;
     const int clr = (int)((t + 2u) % 3u);
     const uint32_t* __restrict__ msgc = a.msg[t & 1u];
-    const int32_t hot = a.hot;  // a multiple of 4, so the copy is whole 16-byte units
+    const uint32_t llen = LIST ? cd->c.list_len : 0u;
+    const int32_t hot = LIST ? 0 : a.hot;  // a multiple of 4, so the copy is whole 16-byte units
     if (threadIdx.x == 0 && hot > 0) {
         mbar_init(&s_bar, 1u);
         fence_mbar_init();
@@ -687,8 +852,13 @@ __global__ void __launch_bounds__(kPullThreads, 1) trav_pull_a(TravArgs a) {
     if (!staged && hot > 0 && threadIdx.x == 0) atomicAdd(&cd->c.stage_timeouts, 1u);
     const int32_t hlim = staged ? hot : 0;  // without the staged block every message is gathered
     uint32_t mv[kEPT];
-    if (gwarp < ntiles)
-        pull_gather<WB>(msgc, s_hot, hlim, gwarp + 1 == ntiles, lane_valid(gwarp * kWTile + lane * kEPT, m), cur, mv);
+    if (gwarp < ntiles) {
+        if (LIST)
+            pull_gather_list<WB>(a, llen, gwarp + 1 == ntiles, lane_valid(gwarp * kWTile + lane * kEPT, m), cur, mv);
+        else
+            pull_gather<WB>(msgc, s_hot, hlim, gwarp + 1 == ntiles, lane_valid(gwarp * kWTile + lane * kEPT, m), cur,
+                            mv);
+    }
 
     for (uint32_t k = gwarp; k < ntiles; k += nwarps) {
         const uint32_t nv = lane_valid(k * kWTile + lane * kEPT, m);
@@ -705,8 +875,13 @@ __global__ void __launch_bounds__(kPullThreads, 1) trav_pull_a(TravArgs a) {
         const int32_t c0 = cur.c0;
         // pipeline: gather tile k+1's messages, stream tile k+2's sources
         const uint32_t k1 = k + nwarps, k2 = k1 + nwarps;
-        if (k1 < ntiles)
-            pull_gather<WB>(msgc, s_hot, hlim, k1 + 1 == ntiles, lane_valid(k1 * kWTile + lane * kEPT, m), nxt, mv);
+        if (k1 < ntiles) {
+            if (LIST)
+                pull_gather_list<WB>(a, llen, k1 + 1 == ntiles, lane_valid(k1 * kWTile + lane * kEPT, m), nxt, mv);
+            else
+                pull_gather<WB>(msgc, s_hot, hlim, k1 + 1 == ntiles, lane_valid(k1 * kWTile + lane * kEPT, m), nxt,
+                                mv);
+        }
         cur = nxt;
         if (k2 < ntiles) pull_load_tile<WB>(a, k2, lane, nxt);
         scanned += nv;
@@ -800,11 +975,13 @@ constexpr int kBuCols = 2;       // the same in the bottom-up BFS pull (more sta
 
 // BFS pull superstep in one kernel: the bottom-up search and Apply.  A column is
 // owned by one lane, so the depth is written and the vertex queued directly.
+template <bool LIST>
 __global__ void __launch_bounds__(kThreads, 4) trav_pull_bu(TravArgs a) {
     TravCtlDev* cd = a.ctl;
     if (cd->c.done || cd->c.dir != 1u) return;
     const uint32_t t = cd->c.iter;
     const int cur = (int)(t % 3u), nxt = (int)((t + 1u) % 3u), clr = (int)((t + 2u) % 3u);
+    const uint32_t llen = LIST ? cd->c.list_len : 0u;
     relax_prologue<false>(a, &cd->c, t, clr);
     __shared__ WarpQ s_q[kWarps];
     __shared__ unsigned long long s_stat[6];
@@ -866,7 +1043,7 @@ __global__ void __launch_bounds__(kThreads, 4) trav_pull_bu(TravArgs a) {
                     p[k] += nn;
                 }
 #pragma unroll
-                for (int j = 0; j < 4; ++j) found[k] |= u[k][j] >= 0 && test_bit(bvc, u[k][j]);
+                for (int j = 0; j < 4; ++j) found[k] |= u[k][j] >= 0 && in_frontier<LIST>(a, bvc, llen, u[k][j]);
             }
         }
         // the rest of long unvisited columns, one column at a time by the whole warp
@@ -884,7 +1061,7 @@ __global__ void __launch_bounds__(kThreads, 4) trav_pull_bu(TravArgs a) {
                     for (int j = 0; j < 4; ++j) {
                         const int32_t q = q0 + j * 32 + lane;
                         if (q < pe) {
-                            h |= test_bit(bvc, __ldg(row + q));
+                            h |= in_frontier<LIST>(a, bvc, llen, __ldg(row + q));
                             acc.scanned++;
                         }
                     }
@@ -1445,6 +1622,9 @@ __global__ void reached_kernel(const uint32_t* __restrict__ dist, const int32_t*
 // Workspace layout inside g->work for BFS/SSSP.
 struct TravWork {
     uint32_t* msg[2];
+    uint32_t* lkey;
+    uint32_t* lval;
+    uint32_t* ltile;
     uint32_t* ycol;
     uint32_t* bv[3];
     int32_t* q[3][3];
@@ -1466,6 +1646,9 @@ TravWork work_layout(gm_graph* g, size_t* total_bytes = nullptr) {
     };
     for (int s = 0; s < 2; ++s) w.msg[s] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * n));
     w.ycol = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * n));
+    w.lkey = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * n));
+    w.lval = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * n));
+    w.ltile = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * ((n + kListTile - 1) / kListTile + 1)));
     for (int s = 0; s < 3; ++s) w.bv[s] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * nwords));
     for (int s = 0; s < 3; ++s) {
         w.q[s][0] = nullptr;
@@ -1506,6 +1689,9 @@ TravArgs make_args(gm_graph* g) {
     a.dist = as<uint32_t>(g->state);
     for (int s = 0; s < 2; ++s) a.msg[s] = w.msg[s];
     a.ycol = w.ycol;
+    a.lkey = w.lkey;
+    a.lval = w.lval;
+    a.ltile = w.ltile;
     a.dc_head = as<uint32_t>(g->dc_head);
     for (int s = 0; s < 3; ++s) {
         a.bv[s] = w.bv[s];
@@ -1544,22 +1730,27 @@ int push_grid() {
 int pull_grid() {
     static int blocks = [] {
         const int bytes = (int)(kHotMax * sizeof(uint32_t));
-        cudaFuncSetAttribute(trav_pull_a<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        cudaFuncSetAttribute(trav_pull_a<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        cudaFuncSetAttribute(trav_pull_a<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaFuncSetAttribute(trav_pull_a<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaFuncSetAttribute(trav_pull_a<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaFuncSetAttribute(trav_pull_a<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         return num_sms();
     }();
     return blocks;
 }
 
-// The SSSP pull variant for the handle's in-edge layout.
-const void* pull_a_kernel(const TravArgs& a) {
-    if (a.row_rw) return (const void*)trav_pull_a<0>;
-    return a.cw8 ? (const void*)trav_pull_a<1> : (const void*)trav_pull_a<4>;
+// The SSSP pull variant for the handle's in-edge layout (and the sorted-list
+// sparse vector of the ablation).
+const void* pull_a_kernel(const TravArgs& a, bool list = false) {
+    if (list) {
+        if (a.row_rw) return (const void*)trav_pull_a<0, true>;
+        return a.cw8 ? (const void*)trav_pull_a<1, true> : (const void*)trav_pull_a<4, true>;
+    }
+    if (a.row_rw) return (const void*)trav_pull_a<0, false>;
+    return a.cw8 ? (const void*)trav_pull_a<1, false> : (const void*)trav_pull_a<4, false>;
 }
 
 int pull_bu_grid() {
-    static int blocks = grid_for(trav_pull_bu);
+    static int blocks = grid_for(trav_pull_bu<false>);
     return blocks;
 }
 
@@ -1694,7 +1885,7 @@ gm_status build_loop_graph(gm_graph* g, bool sssp) {
     if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n0, body, &ns, 1, &kp);
     cudaGraphNode_t n1b = nullptr;
     if (e == cudaSuccess) {
-        kp.func = !sssp ? (void*)trav_pull_bu : const_cast<void*>(pull_a_kernel(a));
+        kp.func = !sssp ? (void*)trav_pull_bu<false> : const_cast<void*>(pull_a_kernel(a));
         kp.gridDim = dim3((unsigned)(sssp ? pull_grid() : pull_bu_grid()));
         kp.blockDim = dim3(sssp ? kPullThreads : kThreads);
         kp.sharedMemBytes = sssp ? (unsigned)a.hot * 4u : 0u;
@@ -1801,7 +1992,8 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
         return reset_frontier(g);
     }
     TravCtlDev* hp = static_cast<TravCtlDev*>(g->host_pinned);
-    const bool host_loop = g->tune.loop_mode == 1 || g->tune.profile;
+    const bool list = g->tune.sparse_list != 0;  // the ablation's sorted-list frontier: host-issued loop
+    const bool host_loop = g->tune.loop_mode == 1 || g->tune.profile || list;
     if (!host_loop) {
         // one graph: the run parameters, the superstep loop, the copy of the
         // control block to hp and the frontier reset for the next run
@@ -1840,9 +2032,10 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
             GM_CUDA_TRY(cudaEventCreate(&evB));
         }
         unsigned long long prev_e = 0, prev_v = 0;
+        const int list_grid = num_sms() * 8;
         for (int32_t it = 0;; ++it) {
             uint32_t dir_before = 0, frontier_before = 0;
-            if (ev0) {  // direction and frontier size of this superstep, for the trace
+            if (ev0 || list) {  // direction and frontier size of this superstep (trace; list build)
                 GM_CUDA_TRY(cudaMemcpyAsync(hp, g->ctl_buf.p, sizeof(TravCtlDev), cudaMemcpyDeviceToHost, s));
                 GM_CUDA_TRY(cudaStreamSynchronize(s));
                 dir_before = hp->c.dir;
@@ -1851,16 +2044,27 @@ gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
                                   hp->c.count[slot][3];
             }
             if (ev0) cudaEventRecord(ev0, s);
+            if (list && dir_before == 1u) {  // this pull superstep's frontier as a sorted list
+                if (sssp) list_count<true><<<list_grid, kListThreads, 0, s>>>(a);
+                else list_count<false><<<list_grid, kListThreads, 0, s>>>(a);
+                list_scan<<<1, kListScanThreads, 0, s>>>(a);
+                if (sssp) list_scatter<true><<<list_grid, kListThreads, 0, s>>>(a);
+                else list_scatter<false><<<list_grid, kListThreads, 0, s>>>(a);
+                g_launches += 3;
+                LAUNCH_OK();
+            }
             // both are launched; the one not matching the device-side direction returns at once
             if (sssp) trav_push<true><<<pg, kThreads, 0, s>>>(a);
             else trav_push<false><<<pg, kThreads, 0, s>>>(a);
             if (evA) cudaEventRecord(evA, s);
             if (sssp) {
                 void* pargs[] = {&a};
-                GM_CUDA_TRY(cudaLaunchKernel(pull_a_kernel(a), dim3(lg), dim3(kPullThreads), pargs,
-                                             (size_t)a.hot * 4u, s));
+                GM_CUDA_TRY(cudaLaunchKernel(pull_a_kernel(a, list), dim3(lg), dim3(kPullThreads), pargs,
+                                             list ? 0 : (size_t)a.hot * 4u, s));
+            } else if (list) {
+                trav_pull_bu<true><<<lg, kThreads, 0, s>>>(a);
             } else {
-                trav_pull_bu<<<lg, kThreads, 0, s>>>(a);
+                trav_pull_bu<false><<<lg, kThreads, 0, s>>>(a);
             }
             if (evB) cudaEventRecord(evB, s);
             g_launches += 2;

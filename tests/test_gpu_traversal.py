@@ -67,6 +67,39 @@ def test_sssp_pull_in_edge_layouts(gm, packed, stage):
             assert np.array_equal(got, ref) and it == rit
 
 
+@pytest.mark.parametrize("direction", DIRS)
+@pytest.mark.parametrize("kind", ["bfs", "sssp"])
+def test_sorted_list_sparse_vector(gm, kind, direction):
+    """GM_OPT_SPARSE_LIST (the ablation of Section 4.3.2's sparse-vector form):
+    each pull superstep looks its sources up by binary search in a sorted
+    (index, value) list of the frontier instead of the bitvector / dense message
+    array.  Properties and superstep counts equal the oracle's on an RMAT graph
+    (n not a multiple of the 2048-index list tile) and on a graph whose frontier
+    holds a single vertex, from one and from several sources."""
+    n, s, d, w = rmat_case(13, weighted=True)
+    n += 77  # isolated vertices past the RMAT range: a ragged last list tile
+    g = gm.Graph(n, s, d, w)
+    og = oracle.Graph(n, s, d, w)
+    g.set_option(gm.GM_OPT_SPARSE_LIST, 1)
+    g.set_option(gm.GM_OPT_DIRECTION, direction)
+    srcs = synth.pick_sources(n, s, d, 3, seed=21)
+    prog, ref_fn = (gm.GM_BFS, og.bfs) if kind == "bfs" else (gm.GM_SSSP, og.sssp)
+    for src in [[int(srcs[0])], [int(srcs[1])], srcs.tolist()]:
+        got, it = _run(gm, g, prog, src)
+        ref, rit = ref_fn(src)
+        assert np.array_equal(got, ref) and it == rit
+    # a path 0 -> 1 -> ... -> 9: every frontier is one vertex
+    ps, pd = np.arange(9, dtype=np.int32), np.arange(1, 10, dtype=np.int32)
+    pw = np.full(9, 3, np.uint32)
+    gp = gm.Graph(10, ps, pd, pw)
+    gp.set_option(gm.GM_OPT_SPARSE_LIST, 1)
+    gp.set_option(gm.GM_OPT_DIRECTION, direction)
+    opg = oracle.Graph(10, ps, pd, pw)
+    got, it = _run(gm, gp, prog, [0])
+    ref, rit = (opg.bfs if kind == "bfs" else opg.sssp)([0])
+    assert np.array_equal(got, ref) and it == rit
+
+
 @pytest.mark.parametrize("loop_mode", [0, 1])
 @pytest.mark.parametrize("seed", range(3))
 def test_random_graphs_multi_source(gm, seed, loop_mode):
