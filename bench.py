@@ -275,10 +275,13 @@ def pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind):
     per-column result written once (4 B per non-empty column).  The BFS pull
     (trav_pull_bu, bottom-up) is timed beside it."""
     wb = g.scalar(gm.GM_SCALAR_PULL_WEIGHT_BYTES)
-    eb = g.scalar(gm.GM_SCALAR_PULL_EDGE_BYTES) if hasattr(gm, "GM_SCALAR_PULL_EDGE_BYTES") else 4 + wb
     _, in_deg = g.degrees()
     state_bytes = 4.0 * g.n + 4.0 * float(np.count_nonzero(in_deg))
     ncols = float(np.count_nonzero(in_deg))
+
+    def stream_bytes():  # in-edge data one SSSP pull streams in the handle's layout
+        return float(g.scalar(gm.GM_SCALAR_PULL_STREAM_BYTES)) if hasattr(gm, "GM_SCALAR_PULL_STREAM_BYTES") \
+            else g.m * (4 + wb + 1 / 8)
     g.set_option(gm.GM_OPT_PROFILE, 1)
     byts, ms, launches, read_bytes = 0.0, 0.0, 0, 0.0
     bu_ms, bu_edges, bu_launches = 0.0, 0.0, 0
@@ -301,7 +304,7 @@ def pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind):
                 changed = tr[j + 1][2] if j + 1 < len(tr) else 0.0  # the next superstep's frontier
                 if row[1] == 1 and kind == gm.GM_SSSP:
                     byts += row[3] * (4 + sw) + row[3] / 8.0 + state_bytes
-                    read_bytes += row[3] * eb + row[3] / 8.0 + state_bytes
+                    read_bytes += stream_bytes() + state_bytes
                     ms += row[7]
                     launches += 1
                     fin_pull["ms"] += row[9]
@@ -327,9 +330,10 @@ def pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind):
             "frac": (achieved / peak) if achieved else None, "traffic": traffic, "traffic_frac": dram_frac,
             "kernel": "trav_pull_a (SSSP pull)", "peak_source": peak_kind, "weight_bytes": wb,
             "bytes_per_launch": byts / max(launches, 1), "avg_launch_us": 1e3 * ms / max(launches, 1),
-            # what the kernel streams: with the packed layout 4 B per in-edge carry both
-            # the source and its weight, so fewer bytes than the algorithmic figure above
-            "edge_bytes_read": eb, "bytes_read_per_launch": read_bytes / max(launches, 1),
+            # what the kernel streams in the handle's layout (octets of 4-byte words holding
+            # source rank and weight, padded per column, with a header byte per octet),
+            # plus the same vertex state
+            "bytes_read_per_launch": read_bytes / max(launches, 1),
             "frac_of_bytes_read": (read_bytes / (ms / 1e3) / 1e9 / peak) if ms > 0 else None,
             "launches": launches,
             "bfs_pull_bottom_up": {"launches": bu_launches, "avg_launch_us": 1e3 * bu_ms / max(bu_launches, 1),

@@ -239,9 +239,12 @@ enum {
                                           every uint32 weight is below 256 (a one-byte copy is kept),
                                           4 otherwise, 0 for an unweighted graph; set at creation */
     GM_SCALAR_CF_STRATA = 12,          /* int32: blocks per side P of the GM_CF_SGD order in use */
-    GM_SCALAR_PULL_EDGE_BYTES = 13     /* int32: bytes per in-edge the SSSP pull streams for its source and
-                                          weight: 4 when both share one word (GM_OPT_PULL_PACKED), else 4 +
-                                          the weight width (GM_SCALAR_PULL_WEIGHT_BYTES) */
+    GM_SCALAR_PULL_STREAM_BYTES = 13   /* int64: bytes of in-edge data one SSSP pull superstep streams, for
+                                          the layout in use: with GM_OPT_PULL_PACKED, 4 B per slot of the
+                                          column lists padded to whole octets of 8 slots, a header byte per
+                                          octet and 4 B per tile of 32 octets; otherwise 4 B + the weight
+                                          width per in-edge, a first-edge bit per in-edge and 4 B per tile
+                                          of 256 in-edges.  0 until an SSSP gm_program_set has built it. */
 };
 GM_API gm_status gm_get_scalar(gm_graph* g, int32_t which, void* out);
 

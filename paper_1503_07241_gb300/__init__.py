@@ -23,7 +23,7 @@ GM_PAGERANK, GM_BFS, GM_SSSP, GM_TRIANGLE_COUNT, GM_CF, GM_CONNECTED_COMPONENTS,
 (GM_SCALAR_TC_TOTAL, GM_SCALAR_CF_LOSS, GM_SCALAR_REACHED_EDGES, GM_SCALAR_SUPERSTEPS,
  GM_SCALAR_PUSH_STEPS, GM_SCALAR_PULL_STEPS, GM_SCALAR_SCANNED_EDGES, GM_SCALAR_RELAX_MS,
  GM_SCALAR_RELAX_LAUNCHES, GM_SCALAR_PROCESSED_VERTICES, GM_SCALAR_PULL_WEIGHT_BYTES,
- GM_SCALAR_CF_STRATA, GM_SCALAR_PULL_EDGE_BYTES) = range(1, 14)
+ GM_SCALAR_CF_STRATA, GM_SCALAR_PULL_STREAM_BYTES) = range(1, 14)
 (GM_OPT_DIRECTION, GM_OPT_LOOP_MODE, GM_OPT_PROFILE, GM_OPT_BIN_SMALL, GM_OPT_BIN_LARGE,
  GM_OPT_ALPHA_X1000, GM_OPT_BETA_X1000, GM_OPT_SSSP_PULL_PPM, GM_OPT_PULL_STAGE,
  GM_OPT_TEST_STALL_STAGE, GM_OPT_TEST_STALL_SGD, GM_OPT_PULL_PACKED, GM_OPT_SPARSE_LIST) = range(1, 14)
@@ -37,7 +37,7 @@ _SCALAR_TYPES = {
     GM_SCALAR_SCANNED_EDGES: ctypes.c_int64, GM_SCALAR_RELAX_MS: ctypes.c_double,
     GM_SCALAR_RELAX_LAUNCHES: ctypes.c_int32, GM_SCALAR_PROCESSED_VERTICES: ctypes.c_int64,
     GM_SCALAR_PULL_WEIGHT_BYTES: ctypes.c_int32, GM_SCALAR_CF_STRATA: ctypes.c_int32,
-    GM_SCALAR_PULL_EDGE_BYTES: ctypes.c_int32,
+    GM_SCALAR_PULL_STREAM_BYTES: ctypes.c_int64,
 }
 
 

@@ -266,10 +266,16 @@ gm_status gm_get_scalar(gm_graph* g, int32_t which, void* out) {
         case GM_SCALAR_PULL_WEIGHT_BYTES:
             *static_cast<int32_t*>(out) = g->wtype == GM_W_NONE ? 0 : g->cw8.p ? 1 : 4;
             return GM_OK;
-        case GM_SCALAR_PULL_EDGE_BYTES: {
-            // the layout build_pull_edge_words chooses (or has chosen)
-            const bool packed = g->tune.pull_packed && g->cw8.p != nullptr && g->n <= kPackedMaxVertices;
-            *static_cast<int32_t*>(out) = packed ? 4 : 4 + (g->cw8.p ? 1 : 4);
+        case GM_SCALAR_PULL_STREAM_BYTES: {
+            // in-edge data of one SSSP pull in the layout build_pull_edge_words built
+            int64_t b = 0;
+            if (g->oct_w.p) {
+                b = g->oct_slots * 4 + g->oct_slots / kOctet + g->oct_tiles * 4;
+            } else if (g->row_r.p) {
+                const int64_t wb = g->cw8.p ? 1 : 4;
+                b = g->m * (4 + wb) + (g->m + 7) / 8 + g->dc_ntiles * 4;
+            }
+            *static_cast<int64_t*>(out) = b;
             return GM_OK;
         }
         default: break;
@@ -326,9 +332,10 @@ gm_status gm_set_option(gm_graph* g, int32_t option, int64_t value) {
             return GM_OK;
         case GM_OPT_PULL_STAGE:
             if (value < 0 || value > 49152) break;
+            if (t.pull_stage == (int32_t)(value & ~(int64_t)3)) return GM_OK;
             t.pull_stage = (int32_t)(value & ~(int64_t)3);
             trav_release(g);  // the loop graph bakes the shared-memory size in
-            return GM_OK;
+            return balance_octets(g, pull_stage_messages(g));  // slot order for the new stage
         case GM_OPT_TEST_STALL_STAGE:
             if (value < 0 || value > 1) break;
             t.test_stall_stage = (int32_t)value;

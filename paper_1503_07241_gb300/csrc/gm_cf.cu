@@ -19,11 +19,16 @@
 // memory (one 1024-thread CTA per SM; for K = 32, 1792 rows carrying about 57 %
 // of the ratings of the Zipf-shaped workload) and each rating's item is stored
 // as a code: its row's slot there, or -1 - the item, so the gathers of those
-// ratings read shared memory instead of L2; an item pass over the CSC gathers the stored e_uv
-// and accumulates sum_u e_uv p_u; an update kernel applies Eqs. 4-5 to every
-// vertex.  Chunks of one long row are combined with
-// float atomics.  Arithmetic in FP32 on CUDA cores: every product is one
-// K-wide dot product per rating, not a dense tile.
+// ratings read shared memory instead of L2; an item pass over the CSC computes
+// e_uv again from the rating (a one-byte CSC copy when the ratings fit) and the
+// user's row -- the same products summed in the same order by the same lane
+// grouping, so the same value -- and accumulates sum_u e_uv p_u; an update
+// kernel applies Eqs. 4-5 to every vertex.  Recomputing e_uv costs one more
+// K-wide dot product per rating and saves storing it and gathering it back in
+// CSC order (a random 4-byte read from a 4-bytes-per-rating array, one 32-byte
+// sector per rating).  Chunks of one long row are combined with float atomics.
+// Arithmetic in FP32 on CUDA cores: every product is one K-wide dot product per
+// rating, not a dense tile.
 #include <algorithm>
 #include <vector>
 
@@ -70,7 +75,7 @@ __global__ void __launch_bounds__(kThreads) cf_user_pass(const int4* __restrict_
                                                          const int32_t* __restrict__ col,
                                                          const uint32_t* __restrict__ rating,
                                                          const float* __restrict__ p, int K,
-                                                         float* __restrict__ ebuf, float* __restrict__ acc,
+                                                         float* __restrict__ acc,
                                                          double* __restrict__ sq_err) {
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
@@ -94,15 +99,12 @@ __global__ void __launch_bounds__(kThreads) cf_user_pass(const int4* __restrict_
             for (int j = 0; j < KP; ++j) {
                 const int k = lane + 32 * j;
                 pv[j] = k < K ? __ldg(p + (int64_t)v * K + k) : 0.0f;
-                part += pu[j] * pv[j];
+                part = fmaf(pu[j], pv[j], part);
             }
             const float err = (float)__ldg(rating + e) - warp_sum_f(part);
 #pragma unroll
             for (int j = 0; j < KP; ++j) ac[j] += err * pv[j];
-            if (lane == 0) {
-                if (ebuf) ebuf[e] = err;
-                sq += (double)err * (double)err;
-            }
+            if (lane == 0) sq += (double)err * (double)err;
         }
         if (acc) {
 #pragma unroll
@@ -115,11 +117,17 @@ __global__ void __launch_bounds__(kThreads) cf_user_pass(const int4* __restrict_
     if (sq_err && lane == 0 && sq != 0.0) atomicAdd(sq_err, sq);
 }
 
+// Rating q (CSC order) of the item pass: the one-byte copy when the ratings fit.
+__device__ __forceinline__ float csc_rating(const uint8_t* __restrict__ r8, const uint32_t* __restrict__ r32,
+                                            int32_t q) {
+    return r8 ? (float)__ldg(r8 + q) : (float)__ldg(r32 + q);
+}
+
 template <int KP>
 __global__ void __launch_bounds__(kThreads) cf_item_pass(const int4* __restrict__ chunks, int64_t nchunks,
                                                          const int32_t* __restrict__ row,
-                                                         const uint32_t* __restrict__ csc_pos,
-                                                         const float* __restrict__ ebuf,
+                                                         const uint8_t* __restrict__ r8,
+                                                         const uint32_t* __restrict__ r32,
                                                          const float* __restrict__ p, int K,
                                                          float* __restrict__ acc) {
     const int lane = threadIdx.x & 31;
@@ -128,17 +136,26 @@ __global__ void __launch_bounds__(kThreads) cf_item_pass(const int4* __restrict_
     for (int64_t c = gwarp; c < nchunks; c += nwarps) {
         const int4 ch = chunks[c];
         const int32_t v = ch.x;
-        float ac[KP];
+        float ac[KP], pv[KP];
 #pragma unroll
-        for (int j = 0; j < KP; ++j) ac[j] = 0.0f;
+        for (int j = 0; j < KP; ++j) {
+            const int k = lane + 32 * j;
+            pv[j] = k < K ? __ldg(p + (int64_t)v * K + k) : 0.0f;
+            ac[j] = 0.0f;
+        }
         for (int32_t q = ch.y; q < ch.z; ++q) {
             const int32_t u = __ldg(row + q);
-            const float err = __ldg(ebuf + __ldg(csc_pos + q));
+            float pu[KP];
+            float part = 0.0f;  // the user pass's dot product, term for term
 #pragma unroll
             for (int j = 0; j < KP; ++j) {
                 const int k = lane + 32 * j;
-                if (k < K) ac[j] += err * __ldg(p + (int64_t)u * K + k);
+                pu[j] = k < K ? __ldg(p + (int64_t)u * K + k) : 0.0f;
+                part = fmaf(pu[j], pv[j], part);
             }
+            const float err = csc_rating(r8, r32, q) - warp_sum_f(part);
+#pragma unroll
+            for (int j = 0; j < KP; ++j) ac[j] += err * pu[j];
         }
 #pragma unroll
         for (int j = 0; j < KP; ++j) {
@@ -173,7 +190,7 @@ __global__ void __launch_bounds__(kThreads) cf_user_pass_g(const int4* __restric
                                                            const int32_t* __restrict__ col,
                                                            const uint32_t* __restrict__ rating,
                                                            const float* __restrict__ p,
-                                                           float* __restrict__ ebuf, float* __restrict__ acc,
+                                                           float* __restrict__ acc,
                                                            double* __restrict__ sq_err) {
     constexpr int K = 8 * L, R = 32 / L;
     const int lane = threadIdx.x & 31, grp = lane / L, sub = lane % L;
@@ -196,16 +213,13 @@ __global__ void __launch_bounds__(kThreads) cf_user_pass_g(const int4* __restric
             load8f<L>(p, (int64_t)v * K + 8 * sub, pv);
             float part = 0.0f;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) part += pu[j] * pv[j];
+            for (int j = 0; j < 8; ++j) part = fmaf(pu[j], pv[j], part);
 #pragma unroll
             for (int o = L / 2; o >= 1; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
             const float err = ok ? g - part : 0.0f;
 #pragma unroll
             for (int j = 0; j < 8; ++j) ac[j] += err * pv[j];
-            if (ok && sub == 0) {
-                if (ebuf) ebuf[e] = err;
-                sq += (double)err * (double)err;
-            }
+            if (ok && sub == 0) sq += (double)err * (double)err;
         }
         if (acc) {
             group_reduce8<L>(ac);
@@ -224,8 +238,8 @@ __global__ void __launch_bounds__(kThreads) cf_user_pass_g(const int4* __restric
 template <int L>
 __global__ void __launch_bounds__(kThreads) cf_item_pass_g(const int4* __restrict__ chunks, int64_t nchunks,
                                                            const int32_t* __restrict__ row,
-                                                           const uint32_t* __restrict__ csc_pos,
-                                                           const float* __restrict__ ebuf,
+                                                           const uint8_t* __restrict__ r8,
+                                                           const uint32_t* __restrict__ r32,
                                                            const float* __restrict__ p, float* __restrict__ acc) {
     constexpr int K = 8 * L, R = 32 / L;
     const int lane = threadIdx.x & 31, grp = lane / L, sub = lane % L;
@@ -234,16 +248,25 @@ __global__ void __launch_bounds__(kThreads) cf_item_pass_g(const int4* __restric
     for (int64_t c = gwarp; c < nchunks; c += nwarps) {
         const int4 ch = chunks[c];
         const int32_t v = ch.x;
-        float ac[8];
+        float ac[8], pv[8];
+        load8f<L>(p, (int64_t)v * K + 8 * sub, pv);
 #pragma unroll
         for (int j = 0; j < 8; ++j) ac[j] = 0.0f;
         for (int32_t q0 = ch.y; q0 < ch.z; q0 += R) {
             const int32_t q = q0 + grp;
             const bool ok = q < ch.z;
             const int32_t u = ok ? __ldg(row + q) : 0;
-            const float err = ok ? __ldg(ebuf + __ldg(csc_pos + q)) : 0.0f;
+            const float g = ok ? csc_rating(r8, r32, q) : 0.0f;
             float pu[8];
             load8f<L>(p, (int64_t)u * K + 8 * sub, pu);
+            // e_uv as the user pass computes it: the same products, summed in the
+            // same order over the same lanes
+            float part = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) part = fmaf(pu[j], pv[j], part);
+#pragma unroll
+            for (int o = L / 2; o >= 1; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+            const float err = ok ? g - part : 0.0f;
 #pragma unroll
             for (int j = 0; j < 8; ++j) ac[j] += err * pu[j];
         }
@@ -263,7 +286,7 @@ __global__ void __launch_bounds__(1024, 1) cf_user_pass_hot(const int4* __restri
                                                             const uint32_t* __restrict__ rating,
                                                             const float* __restrict__ p,
                                                             const int32_t* __restrict__ hot_ids, int32_t n_hot,
-                                                            float* __restrict__ ebuf, float* __restrict__ acc) {
+                                                            float* __restrict__ acc) {
     constexpr int K = 8 * L, R = 32 / L, K4 = K / 4;
     extern __shared__ float4 s_hot[];  // n_hot rows of K floats
     for (int32_t i = threadIdx.x; i < n_hot * K4; i += blockDim.x) {
@@ -296,13 +319,12 @@ __global__ void __launch_bounds__(1024, 1) cf_user_pass_hot(const int4* __restri
             }
             float part = 0.0f;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) part += pu[j] * pv[j];
+            for (int j = 0; j < 8; ++j) part = fmaf(pu[j], pv[j], part);
 #pragma unroll
             for (int o = L / 2; o >= 1; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
             const float err = ok ? g - part : 0.0f;
 #pragma unroll
             for (int j = 0; j < 8; ++j) ac[j] += err * pv[j];
-            if (ok && sub == 0) ebuf[e] = err;
         }
         group_reduce8<L>(ac);
         if (grp == 0)
@@ -351,7 +373,7 @@ std::vector<int4> make_chunks(const std::vector<int32_t>& ptr, int64_t r0, int64
 }
 
 struct CfState {
-    DevBuf user_chunks, item_chunks, ebuf, acc, scalar;
+    DevBuf user_chunks, item_chunks, acc, scalar;
     DevBuf hot_ids, code;     // staged item rows (grouped K): their vertex ids; per-rating codes
     int32_t n_hot = 0;
     int64_t n_user_chunks = 0, n_item_chunks = 0;
@@ -392,7 +414,7 @@ void cf_release(gm_graph* g) {
     if (!c) return;
     sgd_release(c->sgd, g->stream);
     c->sgd = nullptr;
-    DevBuf* bufs[] = {&c->user_chunks, &c->item_chunks, &c->ebuf, &c->acc, &c->scalar, &c->hot_ids, &c->code};
+    DevBuf* bufs[] = {&c->user_chunks, &c->item_chunks, &c->acc, &c->scalar, &c->hot_ids, &c->code};
     for (DevBuf* b : bufs) dev_free(*b, g->stream);
     delete c;
     g->cf = nullptr;
@@ -449,7 +471,6 @@ gm_status cf_prepare(gm_graph* g) {
     if (sgd) {
         GM_TRY(sgd_prepare(g, &c->sgd));
     } else {
-        GM_TRY(dev_alloc(c->ebuf, sizeof(float) * (g->m > 0 ? g->m : 1), s));
         GM_TRY(dev_alloc(c->acc, sizeof(float) * (n > 0 ? n : 1) * K, s));
         GM_CUDA_TRY(cudaMemsetAsync(c->acc.p, 0, sizeof(float) * (n > 0 ? n : 1) * K, s));
     }
@@ -495,18 +516,18 @@ gm_status cf_run(gm_graph* g, int32_t iters, int32_t* iters_done) {
                     (void)attr;
                     cf_user_pass_hot<L><<<num_sms(), 1024, smem, s>>>(
                         as<int4>(c->user_chunks), c->n_user_chunks, as<int32_t>(c->code), as<uint32_t>(g->w), p,
-                        as<int32_t>(c->hot_ids), c->n_hot, as<float>(c->ebuf), as<float>(c->acc));
+                        as<int32_t>(c->hot_ids), c->n_hot, as<float>(c->acc));
                     g_launches++;
                 } else if (c->n_user_chunks > 0) {
                     cf_user_pass_g<L><<<grid_cf(), kThreads, 0, s>>>(as<int4>(c->user_chunks), c->n_user_chunks,
                                                                       as<int32_t>(g->col), as<uint32_t>(g->w), p,
-                                                                      as<float>(c->ebuf), as<float>(c->acc), nullptr);
+                                                                      as<float>(c->acc), nullptr);
                     g_launches++;
                 }
                 if (c->n_item_chunks > 0) {
                     cf_item_pass_g<L><<<grid_cf(), kThreads, 0, s>>>(as<int4>(c->item_chunks), c->n_item_chunks,
-                                                                      as<int32_t>(g->row), as<uint32_t>(g->csc_pos),
-                                                                      as<float>(c->ebuf), p, as<float>(c->acc));
+                                                                      as<int32_t>(g->row), as<uint8_t>(g->cw8),
+                                                                      as<uint32_t>(g->cw), p, as<float>(c->acc));
                     g_launches++;
                 }
                 GM_CUDA_TRY(cudaGetLastError());
@@ -517,13 +538,13 @@ gm_status cf_run(gm_graph* g, int32_t iters, int32_t* iters_done) {
             if (c->n_user_chunks > 0) {
                 cf_user_pass<KP><<<grid_cf(), kThreads, 0, s>>>(as<int4>(c->user_chunks), c->n_user_chunks,
                                                                  as<int32_t>(g->col), as<uint32_t>(g->w), p, K,
-                                                                 as<float>(c->ebuf), as<float>(c->acc), nullptr);
+                                                                 as<float>(c->acc), nullptr);
                 g_launches++;
             }
             if (c->n_item_chunks > 0) {
                 cf_item_pass<KP><<<grid_cf(), kThreads, 0, s>>>(as<int4>(c->item_chunks), c->n_item_chunks,
-                                                                 as<int32_t>(g->row), as<uint32_t>(g->csc_pos),
-                                                                 as<float>(c->ebuf), p, K, as<float>(c->acc));
+                                                                 as<int32_t>(g->row), as<uint8_t>(g->cw8),
+                                                                 as<uint32_t>(g->cw), p, K, as<float>(c->acc));
                 g_launches++;
             }
             GM_CUDA_TRY(cudaGetLastError());
@@ -556,7 +577,7 @@ gm_status cf_loss(gm_graph* g, double* out) {
             if (c->n_user_chunks > 0) {
                 cf_user_pass_g<L><<<grid_cf(), kThreads, 0, s>>>(as<int4>(c->user_chunks), c->n_user_chunks,
                                                                   as<int32_t>(g->col), as<uint32_t>(g->w),
-                                                                  as<float>(g->state), nullptr, nullptr, d);
+                                                                  as<float>(g->state), nullptr, d);
                 g_launches++;
             }
             return GM_OK;
@@ -566,7 +587,7 @@ gm_status cf_loss(gm_graph* g, double* out) {
         if (c->n_user_chunks > 0) {
             cf_user_pass<KP><<<grid_cf(), kThreads, 0, s>>>(as<int4>(c->user_chunks), c->n_user_chunks,
                                                              as<int32_t>(g->col), as<uint32_t>(g->w),
-                                                             as<float>(g->state), K, nullptr, nullptr, d);
+                                                             as<float>(g->state), K, nullptr, d);
             g_launches++;
         }
         return GM_OK;

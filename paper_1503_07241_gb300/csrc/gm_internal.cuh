@@ -20,6 +20,8 @@ constexpr int kEdgePad = 16;            // per-edge arrays carry this many spare
 constexpr int kChunk = 2048;            // edges of one large-vertex work item (256 threads x 8 edges)
 constexpr int kWTile = 256;             // in-edges of one warp tile of the pull side (32 lanes x 8 edges)
 constexpr int64_t kPackedMaxVertices = 1ll << 24;  // ranks that fit the 24 bits of a packed in-edge word
+constexpr int kOctet = 8;                          // slots of one octet (one lane's share of a tile)
+constexpr int kOctTile = 32;                       // octets of one warp tile
 
 // Library-wide count of kernel launches issued (a graph replay counts each
 // kernel node it runs).
@@ -137,9 +139,18 @@ struct gm_graph {
     // program_set: the SSSP messages live in rank order so that the hottest sources'
     // messages are one contiguous prefix the pull can keep in shared memory.
     gm::DevBuf src_rank;             // rank of each vertex (int32[n])
-    gm::DevBuf row_r;                // CSC sources as ranks (int32[m + pad]); empty when row_rw is built
-    gm::DevBuf row_rw;               // CSC source rank and weight in one word, (rank << 8) | weight
-                                     // (uint32[m + pad]), when every weight fits a byte and n <= 2^24
+    gm::DevBuf row_r;                // CSC sources as ranks (int32[m + pad]); empty when the octets are built
+    // Octet layout of the SSSP pull's in-edges, built instead of row_r when every
+    // weight fits a byte and n <= 2^24: each non-empty column's in-edges, in CSC
+    // order, padded to a multiple of 8 slots, so that every octet (the 8 slots one
+    // lane reads) belongs to one column; 32 octets form a warp tile.
+    gm::DevBuf oct_w;                // uint32 per slot: (source rank << 8) | weight; padding slots 0;
+                                     // per tile slots 0-3 of its 32 octets, then slots 4-7
+    gm::DevBuf oct_meta;             // uint8 per octet: bits 0-3 real slots (1..8), bit 7 first octet of
+                                     // its column; 0 for octets past the last (the tail of the last tile)
+    gm::DevBuf oct_c0;               // int32 per tile: non-empty column index of the tile's first octet
+    int64_t oct_tiles = 0;           // tiles of 32 octets
+    int64_t oct_slots = 0;           // real + padding slots (octets x 8) before the last tile's tail
     gm::DevBuf dc_rank;              // rank of each non-empty column's vertex (int32[ncols])
     gm::DevBuf out_deg, in_deg;      // int32
     gm::DevBuf out_bin, in_bin;      // uint8 bin of each vertex by out/in degree (0 = degree zero)
@@ -200,6 +211,12 @@ gm_status trav_prepare(gm_graph* g);
 gm_status trav_reuse(gm_graph* g);  // program_set between BFS and SSSP with the workspace kept
 gm_status build_source_ranks(gm_graph* g);  // gm_graph.cu
 gm_status build_pull_edge_words(gm_graph* g);  // gm_graph.cu
+gm_status balance_octets(gm_graph* g, int64_t hot);  // gm_graph.cu
+// Messages the SSSP pull stages per CTA (ranks [0, result)): the stage option,
+// at most 49,152 and n rounded down to a multiple of 4.
+inline int64_t pull_stage_messages(const gm_graph* g) {
+    return std::min<int64_t>(std::min<int64_t>(49152, g->tune.pull_stage), g->n & ~(int64_t)3);
+}
 gm_status trav_set_active(gm_graph* g, const int32_t* vertices_dev, int64_t count);
 gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done);
 void trav_release(gm_graph* g);

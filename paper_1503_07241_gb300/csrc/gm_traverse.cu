@@ -66,7 +66,10 @@ struct TravArgs {
                              // indexed by source rank (msg[.][rank[v]] is vertex v's message)
     const int32_t* rank;     // SSSP: rank of each vertex by out-degree (descending)
     const int32_t* row_r;    // SSSP: CSC sources as ranks
-    const uint32_t* row_rw;  // SSSP: (rank << 8) | one-byte weight per in-edge, or nullptr
+    const uint32_t* oct_w;   // SSSP octet layout (or nullptr): (rank << 8) | weight per slot,
+    const uint8_t* oct_meta; //   octet headers (real slots, first octet of a column),
+    const int32_t* oct_c0;   //   first column of every tile of 32 octets
+    int64_t oct_tiles;
     const int32_t* dc_rank;  // SSSP: rank of each non-empty column's vertex
     int32_t hot;             // SSSP pull: messages of ranks [0, hot) are staged in shared memory
     uint32_t stage_extra;    // test hook: bytes the staging barrier expects beyond its copies (0 or 16)
@@ -500,6 +503,7 @@ __device__ __forceinline__ void flush_acc(const TravArgs& a, Acc& acc, int nxt, 
 // ---------------------------------------------------------------- bulk copy (TMA)
 constexpr int kPullThreads = 1024;
 constexpr int32_t kHotMax = 49152;      // staged messages per CTA: at most 192 KB of shared memory
+                                        // (pull_stage_messages caps the option at this)
 constexpr uint32_t kBulkChunk = 32768;  // bytes per cp.async.bulk instruction
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -726,22 +730,17 @@ __device__ __forceinline__ bool in_frontier(const TravArgs& a, const uint32_t* b
 //  pull_apply (SSSP, in the finalize kernel) applies y to the vertex properties
 //          (Apply = min), makes changed vertices the next frontier and resets y
 //          to infinity.
-// One warp tile's streamed inputs per lane: 8 in-edges (WB = 0: one word each
-// holding the source rank in its high 24 bits and the weight in its low 8;
-// otherwise source ranks plus their weights, one-byte weights packed in two words
-// until used), the lane's 8 first-edge bits and the tile's first column.
+// One warp tile's streamed inputs per lane: 8 in-edge source ranks, their
+// weights (one-byte weights stay packed in two words until used), the lane's 8
+// first-edge bits and the tile's first column.
 template <int WB>
 struct PullTile {
     int32_t r[kEPT];
-    uint32_t w[WB == 0 ? 1 : (WB == 1 ? 2 : kEPT)];
+    uint32_t w[WB == 1 ? 2 : kEPT];
     uint32_t hw;
     int32_t c0;
-    __device__ __forceinline__ int32_t rank(int q) const {
-        if (WB == 0) return (int32_t)((uint32_t)r[q] >> 8);
-        return r[q];
-    }
+    __device__ __forceinline__ int32_t rank(int q) const { return r[q]; }
     __device__ __forceinline__ uint32_t weight(int q) const {
-        if (WB == 0) return (uint32_t)r[q] & 0xFFu;
         if (WB == 1) return (w[q >> 2] >> (8 * (q & 3))) & 0xFFu;
         return w[q];
     }
@@ -752,16 +751,12 @@ template <int WB>
 __device__ __forceinline__ void pull_load_tile(const TravArgs& a, uint32_t k, int lane, PullTile<WB>& x) {
     const uint32_t p = k * (uint32_t)kWTile + (uint32_t)lane * kEPT;
     if (p < (uint32_t)a.m) {
-        if (WB == 0) {
-            load8(reinterpret_cast<const int32_t*>(a.row_rw), (int32_t)p, x.r);
-        } else {
-            load8(a.row_r, (int32_t)p, x.r);
-        }
+        load8(a.row_r, (int32_t)p, x.r);
         if (WB == 1) {
             const uint2 v = __ldcs(reinterpret_cast<const uint2*>(a.cw8 + p));
             x.w[0] = v.x;
             x.w[1] = v.y;
-        } else if (WB == 4) {
+        } else {
             uint32_t (&w8)[kEPT] = *reinterpret_cast<uint32_t(*)[kEPT]>(&x.w[0]);
             load8(a.cw, (int32_t)p, w8);
         }
@@ -808,9 +803,9 @@ __device__ __forceinline__ void pull_gather_list(const TravArgs& a, uint32_t len
     }
 }
 
-// WB: bytes per in-edge weight read (0: packed with the rank in one word,
-// 1: the uint8 copy, 4: the uint32 array).  LIST: sources are looked up in the
-// sorted-list sparse vector (no shared-memory stage).
+// WB: bytes per in-edge weight read (1: the uint8 copy, 4: the uint32 array).
+// LIST: sources are looked up in the sorted-list sparse vector (no shared-memory
+// stage).
 // One CTA of kPullThreads per SM; dynamic shared memory holds a.hot messages.
 // Software pipeline per warp: while tile k is reduced, the messages of tile k+1
 // are being gathered and the sources of tile k+2 streamed in.
@@ -942,6 +937,139 @@ __global__ void __launch_bounds__(kPullThreads, 1) trav_pull_a(TravArgs a) {
             const int32_t end_col = c0 + (int32_t)hincl - (int32_t)first_is_head;
             if (lane < 31 && seg0 >= 0) y[end_col] = R;  // its first edge lies in this tile
             else atomicMin(&y[end_col], R);
+        }
+    }
+    scanned = warp_sum_u64(scanned);
+    if (lane == 0 && scanned) atomicAdd(&cd->c.scanned_edges, scanned);
+    if (!staged && hot > 0) mbar_wait_bounded(&s_bar, 0u);  // let a late copy land before the CTA exits
+}
+
+// ---------------------------------------------------------------- pull over octets
+// pull_o (SSSP, octet layout): the same Reduce(min) per column as pull_a, over
+// in-edge lists padded to whole octets so that a lane's 8 slots always belong to
+// one column.  A lane takes the minimum of its (up to 8) candidates msg[u] + w
+// with no per-edge column logic; one segmented min-scan across the warp joins
+// the lanes of a column (a header bit marks a column's first octet), and the
+// last lane of each column stores it -- with atomicMin when the column began in
+// an earlier tile or may continue into the next.  Padding slots gather nothing.
+struct OctTile {
+    uint32_t w[kOctet];  // (rank << 8) | weight
+    uint32_t meta;       // real slots | 0x80 at a column's first octet; 0 past the end
+    int32_t c0;          // column of the tile's first octet
+};
+
+// A lane's octet of tile k: slots 0-3 and 4-7 are each one 16-byte load that
+// the warp makes over 512 consecutive bytes (the tile is stored slot-quad-major).
+__device__ __forceinline__ void oct_load(const TravArgs& a, uint32_t k, int lane, OctTile& x) {
+    const uint32_t o = k * (uint32_t)kOctTile + (uint32_t)lane;  // octets fill whole tiles: in bounds
+    const int4* t = reinterpret_cast<const int4*>(a.oct_w + (size_t)k * (kOctTile * kOctet));
+    const int4 lo = __ldcs(t + lane), hi = __ldcs(t + kOctTile + lane);
+    x.w[0] = (uint32_t)lo.x; x.w[1] = (uint32_t)lo.y; x.w[2] = (uint32_t)lo.z; x.w[3] = (uint32_t)lo.w;
+    x.w[4] = (uint32_t)hi.x; x.w[5] = (uint32_t)hi.y; x.w[6] = (uint32_t)hi.z; x.w[7] = (uint32_t)hi.w;
+    x.meta = __ldcs(a.oct_meta + o);
+    x.c0 = __ldg(a.oct_c0 + k);
+}
+
+// Messages of an octet's slots: staged ranks from shared memory, the rest from
+// global memory, or (LIST) from the sorted list.  Padding slots hold rank 0
+// (staged, or one shared address) and are masked to infinity by the caller, so
+// the loads need no branch.
+template <bool LIST>
+__device__ __forceinline__ void oct_gather(const TravArgs& a, const uint32_t* __restrict__ msgc,
+                                           const uint32_t* s_hot, int32_t hlim, uint32_t llen, const OctTile& x,
+                                           uint32_t (&mv)[kOctet]) {
+#pragma unroll
+    for (int q = 0; q < kOctet; ++q) {
+        const uint32_t rq = x.w[q] >> 8;
+        if (LIST) {
+            const uint32_t p = list_lower(a.lkey, llen, rq);
+            mv[q] = (p < llen && __ldg(a.lkey + p) == rq) ? __ldg(a.lval + p) : kInf;
+        } else {
+            mv[q] = (int32_t)rq < hlim ? s_hot[rq] : __ldg(msgc + rq);
+        }
+    }
+}
+
+template <bool LIST>
+__global__ void __launch_bounds__(kPullThreads, 1) trav_pull_o(TravArgs a) {
+    extern __shared__ __align__(128) uint32_t s_hot[];
+    __shared__ __align__(8) uint64_t s_bar;
+    TravCtlDev* cd = a.ctl;
+    if (cd->c.done || cd->c.dir != 1u) return;
+    const uint32_t t = cd->c.iter;
+    const int clr = (int)((t + 2u) % 3u);
+    const uint32_t* __restrict__ msgc = a.msg[t & 1u];
+    const uint32_t llen = LIST ? cd->c.list_len : 0u;
+    const int32_t hot = LIST ? 0 : a.hot;  // a multiple of 4, so the copy is whole 16-byte units
+    if (threadIdx.x == 0 && hot > 0) {
+        mbar_init(&s_bar, 1u);
+        fence_mbar_init();
+        const uint32_t bytes = (uint32_t)hot * 4u;
+        mbar_arrive_expect_tx(&s_bar, bytes + a.stage_extra);
+        for (uint32_t off = 0; off < bytes; off += kBulkChunk)
+            bulk_copy_g2s(reinterpret_cast<char*>(s_hot) + off, reinterpret_cast<const char*>(msgc) + off,
+                          min(kBulkChunk, bytes - off), &s_bar);
+    }
+    relax_prologue<true>(a, &cd->c, t, clr);
+    const int lane = threadIdx.x & 31;
+    const uint32_t lane_le = 0xFFFFFFFFu >> (31 - lane);  // lanes <= this one
+    const uint32_t gwarp = (blockIdx.x * kPullThreads + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * kPullThreads) >> 5;
+    const uint32_t ntiles = (uint32_t)a.oct_tiles;
+    uint32_t* __restrict__ y = a.ycol;
+    unsigned long long scanned = 0;
+
+    // the warp's first two tiles stream in while the staging copy runs
+    OctTile cur, nxt;
+    if (gwarp < ntiles) oct_load(a, gwarp, lane, cur);
+    if (gwarp + nwarps < ntiles) oct_load(a, gwarp + nwarps, lane, nxt);
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+    bool staged = hot > 0 && mbar_wait_bounded(&s_bar, 0u);
+    staged = __syncthreads_and(staged) != 0;
+    if (!staged && hot > 0 && threadIdx.x == 0) atomicAdd(&cd->c.stage_timeouts, 1u);
+    const int32_t hlim = staged ? hot : 0;  // without the staged block every message is gathered
+    uint32_t mv[kOctet];
+    if (gwarp < ntiles) oct_gather<LIST>(a, msgc, s_hot, hlim, llen, cur, mv);
+
+    for (uint32_t k = gwarp; k < ntiles; k += nwarps) {
+        // the lane's candidates msg[u] + w(u, v), all of one column (padding slots,
+        // q >= the octet's real count, masked out)
+        const uint32_t meta = cur.meta;
+        const uint32_t real = meta & 0xFu;
+        uint32_t R = kInf;
+#pragma unroll
+        for (int q = 0; q < kOctet; ++q) {
+            const uint32_t c = sat_add(mv[q], cur.w[q] & 0xFFu);
+            R = min(R, (uint32_t)q < real ? c : kInf);
+        }
+        const int32_t c0 = cur.c0;
+        // pipeline: gather tile k+1's messages, stream tile k+2's in-edges
+        const uint32_t k1 = k + nwarps, k2 = k1 + nwarps;
+        if (k1 < ntiles) oct_gather<LIST>(a, msgc, s_hot, hlim, llen, nxt, mv);
+        cur = nxt;
+        if (k2 < ntiles) oct_load(a, k2, lane, nxt);
+        scanned += meta & 0xFu;
+
+        // lanes holding a column's first octet start a segment
+        const uint32_t heads = __ballot_sync(kFull, (meta & 0x80u) != 0u);
+        if ((heads & ~1u) == 0u) {  // the whole tile lies in one column (warp-uniform)
+            const uint32_t Rt = __reduce_min_sync(kFull, R);
+            if (lane == 0 && Rt != kInf) atomicMin(&y[c0], Rt);
+            continue;
+        }
+        const uint32_t le = heads & lane_le;
+        const int seg0 = le ? 31 - __clz(le) : -1;  // -1: the column began before this tile
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t Ru = __shfl_up_sync(kFull, R, o);
+            if (lane - o >= max(seg0, 0)) R = min(R, Ru);
+        }
+        // the segment's last lane holds its minimum
+        const bool last = lane == 31 || ((heads >> (lane + 1)) & 1u);
+        if (last && R != kInf) {
+            const int32_t col = c0 + __popc(le & ~1u);
+            if (lane < 31 && seg0 >= 0) y[col] = R;  // the whole column lies in this tile
+            else atomicMin(&y[col], R);
         }
     }
     scanned = warp_sum_u64(scanned);
@@ -1700,11 +1828,12 @@ TravArgs make_args(gm_graph* g) {
     }
     a.rank = as<int32_t>(g->src_rank);
     a.row_r = as<int32_t>(g->row_r);
-    a.row_rw = as<uint32_t>(g->row_rw);
+    a.oct_w = as<uint32_t>(g->oct_w);
+    a.oct_meta = as<uint8_t>(g->oct_meta);
+    a.oct_c0 = as<int32_t>(g->oct_c0);
+    a.oct_tiles = g->oct_tiles;
     a.dc_rank = as<int32_t>(g->dc_rank);
-    a.hot = g->src_rank.p ? (int32_t)std::min<int64_t>(std::min<int64_t>(kHotMax, g->tune.pull_stage),
-                                                         g->n & ~(int64_t)3)
-                          : 0;
+    a.hot = g->src_rank.p ? (int32_t)pull_stage_messages(g) : 0;
     a.stage_extra = g->tune.test_stall_stage ? 16u : 0u;
     a.ctl = as<TravCtlDev>(g->ctl_buf);
     a.use_cond = 0;
@@ -1730,7 +1859,7 @@ int push_grid() {
 int pull_grid() {
     static int blocks = [] {
         const int bytes = (int)(kHotMax * sizeof(uint32_t));
-        cudaFuncSetAttribute(trav_pull_a<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaFuncSetAttribute(trav_pull_o<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         cudaFuncSetAttribute(trav_pull_a<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         cudaFuncSetAttribute(trav_pull_a<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         return num_sms();
@@ -1741,11 +1870,8 @@ int pull_grid() {
 // The SSSP pull variant for the handle's in-edge layout (and the sorted-list
 // sparse vector of the ablation).
 const void* pull_a_kernel(const TravArgs& a, bool list = false) {
-    if (list) {
-        if (a.row_rw) return (const void*)trav_pull_a<0, true>;
-        return a.cw8 ? (const void*)trav_pull_a<1, true> : (const void*)trav_pull_a<4, true>;
-    }
-    if (a.row_rw) return (const void*)trav_pull_a<0, false>;
+    if (a.oct_w) return list ? (const void*)trav_pull_o<true> : (const void*)trav_pull_o<false>;
+    if (list) return a.cw8 ? (const void*)trav_pull_a<1, true> : (const void*)trav_pull_a<4, true>;
     return a.cw8 ? (const void*)trav_pull_a<1, false> : (const void*)trav_pull_a<4, false>;
 }
 

@@ -55,6 +55,7 @@ def test_pull_roofline_adds_the_sssp_pull_launches_only():
     class FakeGM:
         GM_BFS, GM_SSSP = 1, 2
         GM_SCALAR_PULL_WEIGHT_BYTES = 11
+        GM_SCALAR_PULL_STREAM_BYTES = 13
         GM_OPT_PROFILE = 3
 
     class FakeGraph:
@@ -69,8 +70,8 @@ def test_pull_roofline_adds_the_sssp_pull_launches_only():
             self.options = []
 
         def scalar(self, which):
-            assert which == FakeGM.GM_SCALAR_PULL_WEIGHT_BYTES
-            return 1
+            assert which in (FakeGM.GM_SCALAR_PULL_WEIGHT_BYTES, FakeGM.GM_SCALAR_PULL_STREAM_BYTES)
+            return 1 if which == FakeGM.GM_SCALAR_PULL_WEIGHT_BYTES else 5000
 
         def degrees(self):
             return np.zeros(10, np.int32), np.array([0, 1, 2, 0, 3, 1, 0, 0, 5, 1], np.int32)
@@ -100,6 +101,8 @@ def test_pull_roofline_adds_the_sssp_pull_launches_only():
     assert abs(r["avg_launch_us"] - 400.0) < 1e-9
     assert abs(r["achieved"] - per_launch / 0.4e-3 / 1e9) < 1e-9
     assert abs(r["frac"] - r["achieved"] / 6000.0) < 1e-12
+    # bytes the layout streams (5000 here) plus the same vertex state
+    assert r["bytes_read_per_launch"] == 5000 + state
     assert r["bfs_pull_bottom_up"]["launches"] == 2
     assert r["bfs_pull_bottom_up"]["in_edges_checked_per_launch"] == 800
     # SSSP push superstep 0 (1 frontier vertex, 100 edges): 12 B + 16 B per edge, 0.06 ms

@@ -10,7 +10,7 @@ and in L2, and one epoch of the full workload.
 SGD tolerance: the kernel computes in FP32 with a different dot-product order;
 a sequential FP32 replay of the oracle's order differs from FP64 by at most
 3e-6 after two epochs of the 150k-rating case and 1.2e-5 after one epoch of the
-100M-rating workload, so every factor must lie within 5e-5 + 1e-4 |oracle|."""
+100M-rating workload, so every factor must lie within 2e-5 + 1e-4 |oracle|."""
 import numpy as np
 import pytest
 
@@ -69,7 +69,7 @@ def test_rejects_non_bipartite(gm):
         g.program_set(gm.GM_CF, K=8)
 
 
-SGD_ATOL, SGD_RTOL = 5e-5, 1e-4
+SGD_ATOL, SGD_RTOL = 2e-5, 1e-4
 
 
 def _sgd_case(gm, nu, ni, nr, K, gamma, P, epochs=2, seed=7):
@@ -169,6 +169,9 @@ def test_sgd_full_config_one_epoch(gm, full_cf):
     g.run(1)
     got = g.state().astype(np.float64)
     ref = og.cf_sgd(K, LAM, gamma, 1, nu, P, p0)
+    excess = np.abs(got - ref) - SGD_RTOL * np.abs(ref)
+    print(f"full SGD epoch: max |got - ref| {np.max(np.abs(got - ref)):.3e}, "
+          f"max |got - ref| - rtol |ref| {excess.max():.3e} (atol {SGD_ATOL})")
     np.testing.assert_allclose(got, ref, rtol=SGD_RTOL, atol=SGD_ATOL)
     assert og.cf_loss(K, LAM, ref) < og.cf_loss(K, LAM, p0)
 
@@ -207,7 +210,8 @@ def test_full_config_ten_steps_match_oracle(gm, full_cf):
     Jacobi gradient steps of Eqs. 3-5 at CF_FULL_GAMMA.  Every factor against
     the FP64 oracle's ten steps from the same initial factors: relative
     Frobenius error and max-abs error over the largest factor both <= 1e-4, the
-    Eq. 2 loss within 1e-5 relative, and the oracle's loss decreasing."""
+    change of the factors over the ten steps within 1e-4 (relative Frobenius),
+    the Eq. 2 loss within 1e-5 relative, and the oracle's loss decreasing."""
     nu, ni, n, s, d, r, og = full_cf
     g = gm.Graph(n, s, d, r, n_left=nu)
     K = 32
@@ -226,4 +230,7 @@ def test_full_config_ten_steps_match_oracle(gm, full_cf):
           f"loss {loss:.6e} vs {trace[-1]:.6e}")
     assert err_fro <= 1e-4
     assert err_max <= 1e-4
+    # the ten steps' change of the factors itself, not only the factors (at this
+    # step size the change is small next to the initial factors)
+    assert err_upd <= 1e-4
     assert abs(loss - trace[-1]) <= 1e-5 * trace[-1]

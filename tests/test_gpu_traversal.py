@@ -45,12 +45,13 @@ def test_rmat_small_parity(gm, kind, direction):
 @pytest.mark.parametrize("packed", [1, 0])
 @pytest.mark.parametrize("stage", [40960, 0])
 def test_sssp_pull_in_edge_layouts(gm, packed, stage):
-    """The SSSP pull with each in-edge as one word (source rank << 8 | weight)
-    and with separate rank and one-byte weight arrays, with and without the
-    shared-memory stage, forced to pull every superstep and automatic: exact
-    distances and superstep counts on an RMAT graph of several thousand warp
-    tiles and a ragged last tile.  The layout option switched back and forth on
-    one handle rebuilds the in-edge stream."""
+    """The SSSP pull over the octet layout (each in-edge one word, source rank
+    << 8 | weight, column lists padded to whole octets) and over separate rank
+    and one-byte weight arrays, with and without the shared-memory stage,
+    forced to pull every superstep and automatic: exact distances and
+    superstep counts on an RMAT graph of several thousand warp tiles and a
+    ragged last tile.  The layout option switched back and forth on one handle
+    rebuilds the in-edge stream."""
     n, s, d, w = rmat_case(14, weighted=True)
     g = gm.Graph(n, s, d, w)
     og = oracle.Graph(n, s, d, w)
@@ -65,6 +66,36 @@ def test_sssp_pull_in_edge_layouts(gm, packed, stage):
             got, it = _run(gm, g, gm.GM_SSSP, [src])
             ref, rit = og.sssp([src])
             assert np.array_equal(got, ref) and it == rit
+
+
+@pytest.mark.parametrize("packed", [1, 0])
+def test_sssp_pull_column_shapes(gm, packed):
+    """In-degrees that meet the octet layout's edges: columns of exactly 8, 16
+    and 256 in-edges (whole octets, a whole tile of 32 octets), one of 8k + 1,
+    a hub spanning several tiles, single-edge columns, and a graph whose octets
+    fill less than one tile; forced pull from the first superstep and the
+    automatic switch, against the oracle."""
+    rng = np.random.default_rng(77)
+    n = 3000
+    parts = [(np.arange(1, 1001), 0), (np.arange(1001, 1009), 1), (np.arange(1009, 1025), 2),
+             (np.arange(1025, 1281), 3), (np.arange(1281, 1298), 4), (np.arange(1298, 1299), 5)]
+    src = np.concatenate([p for p, _ in parts] + [rng.integers(0, n, 20000)]).astype(np.int32)
+    dst = np.concatenate([np.full(len(p), v) for p, v in parts] + [rng.integers(0, n, 20000)]).astype(np.int32)
+    w = rng.integers(1, 256, len(src)).astype(np.uint32)
+    cases = [(n, src, dst, w), (40, np.array([1, 2, 3, 4, 5, 6, 7, 8, 9, 0, 0], np.int32),
+                                np.array([0, 0, 0, 0, 0, 0, 0, 0, 0, 9, 10], np.int32),
+                                np.arange(1, 12, dtype=np.uint32))]
+    for nn, ss, dd, ww in cases:
+        g = gm.Graph(nn, ss, dd, ww)
+        og = oracle.Graph(nn, ss, dd, ww)
+        g.program_set(gm.GM_SSSP)
+        g.set_option(gm.GM_OPT_PULL_PACKED, packed)
+        for direction in (2, 0):
+            g.set_option(gm.GM_OPT_DIRECTION, direction)
+            for seeds in ([int(ss[0])], [int(x) for x in ss[:5]], [0]):
+                got, it = _run(gm, g, gm.GM_SSSP, seeds)
+                ref, rit = og.sssp(seeds)
+                assert np.array_equal(got, ref) and it == rit
 
 
 @pytest.mark.parametrize("direction", DIRS)

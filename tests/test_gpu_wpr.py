@@ -98,8 +98,11 @@ def test_backward_before_forward_is_rejected(gm):
 @pytest.mark.slow
 def test_scale20_config_gradient(gm):
     """The weighted-PageRank workload: RMAT scale 20, edge factor 16, w ~ U[0.5, 1.5],
-    30 supersteps, checkpoints every 5: forward within 1e-5 and the gradient of
-    every edge within 1e-4 (relative L2) of the FP64 oracle adjoint."""
+    30 supersteps, checkpoints every 5: forward within 1e-5 and the gradient
+    within 1e-4 of the FP64 oracle adjoint, both as relative L2 over all edges
+    and edge by edge, |g - g*| <= 1e-4 max(|g*|, 1e-3 max|g*|) (the floor of the
+    finite-difference check: a per-edge relative error means nothing where the
+    gradient is a rounding-level remainder of the row-normalisation term)."""
     g, og, w, tau, tw, ttau = _setup(gm, 20, seed=20)
     x = g.wpagerank_forward(tw, R, STEPS, 5)
     xo, _ = og.wpr_forward(w.astype(np.float64), tau.astype(np.float64), R, STEPS)
@@ -107,3 +110,10 @@ def test_scale20_config_gradient(gm):
     grad = g.wpagerank_backward(2.0 * (x - ttau)).cpu().numpy().astype(np.float64)
     go, _ = og.wpr_gradient(w.astype(np.float64), tau.astype(np.float64), R, STEPS)
     assert _rel_l2(grad, go) <= 1e-4
+    floor = 1e-3 * np.abs(go).max()
+    per_edge = np.abs(grad - go) / np.maximum(np.abs(go), floor)
+    worst = int(np.argmax(per_edge))
+    print(f"scale-20 gradient: rel L2 {_rel_l2(grad, go):.3e}, worst per-edge {per_edge[worst]:.3e} "
+          f"(edge {worst}, g* {go[worst]:.3e}, floor {floor:.3e}), "
+          f"edges above the floor {int(np.count_nonzero(np.abs(go) >= floor))} of {g.m}")
+    assert per_edge.max() <= 1e-4
