@@ -268,12 +268,15 @@ def reference_arm(args):
 
 
 def pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind):
-    """trav_pull_a, the dominant kernel (SSSP pull): CUDA events around each of its
+    """The dominant kernel, the SSSP pull (trav_pull_o over the octet layout; the
+    mixed-tile trav_pull_a for wide weights): CUDA events around each of its
     launches (profile mode); algorithmic bytes per launch = in-edges read x (4 B
     source id + the stored weight width + 1 bit of column start) + the message
     array once (4 B per vertex: vertex state counts once per superstep) + the
-    per-column result written once (4 B per non-empty column).  The BFS pull
-    (trav_pull_bu, bottom-up) is timed beside it."""
+    per-column result written once (4 B per non-empty column) -- a definition
+    independent of the layout; bytes_read_per_launch is what the layout streams.
+    The BFS pull (trav_pull_bu, bottom-up) is timed beside it, and the SSSP
+    push and finalize kernels get lines of their own."""
     wb = g.scalar(gm.GM_SCALAR_PULL_WEIGHT_BYTES)
     _, in_deg = g.degrees()
     state_bytes = 4.0 * g.n + 4.0 * float(np.count_nonzero(in_deg))
@@ -328,7 +331,7 @@ def pull_roofline(gm, g, bfs_src, sssp_src, src_dev, peak, peak_kind):
     dram_frac = (traffic / (ms / max(launches, 1) / 1e3) / 1e9 / peak) if (traffic and ms > 0) else None
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic, "traffic_frac": dram_frac,
-            "kernel": "trav_pull_a (SSSP pull)", "peak_source": peak_kind, "weight_bytes": wb,
+            "kernel": "trav_pull_o (SSSP pull over octets)", "peak_source": peak_kind, "weight_bytes": wb,
             "bytes_per_launch": byts / max(launches, 1), "avg_launch_us": 1e3 * ms / max(launches, 1),
             # what the kernel streams in the handle's layout (octets of 4-byte words holding
             # source rank and weight, padded per column, with a header byte per octet),
@@ -372,17 +375,20 @@ def _kernel_line(name, acc, peak):
             "achieved": gbs, "unit": "GB/s", "peak": peak, "frac": gbs / peak}
 
 
-# DRAM bytes (read + write) per trav_pull_a launch in the bench's timed step, from
-# one ncu capture of this bench command; valid only for the kernel source it was
-# taken on (hash of the traversal source files at capture time).
-PULL_A_TRAFFIC = {"source_sha256": "71d8e9daf29f6afac47967a1d20fd8ff92cdd433b99da93c585d6786999c8691",
-                  "bytes_per_launch": 365.08e6}
+# DRAM bytes (read + write) per launch of the SSSP pull on the bench graph, from
+# one ncu capture of that kernel (profiles/trav_pull_o_rmat22_traffic.md: two
+# launches, supersteps 3 and 4 of the first SSSP source); valid only for the
+# sources it was taken on (hash of the traversal kernels and of the graph build,
+# which lays the octets out).
+PULL_A_TRAFFIC = {"source_sha256": "9c88b2dc9535f46d79fa23adf6b419ba914d0829b70a62bfd5617ae57e33e4da",
+                  "bytes_per_launch": 333.6e6}
+_TRAFFIC_SOURCES = ("gm_traverse.cu", "gm_internal.cuh", "gm_graph.cu")
 
 
 def _kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("gm_traverse.cu", "gm_internal.cuh"):
+    for f in _TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, "paper_1503_07241_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
