@@ -460,6 +460,26 @@ def case_components(gm, synth):
     return g, lambda: (g.program_set(gm.GM_CONNECTED_COMPONENTS), g.run(-1))
 
 
+def cf_roofline(m, n, K, ms_iter, hbm_peak):
+    """A gradient-descent step of CF (Eqs. 3-5) two ways.  HBM, algorithmic: the
+    two passes stream every rating once each (4 B index + 4 B rating in the user
+    pass, 4 B index + 1 B rating in the item pass) and touch the factor state
+    seven times (read by each pass, the gradient accumulated, read and cleared by
+    the update, the factors read and written by it).  L2: each pass gathers one
+    K-wide factor row (4K B) per rating -- from L2, or from shared memory for
+    the most-rated items in the user pass -- which is what bounds the passes.
+    No L2 peak is reported: library copies over L2-resident buffers are bound
+    by their launch and ramp (a 48 MB copy reaches 5.1 TB/s, below a 512 MB
+    copy from HBM), so they do not measure it."""
+    hbm_bytes = m * (8 + 5) + 7 * n * K * 4
+    gather_bytes = 2 * m * K * 4
+    s = ms_iter / 1e3
+    return {"bound": "l2", "achieved": gather_bytes / s / 1e9, "unit": "GB/s",
+            "gather_bytes_per_iter": gather_bytes, "peak": None, "frac": None,
+            "hbm_algorithmic_bytes_per_iter": hbm_bytes, "hbm_achieved": hbm_bytes / s / 1e9,
+            "hbm_peak": hbm_peak, "hbm_frac": hbm_bytes / s / 1e9 / hbm_peak}
+
+
 def cf_sgd_summary(gm, g, ms_epoch):
     """One SGD epoch's figures.  The ratings of one item are serial in every order
     that reproduces serial SGD, so an epoch takes at least (ratings of the
@@ -720,7 +740,8 @@ def extras(gm):
         out["cf_100M_k32"] = {"ms_10_iters": ms, "ratings": g.m, "gamma": CF_GAMMA,
                               "loss_after_1": loss_a, "loss_after_11": loss_b, "loss_decreased": loss_b < loss_a,
                               "ratings_per_s": 10 * g.m / (ms / 1e3),
-                              "gflops": 10 * g.m * 6 * 32 / (ms / 1e3) / 1e9}
+                              "gflops": 10 * g.m * 6 * 32 / (ms / 1e3) / 1e9,
+                              "roofline": cf_roofline(g.m, g.n, 32, ms / 10, _peaks()[0])}
     except Exception as e:  # pragma: no cover
         out["cf_100M_k32"] = {"error": str(e)}
     try:  # the same ratings by stochastic gradient descent, 3 epochs in the default strata

@@ -122,3 +122,16 @@ def test_recorded_traffic_is_dropped_when_the_kernel_source_changes(monkeypatch)
     assert bench._recorded_traffic() is None
     monkeypatch.setattr(bench, "_kernel_source_hash", lambda: bench.PULL_A_TRAFFIC["source_sha256"])
     assert bench._recorded_traffic() == bench.PULL_A_TRAFFIC["bytes_per_launch"]
+
+
+def test_cf_roofline_arithmetic():
+    """CF step roofline: HBM algorithmic bytes = ratings streamed once per pass
+    (8 B + 5 B) + seven touches of the factor state; L2 bytes = one K-wide row
+    gathered per rating in each pass."""
+    import bench
+    r = bench.cf_roofline(m=1000, n=100, K=32, ms_iter=1.0, hbm_peak=5000.0)
+    assert r["hbm_algorithmic_bytes_per_iter"] == 1000 * 13 + 7 * 100 * 32 * 4
+    assert r["gather_bytes_per_iter"] == 2 * 1000 * 128
+    assert abs(r["achieved"] - 2 * 1000 * 128 / 1e-3 / 1e9) < 1e-9
+    assert r["bound"] == "l2" and r["peak"] is None
+    assert abs(r["hbm_frac"] - r["hbm_achieved"] / 5000.0) < 1e-12
