@@ -1287,8 +1287,12 @@ __device__ __forceinline__ void pull_apply(const TravArgs& a, uint32_t t, WarpQ*
     flush_acc(a, acc, nxt, false, s_stat);
 }
 
+// SSSP: at most 64 registers, so four CTAs share an SM (the push waits on chains
+// of dependent loads ending in an atomic minimum; measured on RMAT-22: 28.5 ->
+// 25.7 us per launch against three CTAs at 80 registers, a few spilled words
+// included).
 template <bool SSSP>
-__global__ void __launch_bounds__(kThreads) trav_push(TravArgs a) {
+__global__ void __launch_bounds__(kThreads, SSSP ? 4 : 1) trav_push(TravArgs a) {
 
     TravCtlDev* cd = a.ctl;
     if (cd->c.done || cd->c.dir != 0u) return;
