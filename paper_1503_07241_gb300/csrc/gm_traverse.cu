@@ -1287,12 +1287,13 @@ __device__ __forceinline__ void pull_apply(const TravArgs& a, uint32_t t, WarpQ*
     flush_acc(a, acc, nxt, false, s_stat);
 }
 
-// SSSP: at most 64 registers, so four CTAs share an SM (the push waits on chains
-// of dependent loads ending in an atomic minimum; measured on RMAT-22: 28.5 ->
-// 25.7 us per launch against three CTAs at 80 registers, a few spilled words
-// included).
+// Occupancy: the push waits on chains of dependent loads (ending in an atomic
+// minimum for SSSP), so more resident warps pay.  SSSP at most 64 registers,
+// four CTAs per SM (RMAT-22: 28.5 -> 25.7 us per launch against three at 80, a
+// few spilled words included); BFS at most 80, three CTAs (two at its natural
+// 96; 16 BFS queries 5.25 -> 5.16 ms).
 template <bool SSSP>
-__global__ void __launch_bounds__(kThreads, SSSP ? 4 : 1) trav_push(TravArgs a) {
+__global__ void __launch_bounds__(kThreads, SSSP ? 4 : 3) trav_push(TravArgs a) {
 
     TravCtlDev* cd = a.ctl;
     if (cd->c.done || cd->c.dir != 0u) return;
