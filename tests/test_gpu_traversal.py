@@ -189,6 +189,27 @@ def test_golden_tiny(gm):
         assert got.tolist() == gd["bfs_depth"] and it == gd["bfs_supersteps"]
 
 
+@pytest.mark.parametrize("packed", [1, 0])
+def test_pull_on_graphs_without_in_edges(gm, packed):
+    """SSSP and BFS forced to pull on graphs whose pull has nothing to stream: no
+    edges, only self-loops (removed by cleaning), a single vertex.  The octet
+    layout then has no tile; results and superstep counts equal the oracle's."""
+    cases = [(6, np.zeros(0, np.int32), np.zeros(0, np.int32)),
+             (4, np.array([0, 1, 2], np.int32), np.array([0, 1, 2], np.int32)),
+             (1, np.zeros(0, np.int32), np.zeros(0, np.int32))]
+    for n, s, d in cases:
+        w = np.full(len(s), 7, np.uint32)
+        g = gm.Graph(n, s, d, w)
+        og = oracle.Graph(n, s, d, w)
+        g.program_set(gm.GM_SSSP)
+        g.set_option(gm.GM_OPT_PULL_PACKED, packed)
+        g.set_option(gm.GM_OPT_DIRECTION, 2)
+        for kind, ref_fn in ((gm.GM_SSSP, og.sssp), (gm.GM_BFS, og.bfs)):
+            got, it = _run(gm, g, kind, [0])
+            ref, rit = ref_fn([0])
+            assert np.array_equal(got, ref) and it == rit
+
+
 def test_edge_cases(gm):
     # isolated source: one superstep that finds nothing
     g = gm.Graph(5, np.array([1], np.int32), np.array([2], np.int32))
