@@ -641,14 +641,32 @@ gm_status balance_octets(gm_graph* g, int64_t hot) {
 // (oct_w, oct_meta, oct_c0) when every weight fits a byte, n <= 2^24 and the
 // layout option allows it; otherwise the ranks alone (row_r), the weights then
 // coming from cw8 or cw.  Replaces whichever exists.
-gm_status build_pull_edge_words(gm_graph* g) {
+namespace {
+void free_pull_edge_words(gm_graph* g) {
     cudaStream_t s = g->stream;
-    const int64_t m = g->m, ncols = g->dc_ncols;
     dev_free(g->row_r, s);
     dev_free(g->oct_w, s);
     dev_free(g->oct_meta, s);
     dev_free(g->oct_c0, s);
     g->oct_tiles = g->oct_slots = 0;
+}
+
+gm_status build_pull_edge_words_impl(gm_graph* g);
+}  // namespace
+
+// All or nothing: a failure leaves neither layout (the SSSP pull then refuses
+// to run until the next gm_program_set builds it).
+gm_status build_pull_edge_words(gm_graph* g) {
+    const gm_status st = build_pull_edge_words_impl(g);
+    if (st != GM_OK) free_pull_edge_words(g);
+    return st;
+}
+
+namespace {
+gm_status build_pull_edge_words_impl(gm_graph* g) {
+    cudaStream_t s = g->stream;
+    const int64_t m = g->m, ncols = g->dc_ncols;
+    free_pull_edge_words(g);
     const bool packed = g->tune.pull_packed && g->cw8.p != nullptr && g->n <= kPackedMaxVertices;
     if (!packed) {
         GM_TRY(dev_alloc(g->row_r, sizeof(int32_t) * (m + kEdgePad), s));
@@ -695,9 +713,30 @@ gm_status build_pull_edge_words(gm_graph* g) {
     g->oct_slots = (int64_t)octets * kOctet;
     return balance_octets(g, pull_stage_messages(g));
 }
+}  // namespace
 
+namespace {
+gm_status build_source_ranks_impl(gm_graph* g);
+}  // namespace
+
+// All or nothing: on failure the ranks and the in-edge layout are freed, so the
+// next SSSP gm_program_set builds them again.
 gm_status build_source_ranks(gm_graph* g) {
-    if (g->src_rank.p) return GM_OK;
+    if (g->src_rank.p) {  // ranks exist; the layout too unless its last rebuild failed
+        if (g->oct_w.p || g->row_r.p) return GM_OK;
+        return build_pull_edge_words(g);
+    }
+    const gm_status st = build_source_ranks_impl(g);
+    if (st != GM_OK) {
+        dev_free(g->src_rank, g->stream);
+        dev_free(g->dc_rank, g->stream);
+        free_pull_edge_words(g);
+    }
+    return st;
+}
+
+namespace {
+gm_status build_source_ranks_impl(gm_graph* g) {
     cudaStream_t s = g->stream;
     const int64_t n = g->n, m = g->m;
     struct Tmp {
@@ -730,6 +769,7 @@ gm_status build_source_ranks(gm_graph* g) {
     GM_CUDA_TRY(cudaStreamSynchronize(s));  // the temporaries are freed on return
     return GM_OK;
 }
+}  // namespace
 
 void release_graph(gm_graph* g);
 

@@ -5,6 +5,7 @@
 #include <cstdio>
 
 #include <atomic>
+#include <mutex>
 
 #include "gm_internal.cuh"
 
@@ -27,6 +28,41 @@ const char* last_error() { return t_err; }
 // gm_debug_fail_allocations_after); < 0 disables.
 std::atomic<int64_t> g_alloc_budget{-1};
 
+// The library's stream-ordered memory pool on the current device, created on
+// first use.  Freed memory stays in the pool, up to an eighth of the device's
+// memory, so the next graph build or program set reuses it instead of mapping
+// new pages: graph ingest allocates and frees gigabytes of temporaries, and the
+// default pool hands them back to the system at every synchronisation
+// (RMAT-22: graph creation 25.6 -> 17.0 ms).  An allocation the pool cannot
+// satisfy trims the pool and is tried once more.  nullptr: no pool (the
+// default pool is used).
+cudaMemPool_t library_pool() {
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static cudaMemPool_t pools[kMaxDev] = {};
+    static bool tried[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!tried[dev]) {
+        tried[dev] = true;
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+            size_t free_b = 0, total_b = 0;
+            uint64_t keep = cudaMemGetInfo(&free_b, &total_b) == cudaSuccess ? (uint64_t)total_b / 8 : 0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            pools[dev] = pool;
+        } else {
+            cudaGetLastError();  // fall back to the default pool
+        }
+    }
+    return pools[dev];
+}
+
 gm_status dev_alloc(DevBuf& b, size_t bytes, cudaStream_t s) {
     dev_free(b, s);
     if (bytes == 0) bytes = 16;
@@ -37,7 +73,14 @@ gm_status dev_alloc(DevBuf& b, size_t bytes, cudaStream_t s) {
         }
         if (g_alloc_budget.compare_exchange_weak(left, left - 1)) break;
     }
-    cudaError_t e = cudaMallocAsync(&b.p, bytes, s);
+    cudaMemPool_t pool = library_pool();
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(&b.p, bytes, pool, s) : cudaMallocAsync(&b.p, bytes, s);
+    if (e == cudaErrorMemoryAllocation && pool) {  // give the cached memory back and try once more
+        cudaGetLastError();
+        cudaStreamSynchronize(s);
+        cudaMemPoolTrimTo(pool, 0);
+        e = cudaMallocFromPoolAsync(&b.p, bytes, pool, s);
+    }
     if (e != cudaSuccess) {
         b.p = nullptr;
         set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));

@@ -2076,7 +2076,9 @@ gm_status trav_prepare(gm_graph* g) {
 // changed (the message arrays are SSSP's alone).
 gm_status trav_reuse(gm_graph* g) {
     cudaStream_t s = g->stream;
-    if (g->kind == GM_SSSP && !g->src_rank.p) {  // the SSSP loop graph needs the ranks; build them first
+    // the SSSP loop graph needs the ranks and the pull's in-edge layout; build
+    // them first (or again, after a failed rebuild of the layout)
+    if (g->kind == GM_SSSP && (!g->src_rank.p || (!g->oct_w.p && !g->row_r.p))) {
         GM_TRY(build_source_ranks(g));
         trav_release(g);
     }
@@ -2115,6 +2117,11 @@ gm_status trav_set_active(gm_graph* g, const int32_t* vertices_dev, int64_t coun
 gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done) {
     cudaStream_t s = g->stream;
     const bool sssp = g->kind == GM_SSSP;
+    if (sssp && (!g->src_rank.p || (!g->oct_w.p && !g->row_r.p))) {
+        set_error("gm_run: the SSSP pull's in-edge layout is missing (a previous call failed to build it); "
+                  "call gm_program_set again");
+        return GM_ERR_STATE;
+    }
     g->stats = RunStats{};
     g->frontier_clean = false;
     if (sssp) g->msg_clean = false;

@@ -91,3 +91,55 @@ def test_sgd_grid_barrier_wait_runs_out(gm):
     ref = og.cf_sgd(32, 0.05, 1e-2, 2, nu, 64, p0)
     assert g.run(2) == 2
     np.testing.assert_allclose(g.state().astype(np.float64), ref, rtol=1e-4, atol=2e-5)
+
+
+def test_failed_layout_builds_recover_on_the_same_handle(gm):
+    """An allocation failure while the SSSP pull's ranks and in-edge layout are
+    built (gm_program_set) or rebuilt (the layout option) leaves the handle
+    without a layout: gm_run refuses with an error instead of running, and the
+    next successful gm_program_set builds it again; the same handle then matches
+    the oracle."""
+    rng = np.random.default_rng(93)
+    n, s, d, w = random_case(rng, 3000, 20000, weighted=True)
+    og = oracle.Graph(n, s, d, w)
+    want, wit = og.sssp([0])
+    recovered = 0
+    for k in range(12):
+        g = gm.Graph(n, s, d, w)
+        g.program_set(gm.GM_BFS)
+        gm.lib().gm_debug_fail_allocations_after(k)
+        try:
+            g.program_set(gm.GM_SSSP)
+            failed = False
+        except gm.GMError as e:
+            assert e.status == gm.GM_ERR_OUT_OF_MEMORY
+            failed = True
+        finally:
+            gm.lib().gm_debug_fail_allocations_after(-1)
+        if failed:
+            with pytest.raises(gm.GMError):
+                g.run(-1)
+            g.program_set(gm.GM_SSSP)
+            recovered += 1
+        g.set_active([0])
+        it = g.run(-1)
+        assert np.array_equal(g.state(), want) and it == wit
+    assert recovered >= 3
+    # the layout option's rebuild fails: no run until the next program_set
+    g = gm.Graph(n, s, d, w)
+    g.program_set(gm.GM_SSSP)
+    gm.lib().gm_debug_fail_allocations_after(0)
+    try:
+        with pytest.raises(gm.GMError) as ei:
+            g.set_option(gm.GM_OPT_PULL_PACKED, 0)
+        assert ei.value.status == gm.GM_ERR_OUT_OF_MEMORY
+    finally:
+        gm.lib().gm_debug_fail_allocations_after(-1)
+    g.set_active([0])
+    with pytest.raises(gm.GMError) as ei:
+        g.run(-1)
+    assert ei.value.status == gm.GM_ERR_STATE
+    g.program_set(gm.GM_SSSP)
+    g.set_active([0])
+    it = g.run(-1)
+    assert np.array_equal(g.state(), want) and it == wit
