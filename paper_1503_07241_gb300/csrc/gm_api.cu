@@ -110,8 +110,18 @@ gm_status gm_program_set(gm_graph* g, int32_t kind, const gm_program_params* par
         if (st != GM_OK) g->kind = -1;
         return st;
     }
+    if (kind == GM_PAGERANK && g->kind == GM_PAGERANK && g->state.p && g->work.p) {
+        // PageRank again: keep the buffers and the cached superstep graph (it is
+        // rebuilt at the next run only if r or the apply rule changed)
+        g->params = p;
+        g->stats = RunStats{};
+        const gm_status st = pr_reset(g);
+        if (st != GM_OK) g->kind = -1;
+        return st;
+    }
     trav_release(g);
     cf_release(g);
+    pr_release(g);
     dev_free(g->state, g->stream);
     dev_free(g->work, g->stream);
     g->kind = kind;

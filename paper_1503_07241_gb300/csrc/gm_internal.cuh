@@ -203,6 +203,7 @@ struct gm_graph {
     uint64_t tc_total = 0;
     void* wpr = nullptr;             // weighted-PageRank buffers (gm_wpr.cu)
     void* cf = nullptr;              // collaborative-filtering buffers (gm_cf.cu)
+    void* pr = nullptr;              // PageRank's cached superstep graph (gm_pagerank.cu)
 };
 
 namespace gm {
@@ -229,6 +230,8 @@ gm_status cf_loss(gm_graph* g, double* out);
 gm_status reached_edges(gm_graph* g, int64_t* out);
 void wpr_release(gm_graph* g);
 void cf_release(gm_graph* g);
+void pr_release(gm_graph* g);
+gm_status pr_reset(gm_graph* g);  // ranks back to 1.0, buffers kept
 gm_status cc_prepare(gm_graph* g);  // gm_cc.cu
 gm_status cc_run(gm_graph* g, int32_t max_iters, int32_t* iters_done);
 // Per-edge source ids of a CSR (out[e] = v for e in [ptr[v], ptr[v+1])).

@@ -1,12 +1,16 @@
 // PageRank supersteps (Eq. 1) as a pull SpMV over the CSC form with Apply fused:
 //   x_{t+1}(v) = r + (1 - r) * sum_{u -> v} c_t(u),   c_t(u) = x_t(u) / deg(u).
 // Every vertex is active in every superstep, so the sparse vector is dense and
-// the pull form needs no frontier test and no atomics: each destination is
-// reduced by exactly one thread group (a lane for in-degree < bin_small -- that bin
-// is stored ordered by degree, so a warp's 32 destinations have about the same
-// length -- a warp up to bin_large, a CTA beyond), four in-edges in flight per
-// thread, in a fixed order, in FP32.  The Apply step writes both the new rank and
-// the next contribution c_{t+1}(v).
+// the pull form needs no frontier test.  The in-edges are cut into fixed
+// 256-edge warp tiles (pr_tiles), so a hub column is summed by many warps at
+// once instead of one CTA walking its whole list; the pieces of a column that
+// crosses tiles are combined by pr_cross.  FP32, every sum in a fixed order
+// (deterministic); the Apply step writes both the new rank and the next
+// contribution c_{t+1}(v).
+#include <algorithm>
+#include <cstring>
+#include <new>
+
 #include "gm_internal.cuh"
 
 namespace gm {
@@ -17,19 +21,15 @@ constexpr int kThreads = 256;
 constexpr uint32_t kFull = 0xffffffffu;
 
 struct PrArgs {
-    const int32_t* col_ptr; const int32_t* row; const int32_t* out_deg;
-    const int32_t* in_list; int64_t in_off[4];
+    const int32_t* row; const int32_t* out_deg;
+    const int32_t* dc_jc; const int32_t* dc_cp; const int32_t* dc_tile; const uint32_t* dc_head;
+    int64_t ntiles, m;
     const int32_t* zero_in; int64_t zero_count;
     const float* x_cur; float* x_nxt;
     const float* c_cur; float* c_nxt;
+    float* lead; float* trail;  // per tile: partial sums of the columns that cross tiles
     float r; int apply_all;
 };
-
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
 
 __device__ __forceinline__ void pr_apply(const PrArgs& a, int32_t v, float sum) {
     const float x = a.r + (1.0f - a.r) * sum;
@@ -38,67 +38,111 @@ __device__ __forceinline__ void pr_apply(const PrArgs& a, int32_t v, float sum) 
     a.c_nxt[v] = d > 0 ? x / (float)d : 0.0f;
 }
 
-__global__ void __launch_bounds__(kThreads) pr_step(PrArgs a) {
+// Apply for the vertex of non-empty column col.
+__device__ __forceinline__ void pr_apply_col(const PrArgs& a, int32_t col, float sum) {
+    pr_apply(a, __ldg(a.dc_jc + col), sum);
+}
+
+constexpr int kEPT = 8;  // in-edges per lane of a 256-edge warp tile (kWTile = 32 x 8)
+
+// PageRank superstep over 256-edge warp tiles of the CSC (the doubly compressed
+// CSC's tiles: dc_tile = column holding the tile's first edge, dc_head = one bit
+// per in-edge marking a column's first).  Lane L takes edges 8L..8L+7 of the
+// tile and sums c(u) over them in order, splitting at column starts; a
+// segmented inclusive sum across the lanes (fixed shuffle order) joins the
+// pieces of a column that spans lanes.  A column that begins and ends inside
+// the tile is applied at once.  A column spread over tiles t0..t1 leaves a
+// partial sum in each: trail[t0] (from its start to the end of t0) and lead[t]
+// for t0 < t <= t1 (its part before the first column start of t, the whole
+// tile for t < t1); pr_cross adds them up and applies.  No column's chain of
+// dependent loads is longer than one tile's.
+__global__ void __launch_bounds__(kThreads) pr_tiles(PrArgs a) {
     const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
     const uint32_t gwarp = (blockIdx.x * kThreads + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * kThreads) >> 5;
-    __shared__ float s_red[kThreads / 32];
-
-    // large in-degree: one CTA per vertex
-    for (int64_t i = a.in_off[2] + blockIdx.x; i < a.in_off[3]; i += gridDim.x) {
-        const int32_t v = a.in_list[i];
-        const int32_t beg = a.col_ptr[v], end = a.col_ptr[v + 1];
-        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-        int32_t e = beg + threadIdx.x;
-        for (; e + 3 * kThreads < end; e += 4 * kThreads) {
-            s0 += a.c_cur[a.row[e]];
-            s1 += a.c_cur[a.row[e + kThreads]];
-            s2 += a.c_cur[a.row[e + 2 * kThreads]];
-            s3 += a.c_cur[a.row[e + 3 * kThreads]];
+    const uint32_t ntiles = (uint32_t)a.ntiles, m = (uint32_t)a.m;
+    for (uint32_t k = gwarp; k < ntiles; k += nwarps) {
+        const uint32_t e0 = k * 256u + (uint32_t)lane * kEPT;
+        const uint32_t nv = e0 < m ? min((uint32_t)kEPT, m - e0) : 0u;
+        int32_t src[kEPT];
+        float cv[kEPT];
+        if (nv == (uint32_t)kEPT) {
+            const int4 lo = __ldg(reinterpret_cast<const int4*>(a.row + e0));
+            const int4 hi = __ldg(reinterpret_cast<const int4*>(a.row + e0 + 4));
+            src[0] = lo.x; src[1] = lo.y; src[2] = lo.z; src[3] = lo.w;
+            src[4] = hi.x; src[5] = hi.y; src[6] = hi.z; src[7] = hi.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < kEPT; ++q) src[q] = (uint32_t)q < nv ? __ldg(a.row + e0 + q) : 0;
         }
-        for (; e < end; e += kThreads) s0 += a.c_cur[a.row[e]];
-        float s = warp_sum_f((s0 + s1) + (s2 + s3));
-        if (lane == 0) s_red[wid] = s;
-        __syncthreads();
-        if (wid == 0) {
-            float t = lane < kThreads / 32 ? s_red[lane] : 0.0f;
-            t = warp_sum_f(t);
-            if (lane == 0) pr_apply(a, v, t);
+#pragma unroll
+        for (int q = 0; q < kEPT; ++q) cv[q] = (uint32_t)q < nv ? __ldg(a.c_cur + src[q]) : 0.0f;
+        const uint32_t hw = e0 < m ? __ldg(a.dc_head + (e0 >> 5)) : 0u;
+        const uint32_t heads = (hw >> ((lane & 3) * 8)) & ((1u << nv) - 1u);
+        const int32_t c0 = __ldg(a.dc_tile + k);
+        // column numbering: column starts before this lane, and whether the tile starts one
+        uint32_t hincl = (uint32_t)__popc(heads);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, hincl, o);
+            if (lane >= o) hincl += y;
         }
-        __syncthreads();
-    }
-    // medium: one warp per vertex
-    for (int64_t i = a.in_off[1] + gwarp; i < a.in_off[2]; i += nwarps) {
-        const int32_t v = a.in_list[i];
-        const int32_t beg = a.col_ptr[v], end = a.col_ptr[v + 1];
-        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-        int32_t e = beg + lane;
-        for (; e + 96 < end; e += 128) {
-            s0 += a.c_cur[a.row[e]];
-            s1 += a.c_cur[a.row[e + 32]];
-            s2 += a.c_cur[a.row[e + 64]];
-            s3 += a.c_cur[a.row[e + 96]];
+        const uint32_t hex = hincl - (uint32_t)__popc(heads);
+        const uint32_t bal_first = __ballot_sync(kFull, heads & 1u);
+        const uint32_t bal_seen = __ballot_sync(kFull, heads != 0u);
+        const uint32_t first_is_head = bal_first & 1u;
+        const int32_t col_base = c0 + (int32_t)hex - (int32_t)first_is_head;
+        // lane runs: F before the first start, complete runs applied, the last run open
+        float F = 0.0f, run = 0.0f;
+        int32_t run_col = col_base;
+        const bool seen = heads != 0u;
+#pragma unroll
+        for (int q = 0; q < kEPT; ++q) {
+            if ((heads >> q) & 1u) {
+                if ((heads & ((1u << q) - 1u)) != 0u) pr_apply_col(a, run_col, run);  // inside this lane
+                else F = run;
+                run = 0.0f;
+                run_col = col_base + (int32_t)__popc(heads & ((2u << q) - 1u));
+            }
+            run += cv[q];
         }
-        for (; e < end; e += 32) s0 += a.c_cur[a.row[e]];
-        const float s = warp_sum_f((s0 + s1) + (s2 + s3));
-        if (lane == 0) pr_apply(a, v, s);
-    }
-    // small: one lane per vertex, four in-edges in flight
-    for (int64_t i = a.in_off[0] + (int64_t)gwarp * 32 + lane; i - lane < a.in_off[1]; i += (int64_t)nwarps * 32) {
-        if (i >= a.in_off[1]) continue;
-        const int32_t v = a.in_list[i];
-        const int32_t beg = a.col_ptr[v], end = a.col_ptr[v + 1];
-        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-        int32_t e = beg;
-        for (; e + 3 < end; e += 4) {
-            s0 += a.c_cur[a.row[e]];
-            s1 += a.c_cur[a.row[e + 1]];
-            s2 += a.c_cur[a.row[e + 2]];
-            s3 += a.c_cur[a.row[e + 3]];
+        if (!seen) F = run;
+        float R = seen ? run : F;
+        const uint32_t le = bal_seen & (0xFFFFFFFFu >> (31 - lane));
+        const int seg0 = le ? 31 - __clz(le) : -1;  // -1: the segment began before the tile
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float Ru = __shfl_up_sync(kFull, R, o);
+            if (lane - o >= max(seg0, 0)) R += Ru;
         }
-        for (; e < end; ++e) s0 += a.c_cur[a.row[e]];
-        pr_apply(a, v, (s0 + s1) + (s2 + s3));
+        float Rprev = __shfl_up_sync(kFull, R, 1);
+        if (lane == 0) Rprev = 0.0f;
+        const bool fprev = lane > 0 && (bal_seen & ((1u << lane) - 1u)) != 0u;
+        // the leading segment belongs to column c0, begun in an earlier tile
+        float lead = 0.0f;
+        bool lead_end = false;
+        if (seen && !(heads & 1u)) {  // this lane's first edges finish a column begun to its left
+            if (fprev) pr_apply_col(a, col_base, F + Rprev);
+            else { lead = F + Rprev; lead_end = true; }
+        }
+        const bool next_head = lane < 31 && ((bal_first >> (lane + 1)) & 1u);
+        if (lane == 31 || next_head) {
+            const int32_t end_col = c0 + (int32_t)hincl - (int32_t)first_is_head;
+            if (seg0 < 0) {
+                lead = R;  // the leading segment ends here
+                lead_end = true;
+            } else if (lane < 31) {
+                pr_apply_col(a, end_col, R);  // complete inside the tile
+            } else {  // the trailing segment: complete unless the column goes on
+                const int64_t t1 = ((int64_t)__ldg(a.dc_cp + end_col + 1) - 1) >> 8;
+                if (t1 == (int64_t)k) {
+                    pr_apply_col(a, end_col, R);
+                } else {
+                    a.trail[k] = R;
+                }
+            }
+        }
+        if (lead_end) a.lead[k] = lead;
     }
     // vertices without in-edges receive no message
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < a.zero_count;
@@ -107,9 +151,54 @@ __global__ void __launch_bounds__(kThreads) pr_step(PrArgs a) {
         if (a.apply_all) {
             pr_apply(a, v, 0.0f);
         } else {
-            const float x = a.x_cur[v];
-            a.x_nxt[v] = x;
+            a.x_nxt[v] = a.x_cur[v];
             a.c_nxt[v] = a.c_cur[v];
+        }
+    }
+}
+
+constexpr int64_t kSerialTiles = 8;  // crossing columns over more tiles are summed by a whole warp
+
+// The second half of a superstep: the columns that cross tiles.  Tile k's last
+// column continues into tile k + 1 when edge 256(k+1) starts no column; it
+// starts in tile k (so k is its t0) when its first edge lies there.  One thread
+// per tile finds its column and, when the column spans at most kSerialTiles
+// tiles, sums trail[t0] + lead[t0+1] + ... + lead[t1] in that order; longer
+// ones (the hubs) are summed by the whole warp, each lane over a fixed stride
+// of tiles, then a fixed shuffle tree.  Either way the order is fixed.
+__global__ void __launch_bounds__(kThreads) pr_cross(PrArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nt = a.ntiles;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t base = (int64_t)blockIdx.x * kThreads + (threadIdx.x & ~31); base < nt - 1; base += stride) {
+        const int64_t k = base + lane;
+        bool cross = false;
+        int32_t col = 0;
+        int64_t t1 = 0;
+        if (k < nt - 1 && (__ldg(a.dc_head + (k + 1) * 8) & 1u) == 0u) {
+            col = __ldg(a.dc_tile + k + 1);
+            if (((int64_t)__ldg(a.dc_cp + col) >> 8) == k) {
+                cross = true;
+                t1 = ((int64_t)__ldg(a.dc_cp + col + 1) - 1) >> 8;
+            }
+        }
+        if (cross && t1 - k <= kSerialTiles) {
+            float sum = __ldg(a.trail + k);
+            for (int64_t t = k + 1; t <= t1; ++t) sum += __ldg(a.lead + t);
+            pr_apply_col(a, col, sum);
+        }
+        uint32_t big = __ballot_sync(kFull, cross && t1 - k > kSerialTiles);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int64_t kk = __shfl_sync(kFull, k, src);
+            const int64_t tt = __shfl_sync(kFull, t1, src);
+            const int32_t cc = __shfl_sync(kFull, col, src);
+            float sum = lane == 0 ? __ldg(a.trail + kk) : 0.0f;
+            for (int64_t t = kk + 1 + lane; t <= tt; t += 32) sum += __ldg(a.lead + t);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+            if (lane == 0) pr_apply_col(a, cc, sum);
         }
     }
 }
@@ -131,7 +220,7 @@ int pr_grid() {
     static int blocks = 0;
     if (blocks == 0) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pr_step, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pr_tiles, kThreads, 0);
         if (per_sm <= 0) per_sm = 1;
         if (per_sm > 8) per_sm = 8;
         blocks = per_sm * num_sms();
@@ -139,35 +228,113 @@ int pr_grid() {
     return blocks;
 }
 
+int cross_grid(const gm_graph* g) {
+    const int64_t blocks = (g->dc_ntiles + kThreads - 1) / kThreads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)num_sms() * 8));
+}
+
+// Workspace: the other rank array, two contribution arrays, and per tile the
+// leading and trailing partial sums.
+size_t pr_work_bytes(const gm_graph* g) {
+    const int64_t n = g->n > 0 ? g->n : 1, nt = g->dc_ntiles > 0 ? g->dc_ntiles : 1;
+    return sizeof(float) * (3 * (size_t)n + 2 * (size_t)nt);
+}
+
 PrArgs make_pr_args(gm_graph* g, int parity) {
-    const int64_t n = g->n > 0 ? g->n : 1;
-    float* X[2] = {as<float>(g->state), as<float>(g->work)};
-    float* C[2] = {as<float>(g->work) + n, as<float>(g->work) + 2 * n};
+    const int64_t n = g->n > 0 ? g->n : 1, nt = g->dc_ntiles > 0 ? g->dc_ntiles : 1;
+    float* work = as<float>(g->work);
+    float* X[2] = {as<float>(g->state), work};
+    float* C[2] = {work + n, work + 2 * n};
     PrArgs a{};
-    a.col_ptr = as<int32_t>(g->col_ptr);
     a.row = as<int32_t>(g->row);
     a.out_deg = as<int32_t>(g->out_deg);
-    a.in_list = as<int32_t>(g->in_list);
-    for (int b = 0; b < 4; ++b) a.in_off[b] = g->in_list_count[b];
+    a.dc_jc = as<int32_t>(g->dc_jc);
+    a.dc_cp = as<int32_t>(g->dc_cp);
+    a.dc_tile = as<int32_t>(g->dc_tile);
+    a.dc_head = as<uint32_t>(g->dc_head);
+    a.ntiles = g->dc_ntiles;
+    a.m = g->m;
     a.zero_in = as<int32_t>(g->zero_in_list);
     a.zero_count = g->zero_in_count;
     a.x_cur = X[parity];
     a.x_nxt = X[parity ^ 1];
     a.c_cur = C[parity];
     a.c_nxt = C[parity ^ 1];
+    a.lead = work + 3 * n;
+    a.trail = work + 3 * n + nt;
     a.r = (float)g->params.r;
     a.apply_all = g->params.pr_apply_all;
     return a;
 }
 
+// The superstep graph of a run: `iters` pairs of nodes (pr_tiles, pr_cross), the arguments
+// alternating between the two parities.  Kept on the handle and reused while
+// the superstep count and the arguments (buffers, r, the apply rule) are
+// unchanged.
+struct PrGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int32_t iters = 0;
+    PrArgs args[2];
+};
+
+gm_status pr_graph_for(gm_graph* g, int32_t iters, int grid, int cgrid) {
+    PrArgs args[2] = {make_pr_args(g, 0), make_pr_args(g, 1)};
+    PrGraph* pg = static_cast<PrGraph*>(g->pr);
+    if (pg && pg->exec && pg->iters == iters && std::memcmp(pg->args, args, sizeof(args)) == 0) return GM_OK;
+    pr_release(g);
+    pg = new (std::nothrow) PrGraph();
+    if (!pg) { set_error("PageRank graph: host allocation failed"); return GM_ERR_OUT_OF_MEMORY; }
+    std::memcpy(pg->args, args, sizeof(args));
+    pg->iters = iters;
+    cudaError_t e = cudaGraphCreate(&pg->graph, 0);
+    cudaGraphNode_t prev = nullptr;
+    for (int32_t it = 0; it < 2 * iters && e == cudaSuccess; ++it) {
+        void* kargs[] = {&pg->args[(it >> 1) & 1]};
+        cudaKernelNodeParams kp = {};
+        kp.func = (it & 1) ? (void*)pr_cross : (void*)pr_tiles;
+        kp.gridDim = dim3((unsigned)((it & 1) ? cgrid : grid));
+        kp.blockDim = dim3(kThreads);
+        kp.kernelParams = kargs;
+        cudaGraphNode_t node;
+        e = cudaGraphAddKernelNode(&node, pg->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+        prev = node;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&pg->exec, pg->graph, 0);
+    g->pr = pg;
+    if (e != cudaSuccess) {
+        pr_release(g);
+        set_error("PageRank graph: %s", cudaGetErrorString(e));
+        return GM_ERR_CUDA;
+    }
+    return GM_OK;
+}
+
 }  // namespace
+
+void pr_release(gm_graph* g) {
+    PrGraph* pg = static_cast<PrGraph*>(g->pr);
+    if (!pg) return;
+    if (pg->exec) cudaGraphExecDestroy(pg->exec);
+    if (pg->graph) cudaGraphDestroy(pg->graph);
+    delete pg;
+    g->pr = nullptr;
+}
+
+gm_status pr_reset(gm_graph* g) {
+    fill_f32<<<num_sms() * 4, 256, 0, g->stream>>>(as<float>(g->state), g->n, 1.0f);
+    g_launches++;
+    GM_CUDA_TRY(cudaGetLastError());
+    GM_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return GM_OK;
+}
 
 gm_status pr_prepare(gm_graph* g) {
     cudaStream_t s = g->stream;
     const int64_t n = g->n > 0 ? g->n : 1;
     GM_TRY(dev_alloc(g->state, sizeof(float) * n, s));
-    GM_TRY(dev_alloc(g->work, sizeof(float) * 3 * n, s));
-    g->work_bytes = (int64_t)(sizeof(float) * 3 * n);
+    GM_TRY(dev_alloc(g->work, pr_work_bytes(g), s));
+    g->work_bytes = (int64_t)pr_work_bytes(g);
     fill_f32<<<num_sms() * 4, 256, 0, s>>>(as<float>(g->state), g->n, 1.0f);
     g_launches++;
     GM_CUDA_TRY(cudaGetLastError());
@@ -190,7 +357,7 @@ gm_status pr_run(gm_graph* g, int32_t iters, int32_t* iters_done) {
                                                   as<float>(g->work) + n);
     g_launches++;
     GM_CUDA_TRY(cudaGetLastError());
-    const int grid = pr_grid();
+    const int grid = pr_grid(), cgrid = cross_grid(g);
     if (g->tune.profile || g->tune.loop_mode == 1) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (g->tune.profile) {
@@ -200,9 +367,10 @@ gm_status pr_run(gm_graph* g, int32_t iters, int32_t* iters_done) {
         for (int32_t it = 0; it < iters; ++it) {
             PrArgs a = make_pr_args(g, it & 1);
             if (e0) cudaEventRecord(e0, s);
-            pr_step<<<grid, kThreads, 0, s>>>(a);
+            pr_tiles<<<grid, kThreads, 0, s>>>(a);
+            pr_cross<<<cgrid, kThreads, 0, s>>>(a);
             if (e1) cudaEventRecord(e1, s);
-            g_launches++;
+            g_launches += 2;
             GM_CUDA_TRY(cudaGetLastError());
             if (e0) {
                 GM_CUDA_TRY(cudaEventSynchronize(e1));
@@ -215,32 +383,9 @@ gm_status pr_run(gm_graph* g, int32_t iters, int32_t* iters_done) {
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
     } else {
-        cudaGraph_t graph;
-        GM_CUDA_TRY(cudaGraphCreate(&graph, 0));
-        cudaGraphNode_t prev = nullptr;
-        cudaError_t e = cudaSuccess;
-        PrArgs args[2] = {make_pr_args(g, 0), make_pr_args(g, 1)};
-        for (int32_t it = 0; it < iters && e == cudaSuccess; ++it) {
-            void* kargs[] = {&args[it & 1]};
-            cudaKernelNodeParams kp = {};
-            kp.func = (void*)pr_step;
-            kp.gridDim = dim3((unsigned)grid);
-            kp.blockDim = dim3(kThreads);
-            kp.kernelParams = kargs;
-            cudaGraphNode_t node;
-            e = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
-            prev = node;
-        }
-        cudaGraphExec_t exec = nullptr;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-        if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
-        if (exec) cudaGraphExecDestroy(exec);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) {
-            set_error("PageRank graph: %s", cudaGetErrorString(e));
-            return GM_ERR_CUDA;
-        }
-        g_launches += (uint64_t)iters;
+        GM_TRY(pr_graph_for(g, iters, grid, cgrid));
+        GM_CUDA_TRY(cudaGraphLaunch(static_cast<PrGraph*>(g->pr)->exec, s));
+        g_launches += 2ull * (uint64_t)iters;
     }
     if (iters & 1) GM_CUDA_TRY(cudaMemcpyAsync(g->state.p, g->work.p, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
     GM_CUDA_TRY(cudaStreamSynchronize(s));
