@@ -28,6 +28,8 @@ struct PrArgs {
     const float* x_cur; float* x_nxt;
     const float* c_cur; float* c_nxt;
     float* lead; float* trail;  // per tile: partial sums of the columns that cross tiles
+    const int2* vd;             // per non-empty column: (vertex, out-degree)
+    const int4* xk;             // per tile k: (t1, vertex, out-degree, -) of the crossing column starting in k, t1 = -1 if none
     float r; int apply_all;
 };
 
@@ -38,9 +40,16 @@ __device__ __forceinline__ void pr_apply(const PrArgs& a, int32_t v, float sum) 
     a.c_nxt[v] = d > 0 ? x / (float)d : 0.0f;
 }
 
-// Apply for the vertex of non-empty column col.
+__device__ __forceinline__ void pr_apply_vd(const PrArgs& a, int32_t v, int32_t d, float sum) {
+    const float x = a.r + (1.0f - a.r) * sum;
+    a.x_nxt[v] = x;
+    a.c_nxt[v] = d > 0 ? x / (float)d : 0.0f;
+}
+
+// Apply for the vertex of non-empty column col (one load for vertex and degree).
 __device__ __forceinline__ void pr_apply_col(const PrArgs& a, int32_t col, float sum) {
-    pr_apply(a, __ldg(a.dc_jc + col), sum);
+    const int2 vd = __ldg(a.vd + col);
+    pr_apply_vd(a, vd.x, vd.y, sum);
 }
 
 constexpr int kEPT = 8;  // in-edges per lane of a 256-edge warp tile (kWTile = 32 x 8)
@@ -78,6 +87,8 @@ __global__ void __launch_bounds__(kThreads) pr_tiles(PrArgs a) {
 #pragma unroll
         for (int q = 0; q < kEPT; ++q) cv[q] = (uint32_t)q < nv ? __ldg(a.c_cur + src[q]) : 0.0f;
         const uint32_t hw = e0 < m ? __ldg(a.dc_head + (e0 >> 5)) : 0u;
+        // the tile's last column ends in it when the next tile starts a column (or there is none)
+        const bool ends_here = k + 1 >= ntiles || (__ldg(a.dc_head + (k + 1) * 8u) & 1u) != 0u;
         const uint32_t heads = (hw >> ((lane & 3) * 8)) & ((1u << nv) - 1u);
         const int32_t c0 = __ldg(a.dc_tile + k);
         // column numbering: column starts before this lane, and whether the tile starts one
@@ -133,13 +144,10 @@ __global__ void __launch_bounds__(kThreads) pr_tiles(PrArgs a) {
                 lead_end = true;
             } else if (lane < 31) {
                 pr_apply_col(a, end_col, R);  // complete inside the tile
-            } else {  // the trailing segment: complete unless the column goes on
-                const int64_t t1 = ((int64_t)__ldg(a.dc_cp + end_col + 1) - 1) >> 8;
-                if (t1 == (int64_t)k) {
-                    pr_apply_col(a, end_col, R);
-                } else {
-                    a.trail[k] = R;
-                }
+            } else if (ends_here) {  // the trailing segment: complete unless the column goes on
+                pr_apply_col(a, end_col, R);
+            } else {
+                a.trail[k] = R;
             }
         }
         if (lead_end) a.lead[k] = lead;
@@ -159,47 +167,60 @@ __global__ void __launch_bounds__(kThreads) pr_tiles(PrArgs a) {
 
 constexpr int64_t kSerialTiles = 8;  // crossing columns over more tiles are summed by a whole warp
 
-// The second half of a superstep: the columns that cross tiles.  Tile k's last
-// column continues into tile k + 1 when edge 256(k+1) starts no column; it
-// starts in tile k (so k is its t0) when its first edge lies there.  One thread
-// per tile finds its column and, when the column spans at most kSerialTiles
-// tiles, sums trail[t0] + lead[t0+1] + ... + lead[t1] in that order; longer
-// ones (the hubs) are summed by the whole warp, each lane over a fixed stride
-// of tiles, then a fixed shuffle tree.  Either way the order is fixed.
+// The second half of a superstep: the columns that cross tiles, each found
+// from the record xk[t0] of its first tile t0 (built once per graph).  One
+// thread per tile sums trail[t0] + lead[t0+1] + ... + lead[t1] in that order
+// when the column spans at most kSerialTiles tiles; longer ones (the hubs) are
+// summed by the whole warp, each lane over a fixed stride of tiles, then a
+// fixed shuffle tree.  Either way the order is fixed.
 __global__ void __launch_bounds__(kThreads) pr_cross(PrArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t nt = a.ntiles;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
-    for (int64_t base = (int64_t)blockIdx.x * kThreads + (threadIdx.x & ~31); base < nt - 1; base += stride) {
+    for (int64_t base = (int64_t)blockIdx.x * kThreads + (threadIdx.x & ~31); base < nt; base += stride) {
         const int64_t k = base + lane;
-        bool cross = false;
-        int32_t col = 0;
-        int64_t t1 = 0;
-        if (k < nt - 1 && (__ldg(a.dc_head + (k + 1) * 8) & 1u) == 0u) {
-            col = __ldg(a.dc_tile + k + 1);
-            if (((int64_t)__ldg(a.dc_cp + col) >> 8) == k) {
-                cross = true;
-                t1 = ((int64_t)__ldg(a.dc_cp + col + 1) - 1) >> 8;
-            }
-        }
-        if (cross && t1 - k <= kSerialTiles) {
+        const int4 x = k < nt ? __ldg(a.xk + k) : make_int4(-1, 0, 0, 0);
+        const int64_t t1 = x.x;
+        if (t1 >= 0 && t1 - k <= kSerialTiles) {
             float sum = __ldg(a.trail + k);
             for (int64_t t = k + 1; t <= t1; ++t) sum += __ldg(a.lead + t);
-            pr_apply_col(a, col, sum);
+            pr_apply_vd(a, x.y, x.z, sum);
         }
-        uint32_t big = __ballot_sync(kFull, cross && t1 - k > kSerialTiles);
+        uint32_t big = __ballot_sync(kFull, t1 - k > kSerialTiles);
         while (big) {
             const int src = __ffs(big) - 1;
             big &= big - 1;
             const int64_t kk = __shfl_sync(kFull, k, src);
             const int64_t tt = __shfl_sync(kFull, t1, src);
-            const int32_t cc = __shfl_sync(kFull, col, src);
             float sum = lane == 0 ? __ldg(a.trail + kk) : 0.0f;
             for (int64_t t = kk + 1 + lane; t <= tt; t += 32) sum += __ldg(a.lead + t);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
-            if (lane == 0) pr_apply_col(a, cc, sum);
+            if (lane == src) pr_apply_vd(a, x.y, x.z, sum);
         }
+    }
+}
+
+// Per-graph records for the supersteps: (vertex, out-degree) of each non-empty
+// column, and for each tile k the column that starts in k and crosses into
+// k + 1 (tile k + 1 starts with no column start, and that column's first edge
+// lies in k), with the last tile it reaches.
+__global__ void pr_records(PrArgs a, int64_t ncols, int2* vd, int4* xk) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncols; c += stride) {
+        const int32_t v = a.dc_jc[c];
+        vd[c] = make_int2(v, a.out_deg[v]);
+    }
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.ntiles; k += stride) {
+        int4 r = make_int4(-1, 0, 0, 0);
+        if (k + 1 < a.ntiles && (a.dc_head[(k + 1) * 8] & 1u) == 0u) {
+            const int32_t col = a.dc_tile[k + 1];
+            if (((int64_t)a.dc_cp[col] >> 8) == k) {
+                const int32_t v = a.dc_jc[col];
+                r = make_int4((int32_t)(((int64_t)a.dc_cp[col + 1] - 1) >> 8), v, a.out_deg[v], 0);
+            }
+        }
+        xk[k] = r;
     }
 }
 
@@ -233,16 +254,31 @@ int cross_grid(const gm_graph* g) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)num_sms() * 8));
 }
 
-// Workspace: the other rank array, two contribution arrays, and per tile the
-// leading and trailing partial sums.
-size_t pr_work_bytes(const gm_graph* g) {
-    const int64_t n = g->n > 0 ? g->n : 1, nt = g->dc_ntiles > 0 ? g->dc_ntiles : 1;
-    return sizeof(float) * (3 * (size_t)n + 2 * (size_t)nt);
+// Workspace, each part 16-byte aligned: the other rank array, two contribution
+// arrays, per tile the leading and trailing partial sums, then the records
+// (int2 per non-empty column, int4 per tile).
+struct PrLayout {
+    size_t lead, trail, vd, xk, total;
+};
+
+PrLayout pr_layout(const gm_graph* g) {
+    const size_t n = (size_t)(g->n > 0 ? g->n : 1), nt = (size_t)(g->dc_ntiles > 0 ? g->dc_ntiles : 1);
+    const size_t nc = (size_t)(g->dc_ncols > 0 ? g->dc_ncols : 1);
+    auto up = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    PrLayout L;
+    L.lead = up(sizeof(float) * 3 * n);
+    L.trail = up(L.lead + sizeof(float) * nt);
+    L.vd = up(L.trail + sizeof(float) * nt);
+    L.xk = up(L.vd + sizeof(int2) * nc);
+    L.total = L.xk + sizeof(int4) * nt;
+    return L;
 }
 
 PrArgs make_pr_args(gm_graph* g, int parity) {
-    const int64_t n = g->n > 0 ? g->n : 1, nt = g->dc_ntiles > 0 ? g->dc_ntiles : 1;
+    const int64_t n = g->n > 0 ? g->n : 1;
     float* work = as<float>(g->work);
+    char* wb = static_cast<char*>(g->work.p);
+    const PrLayout L = pr_layout(g);
     float* X[2] = {as<float>(g->state), work};
     float* C[2] = {work + n, work + 2 * n};
     PrArgs a{};
@@ -260,8 +296,10 @@ PrArgs make_pr_args(gm_graph* g, int parity) {
     a.x_nxt = X[parity ^ 1];
     a.c_cur = C[parity];
     a.c_nxt = C[parity ^ 1];
-    a.lead = work + 3 * n;
-    a.trail = work + 3 * n + nt;
+    a.lead = reinterpret_cast<float*>(wb + L.lead);
+    a.trail = reinterpret_cast<float*>(wb + L.trail);
+    a.vd = reinterpret_cast<const int2*>(wb + L.vd);
+    a.xk = reinterpret_cast<const int4*>(wb + L.xk);
     a.r = (float)g->params.r;
     a.apply_all = g->params.pr_apply_all;
     return a;
@@ -333,8 +371,16 @@ gm_status pr_prepare(gm_graph* g) {
     cudaStream_t s = g->stream;
     const int64_t n = g->n > 0 ? g->n : 1;
     GM_TRY(dev_alloc(g->state, sizeof(float) * n, s));
-    GM_TRY(dev_alloc(g->work, pr_work_bytes(g), s));
-    g->work_bytes = (int64_t)pr_work_bytes(g);
+    const PrLayout L = pr_layout(g);
+    GM_TRY(dev_alloc(g->work, L.total, s));
+    g->work_bytes = (int64_t)L.total;
+    if (g->dc_ntiles > 0) {
+        char* wb = static_cast<char*>(g->work.p);
+        pr_records<<<num_sms() * 4, 256, 0, s>>>(make_pr_args(g, 0), g->dc_ncols, reinterpret_cast<int2*>(wb + L.vd),
+                                                 reinterpret_cast<int4*>(wb + L.xk));
+        g_launches++;
+        GM_CUDA_TRY(cudaGetLastError());
+    }
     fill_f32<<<num_sms() * 4, 256, 0, s>>>(as<float>(g->state), g->n, 1.0f);
     g_launches++;
     GM_CUDA_TRY(cudaGetLastError());
