@@ -364,16 +364,42 @@ static gm_status ingest(gm_graph* g, const gm_edge_list* el, uint32_t flags) {
     } scope{s};
     DevBuf wide;  // flag: some weight needs more than 8 bits
     scope.add(d_src); scope.add(d_dst); scope.add(d_w); scope.add(wide);
+    // The weights are not needed until the edges are sorted, so from host memory
+    // they are copied on a side stream while the sort runs; the handle's stream
+    // waits for that copy before it first reads them, and in any case before
+    // this function returns (the guard is destroyed before the buffers are freed).
+    struct SideCopy {
+        cudaStream_t main, side = nullptr;
+        cudaEvent_t done = nullptr;
+        bool joined = true;
+        cudaError_t join() {
+            cudaError_t e = cudaSuccess;
+            if (!joined) e = cudaStreamWaitEvent(main, done, 0);
+            joined = true;
+            return e;
+        }
+        ~SideCopy() {
+            join();
+            if (done) cudaEventDestroy(done);
+            if (side) cudaStreamDestroy(side);
+        }
+    } wcopy{s};
     if (!el->on_device && m > 0) {
         GM_TRY(dev_alloc(d_src, sizeof(int32_t) * m, s));
         GM_TRY(dev_alloc(d_dst, sizeof(int32_t) * m, s));
+        if (g->wtype != GM_W_NONE) GM_TRY(dev_alloc(d_w, sizeof(uint32_t) * m, s));
         GM_CUDA_TRY(cudaMemcpyAsync(d_src.p, el->src, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
         GM_CUDA_TRY(cudaMemcpyAsync(d_dst.p, el->dst, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
         src = as<int32_t>(d_src);
         dst = as<int32_t>(d_dst);
         if (g->wtype != GM_W_NONE) {
-            GM_TRY(dev_alloc(d_w, sizeof(uint32_t) * m, s));
-            GM_CUDA_TRY(cudaMemcpyAsync(d_w.p, el->weight, sizeof(uint32_t) * m, cudaMemcpyHostToDevice, s));
+            GM_CUDA_TRY(cudaStreamCreateWithFlags(&wcopy.side, cudaStreamNonBlocking));
+            GM_CUDA_TRY(cudaEventCreateWithFlags(&wcopy.done, cudaEventDisableTiming));
+            GM_CUDA_TRY(cudaEventRecord(wcopy.done, s));  // d_w is allocated (stream-ordered) before the copy
+            GM_CUDA_TRY(cudaStreamWaitEvent(wcopy.side, wcopy.done, 0));
+            GM_CUDA_TRY(cudaMemcpyAsync(d_w.p, el->weight, sizeof(uint32_t) * m, cudaMemcpyHostToDevice, wcopy.side));
+            GM_CUDA_TRY(cudaEventRecord(wcopy.done, wcopy.side));
+            wcopy.joined = false;
             win = as<uint32_t>(d_w);
         }
     }
@@ -466,6 +492,7 @@ static gm_status ingest(gm_graph* g, const gm_edge_list* el, uint32_t flags) {
         GM_CUDA_TRY(cudaMemcpyAsync(g->col.p, edst.p, sizeof(int32_t) * mm, cudaMemcpyDeviceToDevice, s));
     if (g->wtype != GM_W_NONE) {
         GM_TRY(dev_alloc(g->w, sizeof(uint32_t) * (mm + kEdgePad), s));
+        GM_CUDA_TRY(wcopy.join());
         if (mm > 0) {
             gather_u32<<<blocks_for(mm), 256, 0, s>>>(win, as<uint32_t>(perm), mm, as<uint32_t>(g->w));
             LAUNCH_CHECK();

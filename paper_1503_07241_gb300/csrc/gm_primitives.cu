@@ -1,6 +1,7 @@
 // Device-wide primitives used by graph ingest: exclusive scan, stable LSD radix
 // sort of (uint64 key, uint32 value) pairs, and index compaction.  Written for
 // sm_103a: 32-wide warps, warp match/ballot for stable digit ranking.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 
@@ -223,58 +224,94 @@ gm_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaS
 }
 
 // ------------------------------------------------------------------------------
-// Stable LSD radix sort, 8-bit digits.  One pass = per-tile digit histogram,
-// exclusive scan of the digit-major histogram, stable scatter.  The scatter
-// ranks keys inside a tile with __match_any_sync (warp w owns a contiguous
-// sub-range of the tile and walks it 32 keys at a time in input order), places
-// them digit by digit in shared memory, and writes them out from there in order:
-// consecutive threads then write consecutive positions of each digit's run, so
-// the global writes are contiguous instead of one scattered store per key.
+// Stable LSD radix sort, 8-bit digits, one kernel per pass.  Before the passes,
+// one kernel counts every pass's digits over all keys (the digit order does not
+// change a digit's total), which gives each digit's first output position.  A
+// pass then needs, per tile and digit, the count of that digit in all earlier
+// tiles: each tile publishes its own counts as soon as it has ranked its keys,
+// and looks back over the tiles before it, adding their counts until it finds
+// one that has already published a running total (decoupled look-back).  Tiles
+// take their numbers from an atomic counter in the order they start, so the
+// tiles a tile waits for are running or done.  The waits are bounded; a tile
+// that gives up writes nothing and the sort reports GM_ERR_TIMEOUT.
+// Within a tile, keys are ranked with __match_any_sync (warp w owns a
+// contiguous sub-range of the tile and walks it 32 keys at a time in input
+// order), placed digit by digit in shared memory, and written out from there in
+// order: consecutive threads write consecutive positions of each digit's run.
 // ------------------------------------------------------------------------------
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortRounds = 16;                           // 32-key rounds per warp
 constexpr int kSortTile = kSortThreads * kSortRounds;     // 4096 keys per CTA
 constexpr int kRadix = 256;
-// dynamic shared memory of the scatter: the tile's keys and values, per-warp digit
+constexpr int kMaxSortPasses = 8;
+// dynamic shared memory of a pass: the tile's keys and values, per-warp digit
 // counts, the tile's digit offsets
 constexpr size_t kScatterSmem = (size_t)kSortTile * (sizeof(uint64_t) + sizeof(uint32_t)) +
                                 sizeof(uint32_t) * (kSortWarps * kRadix + 2 * kRadix);
+// A tile's status word per digit: the pass's tag (pass + 1) in bits 56-63, what
+// the value is in bits 54-55 (1: the tile's own count, 2: the total over this
+// tile and all before it), the value in bits 0-53.  Words of an earlier pass
+// carry another tag and read as "not yet published".
+constexpr uint64_t kStTagMask = 0xFFull << 56;
+constexpr uint64_t kStOwn = 1ull << 54, kStTotal = 2ull << 54, kStKind = 3ull << 54;
+constexpr uint64_t kStValue = (1ull << 54) - 1ull;
 
-__global__ void __launch_bounds__(kSortThreads) radix_hist(const uint64_t* __restrict__ keys, int64_t n,
-                                                           int shift, int64_t tiles,
-                                                           uint32_t* __restrict__ hist) {
-    __shared__ uint32_t h[kRadix];
-    h[threadIdx.x] = 0;
+__global__ void __launch_bounds__(kSortThreads) radix_hist_all(const uint64_t* __restrict__ keys, int64_t n,
+                                                               int passes, uint32_t* __restrict__ ghist) {
+    __shared__ uint32_t h[kMaxSortPasses * kRadix];
+    for (int i = threadIdx.x; i < kMaxSortPasses * kRadix; i += kSortThreads) h[i] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll 4
-    for (int k = 0; k < kSortRounds; ++k) {
-        int64_t i = base + (int64_t)k * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 0xFF], 1u);
+    for (int64_t i = (int64_t)blockIdx.x * kSortThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kSortThreads) {
+        const uint64_t k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p * kRadix + (int)((k >> (8 * p)) & 0xFF)], 1u);
     }
     __syncthreads();
-    hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+    for (int i = threadIdx.x; i < passes * kRadix; i += kSortThreads)
+        if (h[i]) atomicAdd(&ghist[i], h[i]);
 }
 
-__global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint64_t* __restrict__ keys_in,
-                                                              const uint32_t* __restrict__ vals_in, int64_t n,
-                                                              int shift, int64_t tiles,
-                                                              const uint32_t* __restrict__ hist_scan,
-                                                              uint64_t* __restrict__ keys_out,
-                                                              uint32_t* __restrict__ vals_out) {
+// First output position of every digit of every pass (exclusive scan over digits).
+__global__ void __launch_bounds__(kSortThreads) radix_bases(const uint32_t* __restrict__ ghist, int passes,
+                                                            uint32_t* __restrict__ gbase) {
+    __shared__ uint32_t sw[kScanThreads / 32 + 1];
+    for (int p = 0; p < passes; ++p) {
+        uint32_t excl;
+        block_excl_scan(ghist[p * kRadix + threadIdx.x], sw, excl);
+        gbase[p * kRadix + threadIdx.x] = excl;
+    }
+}
+
+__device__ __forceinline__ uint64_t sort_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_pass(const uint64_t* __restrict__ keys_in,
+                                                           const uint32_t* __restrict__ vals_in, int64_t n,
+                                                           int shift, uint64_t tag,
+                                                           const uint32_t* __restrict__ gbase,
+                                                           unsigned long long* status, uint32_t* tile_ctr,
+                                                           uint64_t* __restrict__ keys_out,
+                                                           uint32_t* __restrict__ vals_out, uint32_t* err) {
     extern __shared__ __align__(16) unsigned char sort_smem[];
     uint64_t* skey = reinterpret_cast<uint64_t*>(sort_smem);
     uint32_t* sval = reinterpret_cast<uint32_t*>(skey + kSortTile);
     uint32_t (*wcnt)[kRadix] = reinterpret_cast<uint32_t (*)[kRadix]>(sval + kSortTile);
     uint32_t* toff = &wcnt[kSortWarps][0];  // digit offsets inside the tile
     uint32_t* goff = toff + kRadix;         // digit offsets in the output
+    __shared__ uint32_t s_tile, s_gave_up;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        s_tile = atomicAdd(tile_ctr, 1u);
+        s_gave_up = 0u;
+    }
     for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&wcnt[0][0])[i] = 0;
-    goff[threadIdx.x] = hist_scan[(int64_t)threadIdx.x * tiles + blockIdx.x];
     __syncthreads();
 
-    const int64_t tbase = (int64_t)blockIdx.x * kSortTile;
+    const int64_t tile = s_tile;
+    const int64_t tbase = tile * kSortTile;
     const int64_t tlen = min((int64_t)kSortTile, n - tbase);  // keys in this tile
     const int wofs = warp * (32 * kSortRounds);                // the warp's sub-range in the tile
     uint32_t rank[kSortRounds];
@@ -297,7 +334,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint64_t* __
         __syncwarp();
     }
     __syncthreads();
-    // per digit: exclusive prefix over warps, and the digit's total
+    // per digit (thread = digit): exclusive prefix over warps, and the tile's count
     uint32_t tot = 0;
 #pragma unroll
     for (int w = 0; w < kSortWarps; ++w) {
@@ -305,7 +342,9 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint64_t* __
         wcnt[w][threadIdx.x] = tot;
         tot += c;
     }
-    // exclusive scan of the digit totals over the CTA (kRadix == kSortThreads)
+    volatile unsigned long long* mine = status + tile * kRadix + threadIdx.x;
+    *mine = tag | (tile == 0 ? kStTotal : kStOwn) | tot;
+    // exclusive scan of the digit counts over the CTA (kRadix == kSortThreads)
     {
         uint32_t x = tot;
 #pragma unroll
@@ -320,7 +359,31 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint64_t* __
         __syncthreads();
         toff[threadIdx.x] = add + x - tot;  // exclusive over the CTA
     }
+    // look back: this digit's count in all earlier tiles
+    uint64_t before = 0;
+    if (tile > 0) {
+        int64_t j = tile - 1;
+        const uint64_t t0 = sort_ns();
+        for (uint32_t tries = 0;;) {
+            const unsigned long long v = reinterpret_cast<volatile unsigned long long*>(status)[j * kRadix + threadIdx.x];
+            if ((v & kStTagMask) == tag && (v & kStKind) != 0ull) {
+                before += v & kStValue;
+                if ((v & kStKind) == kStTotal || j == 0) break;
+                --j;
+                continue;
+            }
+            if (++tries > (1u << 22) || ((tries & 63u) == 0u && sort_ns() - t0 > 1000000000ull)) {
+                s_gave_up = 1u;
+                atomicOr(err, 1u);
+                break;
+            }
+            __nanosleep(32);
+        }
+        *mine = tag | kStTotal | (before + tot);
+    }
+    goff[threadIdx.x] = gbase[threadIdx.x] + (uint32_t)before;
     __syncthreads();
+    if (s_gave_up) return;
     // place each key at its position inside the tile (digit-major, stable)
 #pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
@@ -339,47 +402,73 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint64_t* __
         const uint64_t k = skey[lp];
         const uint32_t d = (uint32_t)((k >> shift) & 0xFF);
         const uint32_t pos = goff[d] + ((uint32_t)lp - toff[d]);
-        keys_out[pos] = k;
-        vals_out[pos] = sval[lp];
+        if (pos < (uint64_t)n) {
+            keys_out[pos] = k;
+            vals_out[pos] = sval[lp];
+        }
     }
 }
 
 gm_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                            int64_t n, int bits, cudaStream_t s) {
     if (n <= 1 || bits <= 0) return GM_OK;
+    if (n >= (int64_t)0xFFFFFFFFll) {
+        set_error("radix sort: %lld keys, at most 2^32 - 2", (long long)n);
+        return GM_ERR_INVALID_ARG;
+    }
     static const cudaError_t attr_ok =
-        cudaFuncSetAttribute(radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+        cudaFuncSetAttribute(radix_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
     if (attr_ok != cudaSuccess) { set_error("radix sort: %s", cudaGetErrorString(attr_ok)); return GM_ERR_CUDA; }
     const int64_t tiles = (n + kSortTile - 1) / kSortTile;
-    const int passes = (bits + 7) / 8;
-    DevBuf hist, hscan;
-    GM_TRY(dev_alloc(hist, sizeof(uint32_t) * kRadix * tiles, s));
-    gm_status st = dev_alloc(hscan, sizeof(uint32_t) * (kRadix * tiles + 1), s);
-    if (st != GM_OK) { dev_free(hist, s); return st; }
+    const int passes = std::min((bits + 7) / 8, kMaxSortPasses);
+    // ghist, gbase (passes x kRadix each), a tile counter per pass, the error flag
+    const size_t meta_words = 2 * (size_t)kMaxSortPasses * kRadix + kMaxSortPasses + 1;
+    DevBuf meta, status;
+    GM_TRY(dev_alloc(meta, sizeof(uint32_t) * meta_words, s));
+    gm_status st = dev_alloc(status, sizeof(unsigned long long) * kRadix * (size_t)tiles, s);
+    if (st != GM_OK) { dev_free(meta, s); return st; }
+    uint32_t* ghist = as<uint32_t>(meta);
+    uint32_t* gbase = ghist + kMaxSortPasses * kRadix;
+    uint32_t* ctr = gbase + kMaxSortPasses * kRadix;
+    uint32_t* err = ctr + kMaxSortPasses;
+    cudaError_t e = cudaMemsetAsync(meta.p, 0, sizeof(uint32_t) * meta_words, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status.p, 0, sizeof(unsigned long long) * kRadix * (size_t)tiles, s);
+    if (e == cudaSuccess) {
+        const int64_t hb = std::min<int64_t>(tiles, (int64_t)num_sms() * 4);
+        radix_hist_all<<<(unsigned)hb, kSortThreads, 0, s>>>(keys, n, passes, ghist);
+        radix_bases<<<1, kSortThreads, 0, s>>>(ghist, passes, gbase);
+        g_launches += 2;
+        e = cudaGetLastError();
+    }
     uint64_t* kin = keys; uint32_t* vin = vals;
     uint64_t* kout = keys_alt; uint32_t* vout = vals_alt;
-    for (int p = 0; p < passes && st == GM_OK; ++p) {
-        const int shift = 8 * p;
-        radix_hist<<<(unsigned)tiles, kSortThreads, 0, s>>>(kin, n, shift, tiles, as<uint32_t>(hist));
+    for (int p = 0; p < passes && e == cudaSuccess; ++p) {
+        radix_pass<<<(unsigned)tiles, kSortThreads, kScatterSmem, s>>>(
+            kin, vin, n, 8 * p, (uint64_t)(p + 1) << 56, gbase + p * kRadix,
+            as<unsigned long long>(status), ctr + p, kout, vout, err);
         g_launches++;
-        st = scan_exclusive_u32(as<uint32_t>(hist), as<uint32_t>(hscan), kRadix * tiles, s);
-        if (st != GM_OK) break;
-        radix_scatter<<<(unsigned)tiles, kSortThreads, kScatterSmem, s>>>(kin, vin, n, shift, tiles,
-                                                                          as<uint32_t>(hscan), kout, vout);
-        g_launches++;
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) { set_error("radix sort: %s", cudaGetErrorString(e)); st = GM_ERR_CUDA; }
+        e = cudaGetLastError();
         uint64_t* tk = kin; kin = kout; kout = tk;
         uint32_t* tv = vin; vin = vout; vout = tv;
     }
-    if (st == GM_OK && kin != keys) {
-        cudaError_t e1 = cudaMemcpyAsync(keys, kin, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s);
-        cudaError_t e2 = cudaMemcpyAsync(vals, vin, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
-        if (e1 != cudaSuccess || e2 != cudaSuccess) { set_error("radix sort copy-back failed"); st = GM_ERR_CUDA; }
+    if (e == cudaSuccess && kin != keys) {
+        e = cudaMemcpyAsync(keys, kin, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(vals, vin, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
     }
-    dev_free(hist, s);
-    dev_free(hscan, s);
-    return st;
+    uint32_t h_err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(meta, s);
+    dev_free(status, s);
+    if (e != cudaSuccess) {
+        set_error("radix sort: %s", cudaGetErrorString(e));
+        return GM_ERR_CUDA;
+    }
+    if (h_err) {
+        set_error("radix sort: a tile waited more than a second for the tiles before it");
+        return GM_ERR_TIMEOUT;
+    }
+    return GM_OK;
 }
 
 // ------------------------------------------------------------------------------
