@@ -364,7 +364,9 @@ enum {
     GM_OPT_BETA_X1000 = 7,    /* BFS pull->push switch: frontier vertices < n / beta */
     GM_OPT_SSSP_PULL_PPM = 8, /* SSSP: pull when frontier edges > ppm * 1e-6 * m */
     GM_OPT_PULL_STAGE = 9,    /* SSSP pull: messages of the highest-out-degree sources each CTA stages in
-                                 shared memory, 0..49152 (rounded down to a multiple of 4; default 40960) */
+                                 shared memory, 0..49152 (rounded down to a multiple of 4; default 40960),
+                                 counted as 4-byte messages; the pull over octets (one-byte weights) stores
+                                 them as 16 bits and so stages twice as many sources in the same bytes */
     GM_OPT_TEST_STALL_STAGE = 10, /* test hook, 0 or 1: the SSSP pull's staging barrier expects 16 bytes more
                                      than its copies bring, so every CTA's bounded wait (about a second)
                                      runs out; those CTAs gather every message from global memory, the

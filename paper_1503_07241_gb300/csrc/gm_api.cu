@@ -345,7 +345,7 @@ gm_status gm_set_option(gm_graph* g, int32_t option, int64_t value) {
             if (t.pull_stage == (int32_t)(value & ~(int64_t)3)) return GM_OK;
             t.pull_stage = (int32_t)(value & ~(int64_t)3);
             trav_release(g);  // the loop graph bakes the shared-memory size in
-            return balance_octets(g, pull_stage_messages(g));  // slot order for the new stage
+            return balance_octets(g, pull_stage16_messages(g));  // slot order for the new stage
         case GM_OPT_TEST_STALL_STAGE:
             if (value < 0 || value > 1) break;
             t.test_stall_stage = (int32_t)value;

@@ -607,17 +607,18 @@ __global__ void octet_fill(const int32_t* __restrict__ cp, int64_t ncols, const 
 }
 
 // Slot order inside each octet, chosen so that the warp's shared-memory reads of
-// staged messages (sources of rank < hot) spread over the 32 banks: for every
-// tile one thread takes the octets in lane order and puts each staged source of
-// an octet into the still-free slot (one of its real slots) whose warp-wide read
-// has used that source's bank least so far; the other sources fill the slots
-// left.  Any order of an octet's real slots gives the same minimum; on RMAT
-// scale 22 (hot = 40,960) it takes the reads from 2.3 to 1.2 bank-conflict
-// wavefronts per warp-wide read.  Padding slots stay last.
+// staged messages (sources of rank < staged, two 16-bit messages per 4-byte
+// bank word, so rank r sits in bank (r / 2) mod 32) spread over the 32 banks:
+// for every tile one thread takes the octets in lane order and puts each staged
+// source of an octet into the still-free slot (one of its real slots) whose
+// warp-wide read has used that source's bank least so far; the other sources
+// fill the slots left.  Any order of an octet's real slots gives the same
+// minimum; on RMAT scale 22 (40,960 4-byte messages then) it took the reads from
+// 2.3 to 1.2 bank-conflict wavefronts per warp-wide read.  Padding slots stay last.
 constexpr int kBalanceThreads = 64;
 __global__ void __launch_bounds__(kBalanceThreads) octet_balance(uint32_t* __restrict__ ow,
                                                                 const uint8_t* __restrict__ meta, int64_t tiles,
-                                                                uint32_t hot) {
+                                                                uint32_t staged) {
     __shared__ uint8_t s_use[kBalanceThreads][kOctet][32];
     uint8_t (*use)[32] = s_use[threadIdx.x];
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * blockDim.x) {
@@ -631,8 +632,8 @@ __global__ void __launch_bounds__(kBalanceThreads) octet_balance(uint32_t* __res
             uint32_t taken = 0;  // slots assigned so far
             for (int j = 0; j < real; ++j) {
                 const uint32_t r = w[j] >> 8;
-                if (r >= hot) continue;
-                const int b = (int)(r & 31u);
+                if (r >= staged) continue;
+                const int b = (int)((r >> 1) & 31u);
                 int best = -1;
                 for (int q = 0; q < real; ++q)
                     if (!((taken >> q) & 1u) && (best < 0 || use[q][b] < use[best][b])) best = q;
@@ -642,7 +643,7 @@ __global__ void __launch_bounds__(kBalanceThreads) octet_balance(uint32_t* __res
             }
             int q = 0;
             for (int j = 0; j < real; ++j) {
-                if ((w[j] >> 8) < hot) continue;
+                if ((w[j] >> 8) < staged) continue;
                 while ((taken >> q) & 1u) ++q;
                 out[q] = w[j];
                 taken |= 1u << q;
@@ -652,13 +653,13 @@ __global__ void __launch_bounds__(kBalanceThreads) octet_balance(uint32_t* __res
     }
 }
 
-// Re-orders the octets' slots for a stage of `hot` messages (octet_balance).
-gm_status balance_octets(gm_graph* g, int64_t hot) {
+// Re-orders the octets' slots for a stage of `staged` messages (octet_balance).
+gm_status balance_octets(gm_graph* g, int64_t staged) {
     if (!g->oct_w.p || g->oct_tiles == 0) return GM_OK;
     cudaStream_t s = g->stream;
     const int64_t blocks = std::min<int64_t>((g->oct_tiles + kBalanceThreads - 1) / kBalanceThreads, 65535);
     octet_balance<<<(unsigned)blocks, kBalanceThreads, 0, s>>>(as<uint32_t>(g->oct_w), as<uint8_t>(g->oct_meta),
-                                                               g->oct_tiles, (uint32_t)std::max<int64_t>(hot, 0));
+                                                               g->oct_tiles, (uint32_t)std::max<int64_t>(staged, 0));
     LAUNCH_CHECK();
     GM_CUDA_TRY(cudaStreamSynchronize(s));
     return GM_OK;
@@ -738,7 +739,7 @@ gm_status build_pull_edge_words_impl(gm_graph* g) {
     GM_CUDA_TRY(cudaStreamSynchronize(s));  // the temporaries are freed on return
     g->oct_tiles = tiles;
     g->oct_slots = (int64_t)octets * kOctet;
-    return balance_octets(g, pull_stage_messages(g));
+    return balance_octets(g, pull_stage16_messages(g));
 }
 }  // namespace
 

@@ -89,7 +89,7 @@ struct TravCtl {
     uint32_t loops;               // iterations of the device loop (for the launch count)
     unsigned long long reached;   // out-degrees of the vertices whose property became finite since the reset
     uint32_t list_len;            // sorted-list sparse vector: entries of the current superstep's list
-    uint32_t list_pad;
+    uint32_t stage16_off;         // superstep + 1 of the last pull whose staged messages did not all fit 16 bits
 };
 
 // Options and tuning knobs of a graph handle.
@@ -212,11 +212,16 @@ gm_status trav_prepare(gm_graph* g);
 gm_status trav_reuse(gm_graph* g);  // program_set between BFS and SSSP with the workspace kept
 gm_status build_source_ranks(gm_graph* g);  // gm_graph.cu
 gm_status build_pull_edge_words(gm_graph* g);  // gm_graph.cu
-gm_status balance_octets(gm_graph* g, int64_t hot);  // gm_graph.cu
+gm_status balance_octets(gm_graph* g, int64_t staged);  // gm_graph.cu
 // Messages the SSSP pull stages per CTA (ranks [0, result)): the stage option,
 // at most 49,152 and n rounded down to a multiple of 4.
 inline int64_t pull_stage_messages(const gm_graph* g) {
     return std::min<int64_t>(std::min<int64_t>(49152, g->tune.pull_stage), g->n & ~(int64_t)3);
+}
+// The octet pull stores its staged messages as 16 bits, so the same shared
+// memory holds twice as many (a multiple of 8: whole 16-byte copies).
+inline int64_t pull_stage16_messages(const gm_graph* g) {
+    return std::min<int64_t>(2 * pull_stage_messages(g), g->n & ~(int64_t)7);
 }
 gm_status trav_set_active(gm_graph* g, const int32_t* vertices_dev, int64_t count);
 gm_status trav_run(gm_graph* g, int32_t max_iters, int32_t* iters_done);

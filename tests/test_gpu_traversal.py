@@ -290,6 +290,36 @@ def test_sssp_staged_and_gathered_messages(gm, direction, stage):
             assert np.array_equal(got, ref) and it == rit
 
 
+@pytest.mark.parametrize("direction", [0, 2])
+def test_sssp_distances_beyond_16_bits(gm, direction):
+    """The octet pull stages its hot messages as 16 bits.  A chain of 600
+    vertices joined by weight-255 edges carries distances up to 152,745, past
+    what 16 bits hold (from superstep 257 on); those pulls must take every
+    message from global memory instead.  Beside the chain, a random graph with
+    small weights whose distances stay low.  Forced pull and the automatic
+    switch, from the chain's head and from the random part, against the oracle."""
+    rng = np.random.default_rng(1616)
+    L, n = 600, 3000
+    chain_s = np.arange(0, L - 1, dtype=np.int32)
+    chain_d = chain_s + 1
+    rs = rng.integers(L, n, 15000).astype(np.int32)
+    rd = rng.integers(L, n, 15000).astype(np.int32)
+    src = np.concatenate([chain_s, rs, np.array([L], np.int32)])
+    dst = np.concatenate([chain_d, rd, np.array([0], np.int32)])
+    w = np.concatenate([np.full(L - 1, 255, np.uint32), rng.integers(1, 8, 15000).astype(np.uint32),
+                        np.array([3], np.uint32)])
+    g = gm.Graph(n, src, dst, w)
+    og = oracle.Graph(n, src, dst, w)
+    g.program_set(gm.GM_SSSP)
+    g.set_option(gm.GM_OPT_DIRECTION, direction)
+    for seeds in ([0], [int(L) + 5], [0, int(L) + 5]):
+        got, it = _run(gm, g, gm.GM_SSSP, seeds)
+        ref, rit = og.sssp(seeds)
+        assert np.array_equal(got, ref) and it == rit
+        if seeds == [0]:
+            assert int(ref[L - 1]) == 255 * (L - 1) > 0xFFFF
+
+
 def test_symmetrized_bfs(gm):
     n, s, d, _ = rmat_case(12)
     flags = CLEAN | oracle.SYMMETRIZE
