@@ -72,7 +72,7 @@ struct TravArgs {
     int64_t oct_tiles;
     const int32_t* dc_rank;  // SSSP: rank of each non-empty column's vertex
     int32_t hot;             // SSSP pull: messages of ranks [0, hot) are staged in shared memory
-    uint16_t* msg16;         // octet pull: the messages of ranks [0, hot16) as 16 bits (0xFFFF = infinity),
+    uint16_t* msg16;         // octet pull: the messages of ranks [0, hot16) as signed 16 bits (-1 = infinity),
     int32_t hot16;           //   written by the push launch of a pull superstep and staged instead of msg
     uint32_t stage_extra;    // test hook: bytes the staging barrier expects beyond its copies (0 or 16)
     uint32_t* lkey;          // sorted-list sparse vector (GM_OPT_SPARSE_LIST): indices, ascending
@@ -976,8 +976,8 @@ __device__ __forceinline__ void oct_load(const TravArgs& a, uint32_t k, int lane
     x.c0 = __ldg(a.oct_c0 + k);
 }
 
-// Messages of an octet's slots: staged ranks from shared memory (16 bits,
-// 0xFFFF = infinity), the rest from global memory, or (LIST) from the sorted
+// Messages of an octet's slots: staged ranks from shared memory (signed 16 bits,
+// -1 = infinity), the rest from global memory, or (LIST) from the sorted
 // list.  Padding slots hold rank 0 (staged, or one shared address) and are
 // masked to infinity by the caller, so the loads need no branch.
 template <bool LIST>
@@ -993,14 +993,9 @@ __device__ __forceinline__ void oct_gather(const TravArgs& a, const uint32_t* __
         } else {
             // shared memory is read only for staged ranks (with no stage the
             // kernel has no dynamic shared memory at all)
-            uint32_t v;
-            if ((int32_t)rq < hlim) {
-                const uint32_t v16 = reinterpret_cast<const uint16_t*>(s_hot)[rq];
-                v = v16 == 0xFFFFu ? kInf : v16;
-            } else {
-                v = __ldg(msgc + rq);
-            }
-            mv[q] = v;
+            // (a signed 16-bit read: 0xFFFF, infinity, widens to 0xFFFFFFFF)
+            mv[q] = (int32_t)rq < hlim ? (uint32_t)(int32_t)reinterpret_cast<const int16_t*>(s_hot)[rq]
+                                       : __ldg(msgc + rq);
         }
     }
 }
@@ -1056,7 +1051,10 @@ __global__ void __launch_bounds__(kPullThreads, 1) trav_pull_o(TravArgs a) {
         uint32_t R = kInf;
 #pragma unroll
         for (int q = 0; q < kOctet; ++q) {
-            const uint32_t c = sat_add(mv[q], cur.w[q] & 0xFFu);
+            // msg + w saturating at infinity: with n <= 2^24 and weights below
+            // 256 no finite sum reaches 2^32 - 1, so only infinity wraps, and
+            // the max keeps it
+            const uint32_t c = max(mv[q], mv[q] + (cur.w[q] & 0xFFu));
             R = min(R, (uint32_t)q < real ? c : kInf);
         }
         const int32_t c0 = cur.c0;
@@ -1305,8 +1303,9 @@ __device__ __forceinline__ void pull_apply(const TravArgs& a, uint32_t t, WarpQ*
 }
 
 // The push launch of a pull superstep (which has no push work) writes the 16-bit
-// copy of the hot messages that the octet pull stages: 0xFFFF for infinity, the
-// distance itself below 0xFFFF.  A finite distance of 0xFFFF or more cannot be
+// copy of the hot messages that the octet pull stages, as signed 16-bit values:
+// -1 (0xFFFF) for infinity, which a signed read widens to 0xFFFFFFFF, and the
+// distance itself below 0x7FFF.  A finite distance of 0x7FFF or more cannot be
 // held; then stage16_off is set to t + 1 and that pull stages nothing (every
 // message comes from global memory, results unchanged).  Kept out of line so
 // that the push's own register allocation does not carry it.
@@ -1315,8 +1314,8 @@ __device__ __noinline__ void pack_stage16(const TravArgs& a, TravCtl* c, uint32_
     uint2* o2 = reinterpret_cast<uint2*>(a.msg16);
     bool wide = false;
     auto enc = [&wide](uint32_t x) {
-        wide |= x != kInf && x >= 0xFFFFu;
-        return x == kInf ? 0xFFFFu : min(x, 0xFFFEu);
+        wide |= x != kInf && x >= 0x7FFFu;
+        return x == kInf ? 0xFFFFu : min(x, 0x7FFEu);
     };
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.hot16 / 4; i += (int64_t)gridDim.x * blockDim.x) {
         const uint4 m = m4[i];

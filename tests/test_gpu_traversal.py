@@ -292,10 +292,10 @@ def test_sssp_staged_and_gathered_messages(gm, direction, stage):
 
 @pytest.mark.parametrize("direction", [0, 2])
 def test_sssp_distances_beyond_16_bits(gm, direction):
-    """The octet pull stages its hot messages as 16 bits.  A chain of 600
-    vertices joined by weight-255 edges carries distances up to 152,745, past
-    what 16 bits hold (from superstep 257 on); those pulls must take every
-    message from global memory instead.  Beside the chain, a random graph with
+    """The octet pull stages its hot messages as signed 16 bits (finite values
+    below 32,767).  A chain of 600 vertices joined by weight-255 edges carries
+    distances up to 152,745, past what the stage holds (from superstep 129 on);
+    those pulls must take every message from global memory instead.  Beside the chain, a random graph with
     small weights whose distances stay low.  Forced pull and the automatic
     switch, from the chain's head and from the random part, against the oracle."""
     rng = np.random.default_rng(1616)
