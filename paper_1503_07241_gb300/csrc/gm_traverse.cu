@@ -482,8 +482,30 @@ __device__ __forceinline__ void flush_acc(const TravArgs& a, Acc& acc, int nxt, 
                                           unsigned long long* s_stat) {
     TravCtl* c = &a.ctl->c;
     if (acc.wq) {
-        warp_flush(a, acc.wq, 1u, nxt);
-        warp_flush(a, acc.wq, 2u, nxt);
+        // one queue reservation per CTA and bin: the warps' staged counts are
+        // summed in shared memory and each warp writes at its own offset
+        __shared__ uint32_t s_off[kWarps][2];
+        __shared__ uint32_t s_base[2];
+        WarpQ* q0 = acc.wq - (threadIdx.x >> 5);
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            uint32_t tot = 0;
+            for (int w = 0; w < kWarps; ++w) {
+                s_off[w][threadIdx.x] = tot;
+                tot += q0[w].n[threadIdx.x];
+            }
+            s_base[threadIdx.x] = tot ? atomicAdd(&c->count[nxt][threadIdx.x + 1], tot) : 0u;
+        }
+        __syncthreads();
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int b = 0; b < 2; ++b) {
+            const uint32_t n = acc.wq->n[b];
+            int32_t* dst = a.q[nxt][b + 1] + s_base[b] + s_off[warp][b];
+            for (uint32_t i = lane; i < n; i += 32) dst[i] = acc.wq->buf[b][i];
+        }
+        __syncwarp();
+        if (lane < 2) acc.wq->n[lane] = 0u;
+        __syncwarp();
     }
     unsigned long long vals[6] = {acc.scanned, acc.verts, acc.medges, acc.unvis, acc.n0, acc.reached};
 #pragma unroll
