@@ -576,33 +576,57 @@ __global__ void octet_counts(const int32_t* __restrict__ cp, int64_t ncols, uint
         cnt[c] = c < ncols ? (uint32_t)((cp[c + 1] - cp[c] + kOctet - 1) / kOctet) : 0u;
 }
 
-// One warp per non-empty column: its in-edges into its octets as one word each,
-// the source's rank in the high 24 bits and the one-byte weight in the low 8
-// (padding slots 0), the octet headers, and the first column of every tile that
-// begins inside the column.  Within a tile of 32 octets the words are stored
-// slot-quad-major: slots 0-3 of octets 0..31, then slots 4-7 of octets 0..31, so
-// that each 16-byte load of a warp reads 512 consecutive bytes.
-__global__ void octet_fill(const int32_t* __restrict__ cp, int64_t ncols, const uint32_t* __restrict__ ooff,
-                           const int32_t* __restrict__ row, const uint8_t* __restrict__ w8,
-                           const int32_t* __restrict__ rank, uint32_t* __restrict__ ow, uint8_t* __restrict__ meta,
-                           int32_t* __restrict__ c0) {
+// The octet layout is built in three steps.  octet_starts marks each column's
+// first octet (header bit 0x80); octet_tile_starts counts the marks of every
+// tile of 32 octets, and an exclusive scan of those counts gives, for each tile,
+// the column of its first octet; octet_fill, one warp per tile and one lane per
+// octet, finds its column from that and its lane's marks, and writes the
+// octet's in-edges as one word each -- the source's rank in the high 24 bits and
+// the one-byte weight in the low 8 (padding slots 0) -- the octet header (real
+// slots, and the mark) and the tile's first column.  Within a tile the words are
+// stored slot-quad-major: slots 0-3 of octets 0..31, then slots 4-7 of octets
+// 0..31, so a lane's octet is two 16-byte stores and the warp's are 512
+// consecutive bytes each.
+__global__ void octet_starts(const uint32_t* __restrict__ ooff, int64_t ncols, uint8_t* __restrict__ meta) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncols; c += (int64_t)gridDim.x * blockDim.x)
+        meta[ooff[c]] = 0x80;
+}
+
+__global__ void octet_tile_starts(const uint8_t* __restrict__ meta, int64_t octets, int64_t tiles,
+                                  uint32_t* __restrict__ tcnt) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < ncols; c += nw) {
-        const int64_t e0 = cp[c], e1 = cp[c + 1];
-        const int64_t o0 = ooff[c], no = ooff[c + 1] - o0;
-        for (int64_t j = lane; j < no; j += 32) {
-            const int64_t o = o0 + j;
-            const int64_t eb = e0 + j * kOctet;
-            const int real = (int)min((int64_t)kOctet, e1 - eb);
-            const int64_t base = (o / kOctTile) * (kOctTile * kOctet) + (o % kOctTile) * 4;
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < tiles; k += nw) {
+        const int64_t o = k * kOctTile + lane;
+        const uint32_t ball = __ballot_sync(0xffffffffu, o < octets && (meta[o] & 0x80));
+        if (lane == 0) tcnt[k] = (uint32_t)__popc(ball);
+    }
+}
+
+__global__ void octet_fill(const int32_t* __restrict__ cp, const uint32_t* __restrict__ ooff, int64_t octets,
+                           int64_t tiles, const uint32_t* __restrict__ tpre, const int32_t* __restrict__ row,
+                           const uint8_t* __restrict__ w8, const int32_t* __restrict__ rank,
+                           uint32_t* __restrict__ ow, uint8_t* __restrict__ meta, int32_t* __restrict__ c0) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < tiles; k += nw) {
+        const int64_t o = k * kOctTile + lane;
+        const bool here = o < octets;
+        const bool start = here && (meta[o] & 0x80);
+        const uint32_t ball = __ballot_sync(0xffffffffu, start);
+        if (!here) continue;  // the tail of the last tile stays zero
+        const int64_t col = (int64_t)tpre[k] + __popc(ball & (0xffffffffu >> (31 - lane))) - 1;
+        const int64_t eb = (int64_t)cp[col] + (o - (int64_t)ooff[col]) * kOctet;
+        const int real = (int)min((int64_t)kOctet, (int64_t)cp[col + 1] - eb);
+        uint32_t wd[kOctet];
 #pragma unroll
-            for (int q = 0; q < kOctet; ++q)
-                ow[base + (q / 4) * (kOctTile * 4) + (q % 4)] =
-                    q < real ? ((uint32_t)rank[row[eb + q]] << 8) | (uint32_t)w8[eb + q] : 0u;
-            meta[o] = (uint8_t)(real | (j == 0 ? 0x80 : 0));
-            if (o % kOctTile == 0) c0[o / kOctTile] = (int32_t)c;
-        }
+        for (int q = 0; q < kOctet; ++q)
+            wd[q] = q < real ? ((uint32_t)rank[row[eb + q]] << 8) | (uint32_t)w8[eb + q] : 0u;
+        uint4* tw = reinterpret_cast<uint4*>(ow + k * (kOctTile * kOctet));
+        tw[lane] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+        tw[kOctTile + lane] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+        meta[o] = (uint8_t)(real | (start ? 0x80 : 0));
+        if (lane == 0) c0[k] = (int32_t)col;
     }
 }
 
@@ -622,33 +646,57 @@ __global__ void __launch_bounds__(kBalanceThreads) octet_balance(uint32_t* __res
     __shared__ uint8_t s_use[kBalanceThreads][kOctet][32];
     uint8_t (*use)[32] = s_use[threadIdx.x];
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * blockDim.x) {
-        for (int q = 0; q < kOctet; ++q)
-            for (int b = 0; b < 32; ++b) use[q][b] = 0;
-        uint32_t* tw = ow + t * (kOctTile * kOctet);
+        uint32_t* u32 = reinterpret_cast<uint32_t*>(&use[0][0]);
+#pragma unroll
+        for (int i = 0; i < kOctet * 32 / 4; ++i) u32[i] = 0u;
+        // the tile is slot-quad-major: octet L's slots 0-3 are 16-byte word L, slots 4-7 word 32 + L
+        uint4* tw = reinterpret_cast<uint4*>(ow + t * (kOctTile * kOctet));
         for (int L = 0; L < kOctTile; ++L) {
-            const int real = meta[t * kOctTile + L] & 0xF;
-            uint32_t w[kOctet], out[kOctet];
-            for (int q = 0; q < kOctet; ++q) w[q] = tw[(q / 4) * (kOctTile * 4) + L * 4 + (q % 4)];
-            uint32_t taken = 0;  // slots assigned so far
-            for (int j = 0; j < real; ++j) {
+            const uint32_t real = meta[t * kOctTile + L] & 0xFu;
+            const uint4 lo = tw[L], hi = tw[kOctTile + L];
+            const uint32_t w[kOctet] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+            const uint32_t slots = (1u << real) - 1u;
+            uint32_t taken = 0u;   // slots assigned so far
+            uint32_t assign = 0u;  // 3 bits per slot: the source placed there
+#pragma unroll
+            for (int j = 0; j < kOctet; ++j) {  // staged sources first, each where its bank is used least
                 const uint32_t r = w[j] >> 8;
-                if (r >= staged) continue;
-                const int b = (int)((r >> 1) & 31u);
-                int best = -1;
-                for (int q = 0; q < real; ++q)
-                    if (!((taken >> q) & 1u) && (best < 0 || use[q][b] < use[best][b])) best = q;
-                out[best] = w[j];
-                taken |= 1u << best;
-                use[best][b]++;
+                if ((uint32_t)j < real && r < staged) {
+                    const uint32_t b = (r >> 1) & 31u;
+                    int best = 0;
+                    uint32_t bu = 0xFFFFu;
+#pragma unroll
+                    for (int q = 0; q < kOctet; ++q) {
+                        const uint32_t u = use[q][b];
+                        if ((((slots & ~taken) >> q) & 1u) && u < bu) {
+                            best = q;
+                            bu = u;
+                        }
+                    }
+                    taken |= 1u << best;
+                    assign |= (uint32_t)j << (3 * best);
+                    use[best][b] = (uint8_t)(bu + 1u);
+                }
             }
-            int q = 0;
-            for (int j = 0; j < real; ++j) {
-                if ((w[j] >> 8) < staged) continue;
-                while ((taken >> q) & 1u) ++q;
-                out[q] = w[j];
-                taken |= 1u << q;
+#pragma unroll
+            for (int j = 0; j < kOctet; ++j) {  // the others into the free slots, in order
+                if ((uint32_t)j < real && (w[j] >> 8) >= staged) {
+                    const int q = __ffs(slots & ~taken) - 1;
+                    taken |= 1u << q;
+                    assign |= (uint32_t)j << (3 * q);
+                }
             }
-            for (int q2 = 0; q2 < real; ++q2) tw[(q2 / 4) * (kOctTile * 4) + L * 4 + (q2 % 4)] = out[q2];
+            uint32_t out[kOctet];
+#pragma unroll
+            for (int q = 0; q < kOctet; ++q) {
+                const uint32_t j = (assign >> (3 * q)) & 7u;
+                uint32_t v = w[0];
+#pragma unroll
+                for (int i = 1; i < kOctet; ++i) v = j == (uint32_t)i ? w[i] : v;
+                out[q] = (uint32_t)q < real ? v : w[q];  // padding slots stay last
+            }
+            tw[L] = make_uint4(out[0], out[1], out[2], out[3]);
+            tw[kOctTile + L] = make_uint4(out[4], out[5], out[6], out[7]);
         }
     }
 }
@@ -709,7 +757,7 @@ gm_status build_pull_edge_words_impl(gm_graph* g) {
     // octet offsets of the columns: an exclusive scan of their octet counts
     struct Tmp {
         cudaStream_t s;
-        DevBuf b[2];
+        DevBuf b[4];
         ~Tmp() { for (DevBuf& x : b) dev_free(x, s); }
     } tmp{s};
     DevBuf &cnt = tmp.b[0], &ooff = tmp.b[1];
@@ -730,10 +778,18 @@ gm_status build_pull_edge_words_impl(gm_graph* g) {
     GM_CUDA_TRY(cudaMemsetAsync(g->oct_meta.p, 0, (size_t)octs_alloc, s));
     GM_CUDA_TRY(cudaMemsetAsync(g->oct_c0.p, 0, sizeof(int32_t) * std::max<int64_t>(tiles, 1), s));
     if (ncols > 0) {
-        octet_fill<<<num_sms() * 8, 256, 0, s>>>(as<int32_t>(g->dc_cp), ncols, as<uint32_t>(ooff),
-                                                 as<int32_t>(g->row), as<uint8_t>(g->cw8), as<int32_t>(g->src_rank),
-                                                 as<uint32_t>(g->oct_w), as<uint8_t>(g->oct_meta),
-                                                 as<int32_t>(g->oct_c0));
+        DevBuf &tcnt = tmp.b[2], &tpre = tmp.b[3];
+        GM_TRY(dev_alloc(tcnt, sizeof(uint32_t) * tiles, s));
+        GM_TRY(dev_alloc(tpre, sizeof(uint32_t) * (tiles + 1), s));
+        octet_starts<<<blocks_for(ncols), 256, 0, s>>>(as<uint32_t>(ooff), ncols, as<uint8_t>(g->oct_meta));
+        LAUNCH_CHECK();
+        const unsigned wb = (unsigned)std::min<int64_t>((tiles + 7) / 8, (int64_t)num_sms() * 16);
+        octet_tile_starts<<<wb, 256, 0, s>>>(as<uint8_t>(g->oct_meta), octets, tiles, as<uint32_t>(tcnt));
+        LAUNCH_CHECK();
+        GM_TRY(scan_exclusive_u32(as<uint32_t>(tcnt), as<uint32_t>(tpre), tiles, s));
+        octet_fill<<<wb, 256, 0, s>>>(as<int32_t>(g->dc_cp), as<uint32_t>(ooff), octets, tiles, as<uint32_t>(tpre),
+                                      as<int32_t>(g->row), as<uint8_t>(g->cw8), as<int32_t>(g->src_rank),
+                                      as<uint32_t>(g->oct_w), as<uint8_t>(g->oct_meta), as<int32_t>(g->oct_c0));
         LAUNCH_CHECK();
     }
     GM_CUDA_TRY(cudaStreamSynchronize(s));  // the temporaries are freed on return
