@@ -380,7 +380,7 @@ def _kernel_line(name, acc, peak):
 # launches, supersteps 3 and 4 of the first SSSP source); valid only for the
 # sources it was taken on (hash of the traversal kernels and of the graph build,
 # which lays the octets out).
-PULL_A_TRAFFIC = {"source_sha256": "2bb54bffe008bee4ef6c7d1dd1049a34857d1dc332e266aaca975d577ec1699b",
+PULL_A_TRAFFIC = {"source_sha256": "0476bca22e26601cdc49f0ae3da4c838b2c8f9f9137b484226264907b3625425",
                   "bytes_per_launch": 332.0e6}
 _TRAFFIC_SOURCES = ("gm_traverse.cu", "gm_internal.cuh", "gm_graph.cu")
 
