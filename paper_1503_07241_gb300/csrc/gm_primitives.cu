@@ -345,6 +345,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass(const uint64_t* __res
     volatile unsigned long long* mine = status + tile * kRadix + threadIdx.x;
     *mine = tag | (tile == 0 ? kStTotal : kStOwn) | tot;
     // exclusive scan of the digit counts over the CTA (kRadix == kSortThreads)
+    uint32_t my_toff;
     {
         uint32_t x = tot;
 #pragma unroll
@@ -357,8 +358,11 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass(const uint64_t* __res
         uint32_t add = 0;
         for (int w = 0; w < warp; ++w) add += toff[w * 32 + 31];
         __syncthreads();
-        toff[threadIdx.x] = add + x - tot;  // exclusive over the CTA
+        my_toff = add + x - tot;  // exclusive over the CTA
     }
+    // each warp's first position for this digit inside the tile (one shared read per key below)
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) wcnt[w][threadIdx.x] += my_toff;
     // look back: this digit's count in all earlier tiles
     uint64_t before = 0;
     if (tile > 0) {
@@ -381,7 +385,8 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass(const uint64_t* __res
         }
         *mine = tag | kStTotal | (before + tot);
     }
-    goff[threadIdx.x] = gbase[threadIdx.x] + (uint32_t)before;
+    // output position of tile position lp of this digit = goff[digit] + lp (mod 2^32)
+    goff[threadIdx.x] = gbase[threadIdx.x] + (uint32_t)before - my_toff;
     __syncthreads();
     if (s_gave_up) return;
     // place each key at its position inside the tile (digit-major, stable)
@@ -391,7 +396,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass(const uint64_t* __res
         if (j < tlen) {
             const uint64_t k = keys_in[tbase + j];
             const uint32_t d = (uint32_t)((k >> shift) & 0xFF);
-            const uint32_t lp = toff[d] + wcnt[warp][d] + rank[r];
+            const uint32_t lp = wcnt[warp][d] + rank[r];
             skey[lp] = k;
             sval[lp] = vals_in[tbase + j];
         }
@@ -401,7 +406,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass(const uint64_t* __res
     for (int lp = threadIdx.x; lp < tlen; lp += kSortThreads) {
         const uint64_t k = skey[lp];
         const uint32_t d = (uint32_t)((k >> shift) & 0xFF);
-        const uint32_t pos = goff[d] + ((uint32_t)lp - toff[d]);
+        const uint32_t pos = goff[d] + (uint32_t)lp;
         if (pos < (uint64_t)n) {
             keys_out[pos] = k;
             vals_out[pos] = sval[lp];
