@@ -241,8 +241,8 @@ gm_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaS
 // ------------------------------------------------------------------------------
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortRounds = 16;                           // 32-key rounds per warp
-constexpr int kSortTile = kSortThreads * kSortRounds;     // 4096 keys per CTA
+constexpr int kSortRounds = 15;  // 32-key rounds per warp: 3840-key tiles, 55 KB of shared memory, 4 CTAs per SM
+constexpr int kSortTile = kSortThreads * kSortRounds;     // keys per CTA
 constexpr int kRadix = 256;
 constexpr int kMaxSortPasses = 8;
 // dynamic shared memory of a pass: the tile's keys and values, per-warp digit
