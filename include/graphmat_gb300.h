@@ -49,7 +49,7 @@ typedef enum gm_status {
     GM_ERR_CUDA = 3,           /* a CUDA runtime call failed (see gm_last_error) */
     GM_ERR_STATE = 4,          /* calls in the wrong order, e.g. gm_run before gm_program_set */
     GM_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
-    GM_ERR_UNSUPPORTED = 6     /* valid request this build does not handle */
+    GM_ERR_UNSUPPORTED = 6     /* valid request the library does not handle */
 } gm_status;
 
 typedef enum gm_weight_type {
